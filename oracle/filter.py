@@ -1,0 +1,139 @@
+"""Accept/reject and one hierarchical filter step.  TEST INFRASTRUCTURE ONLY.
+
+Eq. (hierarchy): after the proposal T_0, level i accepts with
+min{1, exp(-Delta_i)}; the result of a level is the proposal of the next.
+Decision rule: one uniform u per decision (draw map TAG_ACCEPT, counter =
+filter step, level, block), accept iff Delta <= 0 or u < exp(-Delta).
+
+One step of the 3-level filter (domain sweep -> block det ratios -> global
+Schur det ratio), Sec. 3, Eq. (4step) with one DD level and App. C:
+
+ 0) U' = domain sweep of U on the active links at coupling beta0
+    (sweep ids start at step * 2^20).
+ 1) per block b: Delta_b = beta_block * dS_w,b + sum_i (|M_{b,i} xi|^2 - |xi|^2)
+    accepted block by block (blocks with extent >= 3, where the active links
+    of different blocks share no plaquette and the proposal factorises); for
+    smaller blocks one decision on sum_b Delta_b.  Rejected blocks get their
+    old links back.
+ 2) Delta = beta_global * dS_w + Schur estimate between U and the field after
+    level 1; accepted or rejected as a whole.
+ 3) the field is translated by a random vector (after the global step).
+
+dS_w,b attributes every plaquette to the block of the first changed link in
+the order (x,mu), (x+mu,nu), (x+nu,mu), (x,nu); a link belongs to the block of
+its starting site.
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import philox
+from .estimator import block_level, global_level
+from .gauge import domain_sweep, plaquette_field, wilson_action
+from .lattice import gauge_shift
+
+SWEEP_STRIDE = 1 << 20
+
+
+@dataclass
+class FilterParams:
+    kappa: float
+    beta0: float
+    n_iter: int = 1
+    n_or: int = 0
+    n_block: int = 4
+    n_global: int = 4
+    beta_block: float = 0.0
+    beta_global: float = 0.0
+    tol: float = 1e-13
+    global_level: bool = True
+
+
+def gaussian_acceptance(sigma2):
+    """Eq. (acceptance): <P_acc> = erfc(sqrt(Sigma^2 / 8)) for Gaussian Delta."""
+    from math import erfc, sqrt
+    return erfc(sqrt(sigma2 / 8.0))
+
+
+def stochastic_acceptance(lam):
+    """App. A.2: acceptance probability of one stochastic step in terms of the
+    eigenvalues lam of M^dagger M,
+    P_acc = sum_i min(1, 1/lam_i) prod_{j != i} (lam_i - 1)/(lam_i - lam_j),
+    evaluated with 60-digit mpmath arithmetic (distinct eigenvalues)."""
+    import mpmath as mp
+    with mp.workdps(60):
+        lam = [mp.mpf(float(x)) for x in lam]
+        tot = mp.mpf(0)
+        for i, li in enumerate(lam):
+            term = min(mp.mpf(1), 1 / li)
+            for j, lj in enumerate(lam):
+                if j != i:
+                    term *= (li - 1) / (li - lj)
+            tot += term
+        return float(tot)
+
+
+def accept(delta, u):
+    return bool(delta <= 0.0 or u < np.exp(-delta))
+
+
+def per_block_action_change(U, Up, geom):
+    """dS_w,b (without beta) for every block, by plaquette attribution."""
+    changed = np.any(U != Up, axis=(-1, -2))              # [dims, 4]
+    out = np.zeros(geom.n_blocks)
+    bidx = geom.block_index
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            d = -(np.real(np.trace(plaquette_field(Up, mu, nu), axis1=-2, axis2=-1))
+                  - np.real(np.trace(plaquette_field(U, mu, nu), axis1=-2, axis2=-1))) / 3.0
+            cands = [
+                (changed[..., mu], bidx),
+                (gauge_shift(changed[..., nu], mu, +1), gauge_shift(bidx, mu, +1)),
+                (gauge_shift(changed[..., mu], nu, +1), gauge_shift(bidx, nu, +1)),
+                (changed[..., nu], bidx),
+            ]
+            owner = np.full(geom.dims, -1)
+            for ch, bi in cands:
+                sel = (owner < 0) & ch
+                owner[sel] = bi[sel]
+            m = owner >= 0
+            out += np.bincount(owner[m], weights=d[m], minlength=geom.n_blocks)
+    return out
+
+
+def filter_step(U, geom, prm, seed, step):
+    """Returns (new field, record dict)."""
+    active = geom.active_links()
+    Unew, _, failed = domain_sweep(U, geom, prm.beta0, prm.n_iter, prm.n_or, seed, step * SWEEP_STRIDE)
+
+    d_blk = block_level(U, Unew, geom, prm.kappa, prm.n_block, seed, step, tol=prm.tol).sum(axis=1)
+    if prm.beta_block != 0.0:
+        d_blk = d_blk + prm.beta_block * per_block_action_change(U, Unew, geom)
+    per_block = min(geom.block) >= 3
+    if per_block:
+        acc_b = np.array([accept(d_blk[b], philox.accept_uniform(seed, step, 1, b))
+                          for b in range(geom.n_blocks)])
+    else:
+        a = accept(d_blk.sum(), philox.accept_uniform(seed, step, 1, 0))
+        acc_b = np.full(geom.n_blocks, a)
+
+    Umid = U.copy()
+    link_block_acc = acc_b[geom.block_index][..., None] & active
+    Umid[link_block_acc] = Unew[link_block_acc]
+
+    rec = {"delta_block": d_blk, "accept_block": acc_b, "hb_failed": failed}
+    Ufin = Umid
+    if prm.global_level:
+        dg = global_level(U, Umid, geom, prm.kappa, prm.n_global, seed, step, tol=prm.tol)
+        d = float(dg.sum())
+        if prm.beta_global != 0.0:
+            d += prm.beta_global * (wilson_action(Umid) - wilson_action(U))
+        acc_g = accept(d, philox.accept_uniform(seed, step, 2, 0))
+        rec["delta_global"] = d
+        rec["delta_global_terms"] = dg
+        rec["accept_global"] = acc_g
+        if not acc_g:
+            Ufin = U.copy()
+    s = philox.shift_vector(seed, step, geom.dims)
+    rec["shift"] = s
+    return geom.translate(Ufin, s), rec
