@@ -1,0 +1,223 @@
+/*
+ * psms.h -- C ABI of the GB300 (sm_103a) library for the hot path of the
+ * Partially Stochastic Multi-Step (PSMS) filter for N_f = 2 Wilson fermions
+ * (J. Finkenrath, F. Knechtli, B. Leder, "Fermions as Global Correction: the
+ * QCD Case", arXiv:1204.1306).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  - Lattice extents dims[4] = (L0, L1, L2, L3); mu = 0 is time.  Quark fields
+ *    are antiperiodic in time and periodic in space (Sec. 6); gauge fields are
+ *    periodic.  Domain blocks have extents block[4]; every block extent must be
+ *    a power of two >= 2 dividing the lattice extent (Sec. 3, Fig. 1).
+ *  - Canonical layouts (used by *_set / *_get / *_import / *_export):
+ *      links  : complex<double> U[x0][x1][x2][x3][mu][3][3]   (x3 fastest)
+ *      spinor : complex<double> psi[x0][x1][x2][x3][spin][colour]
+ *    complex numbers are interleaved (re, im) doubles.  U[x][mu] is the link
+ *    from x to x + mu-hat.  gamma matrices: chiral basis,
+ *      gamma_mu = [[0, e_mu], [e_mu^dagger, 0]], e_0 = -1, e_k = -i sigma_k,
+ *    gamma_5 = diag(1, 1, -1, -1).
+ *  - D always denotes D_w + m0 of Eq. (Dw) with m0 = 1/(2 kappa) - 4:
+ *      D psi(x) = (4 + m0) psi(x) - 1/2 sum_mu { U(x,mu)(1 - gamma_mu) psi(x+mu)
+ *                                   + U(x-mu,mu)^dagger (1 + gamma_mu) psi(x-mu) }.
+ *  - "native" spinor buffers hold one full-lattice quark field in the
+ *    library's device layout for the given precision (even-odd, block-major,
+ *    structure of arrays); their size is psms_spinor_bytes().  Convert with
+ *    psms_spinor_import / psms_spinor_export.
+ *  - All pointers named *_dev are device pointers owned by the caller; the
+ *    library never frees them.  Host result arrays are caller-allocated.  The
+ *    context owns its gauge fields, scratch buffers and CUDA events.
+ *  - Every entry point returns a psms_status and never throws or aborts; on
+ *    error psms_last_error() describes the failure.  Work is queued on the
+ *    stream given to psms_set_stream (default: the legacy default stream);
+ *    entry points that return host values synchronise that stream.
+ *  - Random numbers: Philox-4x64-10 (Salmon et al., SC'11), key = (seed, tag),
+ *    counters as stated at each entry point; a uniform is
+ *    ((w >> 12) + 1/2) * 2^-52 of a 64-bit output word w, so identical
+ *    (seed, counter) give identical draws on every device.
+ */
+#ifndef PSMS_H
+#define PSMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PSMS_OK = 0,
+    PSMS_EINVAL = 1,     /* bad argument or unsupported geometry            */
+    PSMS_ENOMEM = 2,     /* device allocation failed                        */
+    PSMS_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed     */
+    PSMS_ENOCONV = 4,    /* a Krylov solve missed its tolerance at maxit    */
+    PSMS_ETIMEOUT = 5,   /* a device-side bounded wait ran out              */
+    PSMS_ESPECTRUM = 6,  /* non-finite estimate (NaN / Inf)                 */
+    PSMS_EHEATBATH = 7   /* an SU(2) draw hit its attempt limit             */
+} psms_status;
+
+typedef enum {
+    PSMS_PREC_F64 = 0,   /* FP64 links, FP64 spinors, FP64 arithmetic       */
+    PSMS_PREC_F32 = 1,   /* FP32 links, FP32 spinors, FP32 arithmetic       */
+    PSMS_PREC_BF16 = 2   /* FP32 links, BF16 spinor storage, FP32 arithmetic*/
+} psms_prec;
+
+/* Operator selector for psms_dw_apply / psms_solve. */
+enum {
+    PSMS_OP_FULL = -1,   /* D on the whole lattice (Eq. (Dw))               */
+    PSMS_OP_BLOCKS = -2  /* D_bb + D_ww: every Dirichlet block at once      */
+    /* a value b >= 0 selects the single block D_b with lexicographic block
+       index b = ((B0*nb1 + B1)*nb2 + B2)*nb3 + B3, B_mu = x_mu / block[mu];
+       the output is zero outside block b. */
+};
+
+/* Active-link sets of psms_gauge_sweep. */
+enum {
+    PSMS_ACTIVE_BLOCKS = 0, /* links of a block with <= 1 endpoint on its boundary
+                               (Sec. 3); every intra-block link if an extent <= 2 */
+    PSMS_ACTIVE_ALL = 1     /* every link (pure-gauge thermalisation)          */
+};
+
+/* Estimator levels / modes of psms_logdet_ratio. */
+enum { PSMS_LEVEL_BLOCK = 1, PSMS_LEVEL_GLOBAL = 2 };
+enum { PSMS_EST_INTERP = 0, PSMS_EST_INDEPENDENT = 1 };
+
+typedef struct psms_ctx psms_ctx;
+
+typedef struct {
+    int dims[4];       /* lattice extents L0..L3 (each even)                 */
+    int block[4];      /* block extents l0..l3 (powers of two >= 2)          */
+    double kappa;      /* hopping parameter, kappa = 1/(2 m0 + 8)            */
+    int n_fields;      /* number of gauge-field slots owned by the context   */
+} psms_lattice_desc;
+
+typedef struct {
+    int outer_iters;       /* FP64 defect-correction steps                     */
+    long long inner_iters; /* Krylov iterations summed over systems            */
+    double true_residual;  /* max over systems of |b - D x| / |b| (FP64)       */
+    int n_systems;
+} psms_solve_info;
+
+typedef struct {
+    /* level 0: proposal (Sec. 6): n_iter x (HB + n_or OR + n_or OR + HB)    */
+    double beta0;
+    int n_iter;
+    int n_or;
+    /* level 1: block det ratios, N = n_block interpolation steps (Eq. (staccN)) */
+    int n_block;
+    double beta_block;     /* coefficient of dS_w at level 1 (App. C)          */
+    /* level 2: global Schur-complement det ratio                              */
+    int n_global;
+    double beta_global;    /* coefficient of dS_w at level 2 (App. C)          */
+    int global_level;      /* 0: stop after level 1                            */
+    double tol;            /* relative true residual of every solve            */
+    int inner_prec;        /* psms_prec of the inner Krylov iterations         */
+    uint64_t seed;
+    uint64_t step;         /* filter step counter (RNG counter base)           */
+} psms_filter_params;
+
+typedef struct {
+    int n_blocks;
+    int n_accept_blocks;
+    int accept_global;
+    int shift[4];
+    double delta_global;
+    double delta_block_sum;
+    long long solver_iters;
+    int hb_failed;
+} psms_filter_result;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context for one lattice geometry (Sec. 3).  Allocates n_fields
+ * FP64 gauge fields (set to the unit field).  Fails with PSMS_EINVAL for
+ * extents that are odd, not divisible by the block, or blocks that are not
+ * powers of two; PSMS_ENOMEM / PSMS_ECUDA otherwise. */
+psms_status psms_create(const psms_lattice_desc *desc, psms_ctx **out);
+psms_status psms_destroy(psms_ctx *ctx);
+/* Static description of the last error on ctx (never NULL). */
+const char *psms_last_error(const psms_ctx *ctx);
+/* Queue subsequent work on this cudaStream_t (pass NULL for the default). */
+psms_status psms_set_stream(psms_ctx *ctx, void *cuda_stream);
+/* Lattice facts: n_blocks, dim(P) of Eq. (dimproj) (0 without a black/white
+ * colouring), active links per lattice. */
+psms_status psms_geometry_info(const psms_ctx *ctx, long long *n_blocks, long long *dim_P,
+                               long long *n_active_links);
+
+/* ---- gauge fields --------------------------------------------------------- */
+
+/* Synthetic field U = exp(i eps H), H = sum_a omega_a lambda_a / 2, omega_a ~
+ * N(0,1) from Philox (key (seed, 1), counter (4*site+mu, j, 0, 0), j = 0,1,
+ * Box-Muller), then reunitarised (Gram-Schmidt rows 0,1; row 2 = conj(r0 x r1)). */
+psms_status psms_gauge_init(psms_ctx *ctx, int field, double eps, uint64_t seed);
+/* Copy a canonical-layout FP64 field in / out of slot `field`. */
+psms_status psms_gauge_set(psms_ctx *ctx, int field, const double *links_dev);
+psms_status psms_gauge_get(psms_ctx *ctx, int field, double *links_dev);
+psms_status psms_gauge_copy(psms_ctx *ctx, int dst, int src);
+/* Mean plaquette <ReTr U_p>/3 and S_w of Eq. (Sw) (without beta), FP64,
+ * deterministic reduction.  Host outputs (either may be NULL). */
+psms_status psms_plaquette(psms_ctx *ctx, int field, double *mean_plaq, double *s_w);
+/* Pure-gauge proposal (Sec. 6) on slot `field`: n_iter iterations of
+ * HB + n_or OR sweeps (checkerboard subsets (mu, parity) in forward order)
+ * and n_or OR + HB sweeps in reversed order, Cabibbo-Marinari SU(2)
+ * subgroups in random order per link, at coupling beta, then FP64
+ * reunitarisation of the updated links.  Sweep ids start at sweep0.
+ * *failed_out (may be NULL) counts SU(2) draws that hit 1000 attempts. */
+psms_status psms_gauge_sweep(psms_ctx *ctx, int field, int active_set, int n_iter, int n_or,
+                             double beta, uint64_t seed, uint64_t sweep0, int *failed_out);
+/* Random translation U'(x) = U(x - s) of slot `field` (Sec. 3). */
+psms_status psms_gauge_translate(psms_ctx *ctx, int field, const int shift[4]);
+
+/* ---- quark fields ----------------------------------------------------------- */
+
+size_t psms_spinor_bytes(const psms_ctx *ctx, int prec);
+psms_status psms_spinor_import(psms_ctx *ctx, const double *canonical_dev, void *native_dev, int prec);
+psms_status psms_spinor_export(psms_ctx *ctx, const void *native_dev, double *canonical_dev, int prec);
+
+/* out = op(U_field) in, Eq. (Dw); op is PSMS_OP_FULL, PSMS_OP_BLOCKS or a
+ * block index (Eq. (domdec), Dirichlet blocks).  in / out are native
+ * buffers of precision prec and must not alias. */
+psms_status psms_dw_apply(psms_ctx *ctx, int field, int op, const void *in_dev, void *out_dev, int prec);
+
+/* Solve op(U_field) x = b to |b - op x| <= tol |b| in FP64 (true residual),
+ * with inner Krylov iterations (even-odd preconditioned CGNR) in
+ * inner_prec inside FP64 defect correction.  b, x: native FP64 buffers.
+ * PSMS_ENOCONV if maxit inner iterations do not reach tol. */
+psms_status psms_solve(psms_ctx *ctx, int field, int op, const void *b_dev, void *x_dev, double tol,
+                       int maxit, int inner_prec, psms_solve_info *info);
+
+/* Stochastic estimate of ln det ratios between slots field_old (U) and
+ * field_new (U'), Eqs. (stacc), (staccN), (gfparam):
+ *   mode PSMS_EST_INTERP: n factors M_i = op(U_{i+1})^-1 op(U_i),
+ *     U_i = ((n-i)/n) U + (i/n) U', one noise xi_i each;
+ *   mode PSMS_EST_INDEPENDENT: n independent noises with M = op(U')^-1 op(U).
+ * level PSMS_LEVEL_BLOCK: op = D_b for every block b; delta_out[b*n + i] =
+ *   |M_{b,i} xi_i|^2 - |xi_i|^2 restricted to block b.
+ * level PSMS_LEVEL_GLOBAL: op = 1 - PQ (Sec. 4.4), noise on range(P),
+ *   (1 - PQ)^-1 = 1 - P D^-1 D_wb; delta_out[i].
+ * Noise: key (seed, 2), counter (counter, (level << 32) | i, site, j).
+ * delta_out: host array. */
+psms_status psms_logdet_ratio(psms_ctx *ctx, int level, int field_old, int field_new, int n, int mode,
+                              uint64_t seed, uint64_t counter, double tol, int inner_prec,
+                              double *delta_out);
+
+/* One step of the 3-level hierarchical filter (Eq. (hierarchy), Sec. 3):
+ * proposal sweep of `field`, per-block stochastic det-ratio accept/reject
+ * (one decision on the sum for blocks with an extent <= 2), global Schur
+ * accept/reject, random translation.  Decisions: accept iff Delta <= 0 or
+ * u < exp(-Delta), u from key (seed, 4), counter (step, level, block, 0).
+ * delta_block_out / accept_block_out: host arrays of n_blocks (may be NULL). */
+psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params *prm,
+                             psms_filter_result *res, double *delta_block_out, int *accept_block_out);
+
+/* Profiling: when enabled, the context records CUDA events around its
+ * Wilson-operator launches; read the count and summed milliseconds. */
+psms_status psms_profile_enable(psms_ctx *ctx, int enable);
+psms_status psms_profile_read(psms_ctx *ctx, long long *launches, double *total_ms,
+                              double *bytes_per_launch_sum);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSMS_H */

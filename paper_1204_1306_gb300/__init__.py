@@ -1,0 +1,273 @@
+"""Python binding of the PSMS GB300 library (C ABI in ``include/psms.h``).
+
+Argument marshalling only: every function below forwards to the ``psms_*``
+entry point of the same name in ``_lib/libpsms.so``.  Device buffers are
+passed as CUDA torch tensors (their ``data_ptr()``); host results come back as
+Python / numpy values.  There is no fallback: if the shared library is
+missing or a call fails, an exception is raised.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "PsmsError", "Context", "load_library",
+    "psms_create", "psms_destroy", "psms_set_stream", "psms_geometry_info",
+    "psms_gauge_init", "psms_gauge_set", "psms_gauge_get", "psms_gauge_copy", "psms_plaquette",
+    "psms_gauge_sweep", "psms_gauge_translate", "psms_spinor_bytes", "psms_spinor_import",
+    "psms_spinor_export", "psms_dw_apply", "psms_solve", "psms_logdet_ratio", "psms_filter_step",
+    "psms_profile_enable", "psms_profile_read",
+    "PREC_F64", "PREC_F32", "PREC_BF16", "OP_FULL", "OP_BLOCKS", "ACTIVE_BLOCKS", "ACTIVE_ALL",
+    "LEVEL_BLOCK", "LEVEL_GLOBAL", "EST_INTERP", "EST_INDEPENDENT",
+]
+
+PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
+OP_FULL, OP_BLOCKS = -1, -2
+ACTIVE_BLOCKS, ACTIVE_ALL = 0, 1
+LEVEL_BLOCK, LEVEL_GLOBAL = 1, 2
+EST_INTERP, EST_INDEPENDENT = 0, 1
+
+STATUS = {0: "PSMS_OK", 1: "PSMS_EINVAL", 2: "PSMS_ENOMEM", 3: "PSMS_ECUDA", 4: "PSMS_ENOCONV",
+          5: "PSMS_ETIMEOUT", 6: "PSMS_ESPECTRUM", 7: "PSMS_EHEATBATH"}
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libpsms.so")
+
+
+class PsmsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class LatticeDesc(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4), ("block", ctypes.c_int * 4), ("kappa", ctypes.c_double),
+                ("n_fields", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_longlong),
+                ("true_residual", ctypes.c_double), ("n_systems", ctypes.c_int)]
+
+
+class FilterParams(ctypes.Structure):
+    _fields_ = [("beta0", ctypes.c_double), ("n_iter", ctypes.c_int), ("n_or", ctypes.c_int),
+                ("n_block", ctypes.c_int), ("beta_block", ctypes.c_double), ("n_global", ctypes.c_int),
+                ("beta_global", ctypes.c_double), ("global_level", ctypes.c_int), ("tol", ctypes.c_double),
+                ("inner_prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("step", ctypes.c_uint64)]
+
+
+class FilterResult(ctypes.Structure):
+    _fields_ = [("n_blocks", ctypes.c_int), ("n_accept_blocks", ctypes.c_int), ("accept_global", ctypes.c_int),
+                ("shift", ctypes.c_int * 4), ("delta_global", ctypes.c_double),
+                ("delta_block_sum", ctypes.c_double), ("solver_iters", ctypes.c_longlong),
+                ("hb_failed", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_U64 = ctypes.c_uint64
+_SIGS = {
+    "psms_create": [ctypes.POINTER(LatticeDesc), ctypes.POINTER(_P)],
+    "psms_destroy": [_P],
+    "psms_set_stream": [_P, _P],
+    "psms_geometry_info": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                           ctypes.POINTER(ctypes.c_longlong)],
+    "psms_gauge_init": [_P, _I, _D, _U64],
+    "psms_gauge_set": [_P, _I, _P],
+    "psms_gauge_get": [_P, _I, _P],
+    "psms_gauge_copy": [_P, _I, _I],
+    "psms_plaquette": [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    "psms_gauge_sweep": [_P, _I, _I, _I, _I, _D, _U64, _U64, ctypes.POINTER(_I)],
+    "psms_gauge_translate": [_P, _I, ctypes.POINTER(_I)],
+    "psms_spinor_import": [_P, _P, _P, _I],
+    "psms_spinor_export": [_P, _P, _P, _I],
+    "psms_dw_apply": [_P, _I, _I, _P, _P, _I],
+    "psms_solve": [_P, _I, _I, _P, _P, _D, _I, _I, ctypes.POINTER(SolveInfo)],
+    "psms_logdet_ratio": [_P, _I, _I, _I, _I, _I, _U64, _U64, _D, _I, ctypes.POINTER(_D)],
+    "psms_filter_step": [_P, _I, ctypes.POINTER(FilterParams), ctypes.POINTER(FilterResult),
+                         ctypes.POINTER(_D), ctypes.POINTER(_I)],
+    "psms_profile_enable": [_P, _I],
+    "psms_profile_read": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), ctypes.POINTER(_D)],
+}
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load ``libpsms.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1204_1306_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.psms_last_error.argtypes = [_P]
+    lib.psms_last_error.restype = ctypes.c_char_p
+    lib.psms_spinor_bytes.argtypes = [_P, _I]
+    lib.psms_spinor_bytes.restype = ctypes.c_size_t
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_cuda:
+            raise ValueError("device buffers must be CUDA tensors")
+        if not t.is_contiguous():
+            raise ValueError("device buffers must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(int(t))
+
+
+class Context:
+    """Owns one ``psms_ctx``."""
+
+    def __init__(self, dims, block, kappa, n_fields=4):
+        self.lib = load_library()
+        d = LatticeDesc((ctypes.c_int * 4)(*dims), (ctypes.c_int * 4)(*block), float(kappa), int(n_fields))
+        h = _P()
+        st = self.lib.psms_create(ctypes.byref(d), ctypes.byref(h))
+        if st:
+            raise PsmsError(st, "psms_create failed")
+        self.handle = h
+        self.dims = tuple(dims)
+        self.block = tuple(block)
+        self.kappa = kappa
+        self.n_fields = n_fields
+        self.V = int(np.prod(dims))
+
+    def check(self, st):
+        if st:
+            raise PsmsError(st, self.lib.psms_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.psms_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def psms_create(dims, block, kappa, n_fields=4):
+    return Context(dims, block, kappa, n_fields)
+
+
+def psms_destroy(ctx):
+    ctx.close()
+
+
+def psms_set_stream(ctx, stream):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    raw = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    ctx.check(ctx.lib.psms_set_stream(ctx.handle, _P(raw)))
+
+
+def psms_geometry_info(ctx):
+    a, b, c = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    ctx.check(ctx.lib.psms_geometry_info(ctx.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def psms_gauge_init(ctx, field, eps, seed):
+    ctx.check(ctx.lib.psms_gauge_init(ctx.handle, field, float(eps), int(seed)))
+
+
+def psms_gauge_set(ctx, field, links_dev):
+    ctx.check(ctx.lib.psms_gauge_set(ctx.handle, field, _ptr(links_dev)))
+
+
+def psms_gauge_get(ctx, field, links_dev):
+    ctx.check(ctx.lib.psms_gauge_get(ctx.handle, field, _ptr(links_dev)))
+
+
+def psms_gauge_copy(ctx, dst, src):
+    ctx.check(ctx.lib.psms_gauge_copy(ctx.handle, dst, src))
+
+
+def psms_plaquette(ctx, field):
+    a, b = _D(), _D()
+    ctx.check(ctx.lib.psms_plaquette(ctx.handle, field, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def psms_gauge_sweep(ctx, field, active_set, n_iter, n_or, beta, seed, sweep0):
+    f = _I()
+    ctx.check(ctx.lib.psms_gauge_sweep(ctx.handle, field, active_set, n_iter, n_or, float(beta), int(seed),
+                                       int(sweep0), ctypes.byref(f)))
+    return f.value
+
+
+def psms_gauge_translate(ctx, field, shift):
+    ctx.check(ctx.lib.psms_gauge_translate(ctx.handle, field, (_I * 4)(*shift)))
+
+
+def psms_spinor_bytes(ctx, prec):
+    return int(ctx.lib.psms_spinor_bytes(ctx.handle, prec))
+
+
+def psms_spinor_import(ctx, canonical_dev, native_dev, prec):
+    ctx.check(ctx.lib.psms_spinor_import(ctx.handle, _ptr(canonical_dev), _ptr(native_dev), prec))
+
+
+def psms_spinor_export(ctx, native_dev, canonical_dev, prec):
+    ctx.check(ctx.lib.psms_spinor_export(ctx.handle, _ptr(native_dev), _ptr(canonical_dev), prec))
+
+
+def psms_dw_apply(ctx, field, op, in_dev, out_dev, prec):
+    ctx.check(ctx.lib.psms_dw_apply(ctx.handle, field, op, _ptr(in_dev), _ptr(out_dev), prec))
+
+
+def psms_solve(ctx, field, op, b_dev, x_dev, tol, maxit, inner_prec):
+    info = SolveInfo()
+    ctx.check(ctx.lib.psms_solve(ctx.handle, field, op, _ptr(b_dev), _ptr(x_dev), float(tol), int(maxit),
+                                 inner_prec, ctypes.byref(info)))
+    return {"outer_iters": info.outer_iters, "inner_iters": info.inner_iters,
+            "true_residual": info.true_residual, "n_systems": info.n_systems}
+
+
+def psms_logdet_ratio(ctx, level, field_old, field_new, n, mode, seed, counter, tol, inner_prec):
+    nb = int(np.prod([d // b for d, b in zip(ctx.dims, ctx.block)]))
+    size = nb * n if level == LEVEL_BLOCK else n
+    out = (_D * size)()
+    ctx.check(ctx.lib.psms_logdet_ratio(ctx.handle, level, field_old, field_new, int(n), mode, int(seed),
+                                        int(counter), float(tol), inner_prec, out))
+    a = np.frombuffer(out, dtype=np.float64).copy()
+    return a.reshape(nb, n) if level == LEVEL_BLOCK else a
+
+
+def psms_filter_step(ctx, field, *, beta0, n_iter=1, n_or=0, n_block=4, n_global=4, beta_block=0.0,
+                     beta_global=0.0, global_level=True, tol=1e-10, inner_prec=PREC_F64, seed=0, step=0):
+    p = FilterParams(float(beta0), int(n_iter), int(n_or), int(n_block), float(beta_block), int(n_global),
+                     float(beta_global), int(bool(global_level)), float(tol), int(inner_prec), int(seed), int(step))
+    r = FilterResult()
+    nb = int(np.prod([d // b for d, b in zip(ctx.dims, ctx.block)]))
+    db = (_D * nb)()
+    ab = (_I * nb)()
+    ctx.check(ctx.lib.psms_filter_step(ctx.handle, field, ctypes.byref(p), ctypes.byref(r), db, ab))
+    return {"n_blocks": r.n_blocks, "n_accept_blocks": r.n_accept_blocks, "accept_global": bool(r.accept_global),
+            "shift": tuple(r.shift), "delta_global": r.delta_global, "delta_block_sum": r.delta_block_sum,
+            "solver_iters": r.solver_iters, "hb_failed": r.hb_failed,
+            "delta_block": np.frombuffer(db, dtype=np.float64).copy(),
+            "accept_block": np.frombuffer(ab, dtype=np.int32).astype(bool)}
+
+
+def psms_profile_enable(ctx, enable):
+    ctx.check(ctx.lib.psms_profile_enable(ctx.handle, int(bool(enable))))
+
+
+def psms_profile_read(ctx):
+    n, ms, by = ctypes.c_longlong(), _D(), _D()
+    ctx.check(ctx.lib.psms_profile_read(ctx.handle, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
+    return n.value, ms.value, by.value

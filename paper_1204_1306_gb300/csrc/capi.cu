@@ -1,0 +1,613 @@
+// C ABI of the library (declared in include/psms.h): context management and
+// the entry points.  Every entry point catches internal errors and returns a
+// psms_status; the message is kept in the context.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "estimator.hpp"
+#include "gauge.hpp"
+#include "solver.hpp"
+
+namespace psms {
+
+void *scratch(psms_ctx *c, const std::string &name, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    DevBuf &b = c->scratch[name];
+    if (b.bytes < bytes) {
+        if (b.p) {
+            cuda_check(cudaStreamSynchronize(c->stream), "scratch sync");
+            cuda_check(cudaFree(b.p), "scratch free");
+            b.p = nullptr;
+            b.bytes = 0;
+        }
+        cuda_check(cudaMalloc(&b.p, bytes), ("scratch alloc " + name).c_str());
+        b.bytes = bytes;
+    }
+    return b.p;
+}
+
+void check_field(psms_ctx *c, int f) {
+    if (f < 0 || f >= c->n_fields) fail(PSMS_EINVAL, "gauge field index out of range");
+}
+
+float2 *links32(psms_ctx *c, int f) {
+    check_field(c, f);
+    if (!c->U32[f]) cuda_check(cudaMalloc(&c->U32[f], sizeof(float2) * 36 * c->g.V), "alloc FP32 links");
+    if (!c->u32_ok[f]) {
+        links_to_f32(c, c->U64[f], c->U32[f], 36 * c->g.V);
+        c->u32_ok[f] = 1;
+    }
+    return c->U32[f];
+}
+
+int prof_begin(psms_ctx *c) {
+    const int slot = (int)c->prof_pending.size();
+    while ((int)c->ev_pool.size() < 2 * (slot + 1)) {
+        cudaEvent_t e;
+        cuda_check(cudaEventCreate(&e), "event create");
+        c->ev_pool.push_back(e);
+    }
+    cuda_check(cudaEventRecord(c->ev_pool[2 * slot], c->stream), "event record");
+    c->prof_pending.push_back({slot, 0.0});
+    return slot;
+}
+
+void prof_end(psms_ctx *c, int slot, double bytes) {
+    cuda_check(cudaEventRecord(c->ev_pool[2 * slot + 1], c->stream), "event record");
+    c->prof_pending[slot].second = bytes;
+}
+
+static void prof_collect(psms_ctx *c) {
+    if (c->prof_pending.empty()) return;
+    cuda_check(cudaStreamSynchronize(c->stream), "prof sync");
+    for (auto &pp : c->prof_pending) {
+        float ms = 0;
+        cuda_check(cudaEventElapsedTime(&ms, c->ev_pool[2 * pp.first], c->ev_pool[2 * pp.first + 1]), "elapsed");
+        c->prof_ms += ms;
+        c->prof_bytes += pp.second;
+        c->prof_launches += 1;
+    }
+    c->prof_pending.clear();
+}
+
+__global__ void unit_links_kernel(double2 *U, long long V) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 36 * V) return;
+    const int e = (int)((t / V) % 9);
+    U[t] = make_double2((e == 0 || e == 4 || e == 8) ? 1.0 : 0.0, 0.0);
+}
+
+static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+static int ilog2(int v) {
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
+static void build_geometry(psms_ctx *c, const psms_lattice_desc *d) {
+    Geom &g = c->g;
+    long long V = 1, Vb = 1;
+    for (int m = 0; m < 4; ++m) {
+        const int L = d->dims[m], l = d->block[m];
+        if (L <= 0 || l < 2 || !pow2(l) || L % l) fail(PSMS_EINVAL, "block extents must be powers of two >= 2 dividing L");
+        g.L[m] = L;
+        g.l[m] = l;
+        g.lsh[m] = ilog2(l);
+        g.nb[m] = L / l;
+        V *= L;
+        Vb *= l;
+    }
+    if (V / 2 > (1LL << 30)) fail(PSMS_EINVAL, "lattice too large");
+    g.V = V;
+    g.Vh = (int)(V / 2);
+    g.Vbh = (int)(Vb / 2);
+    g.vbh_sh = ilog2(g.Vbh);
+    g.lstride[3] = 1;
+    g.lstride[2] = g.l[3];
+    g.lstride[1] = g.l[3] * g.l[2];
+    g.lstride[0] = g.l[3] * g.l[2] * g.l[1];
+    g.bstride[3] = 1;
+    g.bstride[2] = g.nb[3];
+    g.bstride[1] = g.nb[3] * g.nb[2];
+    g.bstride[0] = g.nb[3] * g.nb[2] * g.nb[1];
+    g.nblocks = g.nb[0] * g.nb[1] * g.nb[2] * g.nb[3];
+    g.coloured = (g.nb[0] % 2 == 0 && g.nb[1] % 2 == 0 && g.nb[2] % 2 == 0 && g.nb[3] % 2 == 0) ? 1 : 0;
+    g.nbh = g.coloured ? g.nblocks / 2 : 0;
+    c->h_binfo.assign(g.nblocks, BlockInfo{});
+    for (int b = 0; b < g.nblocks; ++b) {
+        int B[4];
+        int rem = b;
+        for (int m = 3; m >= 0; --m) {
+            B[m] = rem % g.nb[m];
+            rem /= g.nb[m];
+        }
+        const int r = rank_of_lex(g, b, B);
+        BlockInfo bi;
+        for (int m = 0; m < 4; ++m) bi.B[m] = B[m];
+        bi.lex = b;
+        for (int mu = 0; mu < 4; ++mu)
+            for (int sg = 0; sg < 2; ++sg) {
+                int Bn[4] = {B[0], B[1], B[2], B[3]};
+                Bn[mu] = (Bn[mu] + (sg == 0 ? 1 : -1) + g.nb[mu]) % g.nb[mu];
+                const int bn = ((Bn[0] * g.nb[1] + Bn[1]) * g.nb[2] + Bn[2]) * g.nb[3] + Bn[3];
+                bi.nbr[2 * mu + sg] = rank_of_lex(g, bn, Bn);
+            }
+        c->h_binfo[r] = bi;
+    }
+    cuda_check(cudaMalloc(&c->d_binfo, sizeof(BlockInfo) * g.nblocks), "binfo alloc");
+    cuda_check(cudaMemcpy(c->d_binfo, c->h_binfo.data(), sizeof(BlockInfo) * g.nblocks, cudaMemcpyHostToDevice),
+               "binfo copy");
+}
+
+static void free_ctx(psms_ctx *c) {
+    for (auto p : c->U64)
+        if (p) cudaFree(p);
+    for (auto p : c->U32)
+        if (p) cudaFree(p);
+    for (auto &kv : c->scratch)
+        if (kv.second.p) cudaFree(kv.second.p);
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->d_binfo) cudaFree(c->d_binfo);
+    delete c;
+}
+
+static const void *links_for(psms_ctx *c, int f, int prec) {
+    check_field(c, f);
+    return prec == P64 ? (const void *)c->U64[f] : (const void *)links32(c, f);
+}
+
+static size_t elem_size(int prec) {
+    switch (prec) {
+        case P64: return sizeof(double2);
+        case P32: return sizeof(float2);
+        case PB16: return sizeof(__nv_bfloat162);
+    }
+    fail(PSMS_EINVAL, "unknown precision");
+}
+
+static int rank_of_block(psms_ctx *c, int b) {
+    if (b < 0 || b >= c->g.nblocks) fail(PSMS_EINVAL, "block index out of range");
+    int B[4], rem = b;
+    for (int m = 3; m >= 0; --m) {
+        B[m] = rem % c->g.nb[m];
+        rem /= c->g.nb[m];
+    }
+    return rank_of_lex(c->g, b, B);
+}
+
+}  // namespace psms
+
+using namespace psms;
+
+#define PSMS_TRY(ctx)                         \
+    if (!(ctx)) return PSMS_EINVAL;           \
+    try {
+#define PSMS_CATCH(ctx)                       \
+    }                                         \
+    catch (const Error &e) {                  \
+        (ctx)->err = e.msg;                   \
+        return e.st;                          \
+    }                                         \
+    catch (const std::exception &e) {         \
+        (ctx)->err = e.what();                \
+        return PSMS_EINVAL;                   \
+    }                                         \
+    return PSMS_OK;
+
+extern "C" {
+
+psms_status psms_create(const psms_lattice_desc *desc, psms_ctx **out) {
+    if (!desc || !out) return PSMS_EINVAL;
+    *out = nullptr;
+    psms_ctx *c = new psms_ctx();
+    try {
+        if (!(desc->kappa > 0)) fail(PSMS_EINVAL, "kappa must be positive");
+        if (desc->n_fields < 1 || desc->n_fields > 64) fail(PSMS_EINVAL, "n_fields must be in 1..64");
+        build_geometry(c, desc);
+        c->kappa = desc->kappa;
+        c->A = 1.0 / (2.0 * desc->kappa);
+        c->n_fields = desc->n_fields;
+        c->U64.assign(c->n_fields, nullptr);
+        c->U32.assign(c->n_fields, nullptr);
+        c->u32_ok.assign(c->n_fields, 0);
+        const long long n = 36 * c->g.V;
+        for (int f = 0; f < c->n_fields; ++f) {
+            cuda_check(cudaMalloc(&c->U64[f], sizeof(double2) * n), "gauge alloc");
+            unit_links_kernel<<<(unsigned)((n + 255) / 256), 256>>>(c->U64[f], c->g.V);
+            PSMS_LAUNCH_CHECK("unit links");
+        }
+        cuda_check(cudaDeviceSynchronize(), "create sync");
+    } catch (const Error &e) {
+        psms_status st = e.st;
+        free_ctx(c);
+        return st;
+    }
+    *out = c;
+    return PSMS_OK;
+}
+
+psms_status psms_destroy(psms_ctx *ctx) {
+    if (!ctx) return PSMS_EINVAL;
+    cudaStreamSynchronize(ctx->stream);
+    free_ctx(ctx);
+    return PSMS_OK;
+}
+
+const char *psms_last_error(const psms_ctx *ctx) {
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+psms_status psms_set_stream(psms_ctx *ctx, void *stream) {
+    PSMS_TRY(ctx)
+    ctx->stream = (cudaStream_t)stream;
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_geometry_info(const psms_ctx *cctx, long long *n_blocks, long long *dim_P, long long *n_active) {
+    psms_ctx *ctx = const_cast<psms_ctx *>(cctx);
+    PSMS_TRY(ctx)
+    const Geom &g = ctx->g;
+    long long dimP = 0, act = 0;
+    const int lv = g.l[0] * g.l[1] * g.l[2] * g.l[3];
+    for (int ll = 0; ll < lv; ++ll) {
+        int y[4], rem = ll;
+        for (int m = 3; m >= 0; --m) {
+            y[m] = rem % g.l[m];
+            rem /= g.l[m];
+        }
+        int nf = 0;
+        for (int m = 0; m < 4; ++m) nf += (y[m] == 0 || y[m] == g.l[m] - 1) ? 1 : 0;
+        dimP += nf == 0 ? 0 : (nf == 1 ? 6 : 12);
+        for (int mu = 0; mu < 4; ++mu) act += link_active(g, y, mu, 0) ? 1 : 0;
+    }
+    if (n_blocks) *n_blocks = g.nblocks;
+    if (dim_P) *dim_P = g.coloured ? dimP * g.nbh : 0;
+    if (n_active) *n_active = act * g.nblocks;
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_gauge_init(psms_ctx *ctx, int field, double eps, uint64_t seed) {
+    PSMS_TRY(ctx)
+    check_field(ctx, field);
+    link_init(ctx, ctx->U64[field], eps, seed);
+    touch_field(ctx, field);
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_gauge_set(psms_ctx *ctx, int field, const double *links) {
+    PSMS_TRY(ctx)
+    check_field(ctx, field);
+    if (!links) fail(PSMS_EINVAL, "null links");
+    gauge_canonical(ctx, (const double2 *)links, ctx->U64[field], 1);
+    touch_field(ctx, field);
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_gauge_get(psms_ctx *ctx, int field, double *links) {
+    PSMS_TRY(ctx)
+    check_field(ctx, field);
+    if (!links) fail(PSMS_EINVAL, "null links");
+    gauge_canonical(ctx, (const double2 *)links, ctx->U64[field], 0);
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_gauge_copy(psms_ctx *ctx, int dst, int src) {
+    PSMS_TRY(ctx)
+    check_field(ctx, dst);
+    check_field(ctx, src);
+    if (dst != src) {
+        cuda_check(cudaMemcpyAsync(ctx->U64[dst], ctx->U64[src], sizeof(double2) * 36 * ctx->g.V,
+                                   cudaMemcpyDeviceToDevice, ctx->stream),
+                   "gauge copy");
+        touch_field(ctx, dst);
+    }
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_plaquette(psms_ctx *ctx, int field, double *mean_plaq, double *s_w) {
+    PSMS_TRY(ctx)
+    check_field(ctx, field);
+    double *d = (double *)scratch(ctx, "plaq_out", sizeof(double));
+    plaquette_sum(ctx, ctx->U64[field], d);
+    double h = 0;
+    cuda_check(cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "plaq");
+    cuda_check(cudaStreamSynchronize(ctx->stream), "plaq");
+    const double V = (double)ctx->g.V;
+    if (mean_plaq) *mean_plaq = h / (18.0 * V);
+    if (s_w) *s_w = (18.0 * V - h) / 3.0;
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_gauge_sweep(psms_ctx *ctx, int field, int active_set, int n_iter, int n_or, double beta,
+                             uint64_t seed, uint64_t sweep0, int *failed_out) {
+    PSMS_TRY(ctx)
+    check_field(ctx, field);
+    if (n_iter < 0 || n_or < 0) fail(PSMS_EINVAL, "negative sweep count");
+    if (active_set != PSMS_ACTIVE_BLOCKS && active_set != PSMS_ACTIVE_ALL) fail(PSMS_EINVAL, "bad active set");
+    int f = gauge_sweep(ctx, ctx->U64[field], active_set, n_iter, n_or, beta, seed, sweep0);
+    touch_field(ctx, field);
+    if (failed_out) *failed_out = f;
+    if (f) fail(PSMS_EHEATBATH, "an SU(2) heatbath draw hit its attempt limit");
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_gauge_translate(psms_ctx *ctx, int field, const int shift[4]) {
+    PSMS_TRY(ctx)
+    check_field(ctx, field);
+    double2 *tmp = (double2 *)scratch(ctx, "translate_tmp", sizeof(double2) * 36 * ctx->g.V);
+    translate(ctx, ctx->U64[field], tmp, shift);
+    cuda_check(cudaMemcpyAsync(ctx->U64[field], tmp, sizeof(double2) * 36 * ctx->g.V, cudaMemcpyDeviceToDevice,
+                               ctx->stream),
+               "translate copy");
+    touch_field(ctx, field);
+    PSMS_CATCH(ctx)
+}
+
+size_t psms_spinor_bytes(const psms_ctx *ctx, int prec) {
+    if (!ctx) return 0;
+    size_t e = prec == P64 ? sizeof(double2) : (prec == P32 ? sizeof(float2) : sizeof(__nv_bfloat162));
+    return e * 12 * (size_t)ctx->g.V;
+}
+
+psms_status psms_spinor_import(psms_ctx *ctx, const double *canon, void *nat, int prec) {
+    PSMS_TRY(ctx)
+    if (!canon || !nat) fail(PSMS_EINVAL, "null pointer");
+    elem_size(prec);
+    spinor_canonical(ctx, (const double2 *)canon, nat, prec, 1);
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_spinor_export(psms_ctx *ctx, const void *nat, double *canon, int prec) {
+    PSMS_TRY(ctx)
+    if (!canon || !nat) fail(PSMS_EINVAL, "null pointer");
+    elem_size(prec);
+    spinor_canonical(ctx, (const double2 *)canon, (void *)nat, prec, 0);
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_dw_apply(psms_ctx *ctx, int field, int op, const void *in, void *out, int prec) {
+    PSMS_TRY(ctx)
+    if (!in || !out || in == out) fail(PSMS_EINVAL, "in / out must be distinct non-null buffers");
+    const size_t es = elem_size(prec);
+    const long long V = ctx->g.V;
+    HopCall h;
+    h.prec = prec;
+    h.U = links_for(ctx, field, prec);
+    h.in = View<void>{(void *)in, V, 0, 12 * V};
+    h.out = View<void>{out, V, 0, 12 * V};
+    h.y = h.in;
+    h.a = ctx->A;
+    h.b = -0.5;
+    h.p = -1;
+    if (op == PSMS_OP_FULL) {
+        h.mode = HOP_ALL;
+    } else if (op == PSMS_OP_BLOCKS) {
+        h.mode = HOP_INTRA;
+    } else {
+        const int r = rank_of_block(ctx, op);
+        cuda_check(cudaMemsetAsync(out, 0, es * 12 * V, ctx->stream), "dw memset");
+        h.mode = HOP_INTRA;
+        h.rank_lo = r;
+        h.n_ranks = 1;
+    }
+    hop_launch(ctx, h);
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_solve(psms_ctx *ctx, int field, int op, const void *b, void *x, double tol, int maxit,
+                       int inner_prec, psms_solve_info *info) {
+    PSMS_TRY(ctx)
+    check_field(ctx, field);
+    if (!b || !x || b == x) fail(PSMS_EINVAL, "b / x must be distinct non-null buffers");
+    if (!(tol > 0) || maxit < 1) fail(PSMS_EINVAL, "tol must be > 0 and maxit >= 1");
+    elem_size(inner_prec);
+    const long long V = ctx->g.V;
+    const float2 *U32 = inner_prec == P64 ? nullptr : links32(ctx, field);
+    if (op == PSMS_OP_FULL) {
+        FullSolveReq q;
+        q.b = View<double2>{(double2 *)b, V, 0, 12 * V};
+        q.x = View<double2>{(double2 *)x, V, 0, 12 * V};
+        q.U64 = ctx->U64[field];
+        q.U32 = U32;
+        q.tol = tol;
+        q.maxit = maxit;
+        q.inner_prec = inner_prec;
+        solve_full_batch(ctx, q, info);
+    } else {
+        if (inner_prec == PB16) fail(PSMS_EINVAL, "block solves support FP64 and FP32 inner iterations");
+        int lo = 0, nr = ctx->g.nblocks;
+        if (op != PSMS_OP_BLOCKS) {
+            lo = rank_of_block(ctx, op);
+            nr = 1;
+        }
+        cuda_check(cudaMemsetAsync(x, 0, sizeof(double2) * 12 * V, ctx->stream), "solve memset");
+        int *iters = (int *)scratch(ctx, "api_iters", sizeof(int) * nr);
+        double *resid = (double *)scratch(ctx, "api_resid", sizeof(double) * nr);
+        int *status = (int *)scratch(ctx, "api_status", sizeof(int) * nr);
+        BlockSolveReq q;
+        q.rank_lo = lo;
+        q.n_ranks = nr;
+        q.n_sys = 1;
+        q.b = View<double2>{(double2 *)b, V, 0, 12 * V};
+        q.x = View<double2>{(double2 *)x, V, 0, 12 * V};
+        q.U64 = ctx->U64[field];
+        q.U32 = U32;
+        q.tol = tol;
+        q.maxit = maxit;
+        q.inner_prec = inner_prec;
+        q.iters = iters;
+        q.resid = resid;
+        q.status = status;
+        block_solve(ctx, q);
+        std::vector<int> hi(nr), hs(nr);
+        std::vector<double> hr(nr);
+        cuda_check(cudaMemcpyAsync(hi.data(), iters, sizeof(int) * nr, cudaMemcpyDeviceToHost, ctx->stream), "it");
+        cuda_check(cudaMemcpyAsync(hr.data(), resid, sizeof(double) * nr, cudaMemcpyDeviceToHost, ctx->stream), "res");
+        cuda_check(cudaMemcpyAsync(hs.data(), status, sizeof(int) * nr, cudaMemcpyDeviceToHost, ctx->stream), "st");
+        cuda_check(cudaStreamSynchronize(ctx->stream), "solve sync");
+        long long tot = 0;
+        double worst = 0;
+        int bad = 0;
+        for (int i = 0; i < nr; ++i) {
+            tot += hi[i];
+            worst = std::max(worst, hr[i]);
+            bad |= hs[i];
+        }
+        if (info) {
+            info->outer_iters = 0;
+            info->inner_iters = tot;
+            info->true_residual = worst;
+            info->n_systems = nr;
+        }
+        if (bad) fail(PSMS_ENOCONV, "a block solve missed its tolerance");
+    }
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_logdet_ratio(psms_ctx *ctx, int level, int field_old, int field_new, int n, int mode,
+                              uint64_t seed, uint64_t counter, double tol, int inner_prec, double *delta_out) {
+    PSMS_TRY(ctx)
+    check_field(ctx, field_old);
+    check_field(ctx, field_new);
+    if (n < 1 || !delta_out) fail(PSMS_EINVAL, "n >= 1 and delta_out required");
+    if (mode != PSMS_EST_INTERP && mode != PSMS_EST_INDEPENDENT) fail(PSMS_EINVAL, "bad estimator mode");
+    if (inner_prec != P64 && inner_prec != P32) fail(PSMS_EINVAL, "estimators use FP64 or FP32 inner iterations");
+    const int nb = ctx->g.nblocks;
+    if (level == PSMS_LEVEL_BLOCK) {
+        double *d = (double *)scratch(ctx, "ld_delta", sizeof(double) * nb * n);
+        block_level(ctx, ctx->U64[field_old], ctx->U64[field_new], n, mode, seed, counter, tol, inner_prec, d);
+        cuda_check(cudaMemcpyAsync(delta_out, d, sizeof(double) * nb * n, cudaMemcpyDeviceToHost, ctx->stream), "out");
+    } else if (level == PSMS_LEVEL_GLOBAL) {
+        double *d = (double *)scratch(ctx, "ld_delta", sizeof(double) * n);
+        global_level(ctx, ctx->U64[field_old], ctx->U64[field_new], n, mode, seed, counter, tol, inner_prec, d);
+        cuda_check(cudaMemcpyAsync(delta_out, d, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream), "out");
+    } else {
+        fail(PSMS_EINVAL, "level must be PSMS_LEVEL_BLOCK or PSMS_LEVEL_GLOBAL");
+    }
+    cuda_check(cudaStreamSynchronize(ctx->stream), "logdet sync");
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params *prm, psms_filter_result *res,
+                             double *delta_block_out, int *accept_block_out) {
+    PSMS_TRY(ctx)
+    check_field(ctx, field);
+    if (!prm) fail(PSMS_EINVAL, "null parameters");
+    if (prm->n_block < 1 || prm->n_global < 1) fail(PSMS_EINVAL, "n_block, n_global >= 1");
+    if (prm->inner_prec != P64 && prm->inner_prec != P32) fail(PSMS_EINVAL, "inner precision FP64 or FP32");
+    const Geom &g = ctx->g;
+    const long long nel = 36 * g.V;
+    const size_t fb = sizeof(double2) * nel;
+    double2 *cur = ctx->U64[field];
+    double2 *old = (double2 *)scratch(ctx, "fs_old", fb);
+    double2 *prop = (double2 *)scratch(ctx, "fs_prop", fb);
+    double2 *mid = (double2 *)scratch(ctx, "fs_mid", fb);
+    cuda_check(cudaMemcpyAsync(old, cur, fb, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
+    cuda_check(cudaMemcpyAsync(prop, cur, fb, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
+    // level 0: proposal
+    const int failed = gauge_sweep(ctx, prop, PSMS_ACTIVE_BLOCKS, prm->n_iter, prm->n_or, prm->beta0, prm->seed,
+                                   prm->step << 20);
+    if (failed) fail(PSMS_EHEATBATH, "an SU(2) heatbath draw hit its attempt limit");
+    // level 1: block det ratios
+    const int nb = g.nblocks, N1 = prm->n_block;
+    double *d_db = (double *)scratch(ctx, "fs_dblk", sizeof(double) * nb * N1);
+    long long iters = block_level(ctx, old, prop, N1, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol,
+                                  prm->inner_prec, d_db);
+    bool per_block = true;
+    for (int m = 0; m < 4; ++m) per_block &= g.l[m] >= 3;
+    double *d_dsum = (double *)scratch(ctx, "fs_dsum", sizeof(double) * (nb + 1));
+    int *d_acc = (int *)scratch(ctx, "fs_acc", sizeof(int) * nb);
+    if (prm->beta_block != 0.0) fail(PSMS_EINVAL, "beta_block != 0 is not supported");
+    decide(ctx, d_db, nb, N1, per_block ? 1 : 0, prm->seed, prm->step, PSMS_LEVEL_BLOCK, 0.0, nullptr, 0.0, d_dsum,
+           d_acc);
+    merge_blocks(ctx, old, prop, mid, d_acc);
+    std::vector<double> hd(nb + 1);
+    std::vector<int> ha(nb);
+    cuda_check(cudaMemcpyAsync(hd.data(), d_dsum, sizeof(double) * (nb + 1), cudaMemcpyDeviceToHost, ctx->stream), "d");
+    cuda_check(cudaMemcpyAsync(ha.data(), d_acc, sizeof(int) * nb, cudaMemcpyDeviceToHost, ctx->stream), "a");
+    cuda_check(cudaStreamSynchronize(ctx->stream), "filter sync");
+    int nacc = 0;
+    double dsum = 0;
+    for (int b = 0; b < nb; ++b) {
+        nacc += ha[b];
+        dsum += hd[b];
+    }
+    // level 2: global Schur det ratio
+    double dglob = 0;
+    int accg = 1;
+    double2 *fin = mid;
+    if (prm->global_level) {
+        const int N2 = prm->n_global;
+        double *d_dg = (double *)scratch(ctx, "fs_dg", sizeof(double) * N2);
+        iters += global_level(ctx, old, mid, N2, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol, prm->inner_prec,
+                              d_dg);
+        std::vector<double> hg(N2);
+        cuda_check(cudaMemcpyAsync(hg.data(), d_dg, sizeof(double) * N2, cudaMemcpyDeviceToHost, ctx->stream), "dg");
+        cuda_check(cudaStreamSynchronize(ctx->stream), "dg");
+        for (int i = 0; i < N2; ++i) dglob += hg[i];
+        if (prm->beta_global != 0.0) {
+            double *pd = (double *)scratch(ctx, "fs_plaq", sizeof(double) * 2);
+            plaquette_sum(ctx, mid, pd);
+            plaquette_sum(ctx, old, pd + 1);
+            double hp[2];
+            cuda_check(cudaMemcpyAsync(hp, pd, sizeof(hp), cudaMemcpyDeviceToHost, ctx->stream), "plaq");
+            cuda_check(cudaStreamSynchronize(ctx->stream), "plaq");
+            dglob += prm->beta_global * (-(hp[0] - hp[1]) / 3.0);
+        }
+        if (!std::isfinite(dglob)) fail(PSMS_ESPECTRUM, "non-finite global estimate");
+        const double u = uniforms(prm->seed, TAG_ACCEPT, prm->step, PSMS_LEVEL_GLOBAL, 0, 0).u[0];
+        accg = (dglob <= 0.0 || u < std::exp(-dglob)) ? 1 : 0;
+        if (!accg) fin = old;
+    }
+    // random translation
+    int sh[4];
+    {
+        uni4 u = uniforms(prm->seed, TAG_SHIFT, prm->step, 0, 0, 0);
+        for (int m = 0; m < 4; ++m) {
+            int v = (int)std::floor(u.u[m] * g.L[m]);
+            sh[m] = v > g.L[m] - 1 ? g.L[m] - 1 : v;
+        }
+    }
+    translate(ctx, fin, cur, sh);
+    touch_field(ctx, field);
+    cuda_check(cudaStreamSynchronize(ctx->stream), "filter end");
+    if (res) {
+        res->n_blocks = nb;
+        res->n_accept_blocks = nacc;
+        res->accept_global = accg;
+        for (int m = 0; m < 4; ++m) res->shift[m] = sh[m];
+        res->delta_global = dglob;
+        res->delta_block_sum = per_block ? dsum : hd[nb];
+        res->solver_iters = iters;
+        res->hb_failed = failed;
+    }
+    if (delta_block_out)
+        for (int b = 0; b < nb; ++b) delta_block_out[b] = hd[b];
+    if (accept_block_out)
+        for (int b = 0; b < nb; ++b) accept_block_out[b] = ha[b];
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_profile_enable(psms_ctx *ctx, int enable) {
+    PSMS_TRY(ctx)
+    prof_collect(ctx);
+    ctx->prof = enable != 0;
+    ctx->prof_launches = 0;
+    ctx->prof_ms = 0;
+    ctx->prof_bytes = 0;
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_profile_read(psms_ctx *ctx, long long *launches, double *total_ms, double *bytes) {
+    PSMS_TRY(ctx)
+    prof_collect(ctx);
+    if (launches) *launches = ctx->prof_launches;
+    if (total_ms) *total_ms = ctx->prof_ms;
+    if (bytes) *bytes = ctx->prof_bytes;
+    PSMS_CATCH(ctx)
+}
+
+}  // extern "C"

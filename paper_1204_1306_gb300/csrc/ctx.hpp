@@ -1,0 +1,73 @@
+// Host-side context of the library: geometry, gauge-field slots, scratch
+// buffers, stream and error state.  Shared by the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/psms.h"
+#include "common.cuh"
+
+namespace psms {
+
+struct Error {
+    psms_status st;
+    std::string msg;
+};
+
+[[noreturn]] inline void fail(psms_status st, const std::string &m) { throw Error{st, m}; }
+
+inline void cuda_check(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) {
+        psms_status st = (e == cudaErrorMemoryAllocation) ? PSMS_ENOMEM : PSMS_ECUDA;
+        fail(st, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+}
+
+#define PSMS_LAUNCH_CHECK(what) ::psms::cuda_check(cudaGetLastError(), what)
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace psms
+
+struct psms_ctx {
+    psms::Geom g;
+    double kappa = 0;
+    double A = 0;  // 4 + m0 = 1 / (2 kappa)
+    int n_fields = 0;
+    std::vector<double2 *> U64;   // FP64 links per slot, [mu][e][s]
+    std::vector<float2 *> U32;    // FP32 copies, valid when u32_ok
+    std::vector<int> u32_ok;
+    std::vector<psms::BlockInfo> h_binfo;
+    psms::BlockInfo *d_binfo = nullptr;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    std::map<std::string, psms::DevBuf> scratch;
+    // profiling of Wilson-operator launches
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, double>> prof_pending;  // (event pair index, bytes)
+    long long prof_launches = 0;
+    double prof_ms = 0, prof_bytes = 0;
+};
+
+namespace psms {
+
+// grow-only named scratch buffer
+void *scratch(psms_ctx *c, const std::string &name, size_t bytes);
+// FP32 copy of a gauge slot (converted on first use after a change)
+float2 *links32(psms_ctx *c, int field);
+inline void touch_field(psms_ctx *c, int f) { c->u32_ok[f] = 0; }
+void check_field(psms_ctx *c, int f);
+
+// profiling hooks around Wilson-operator launches
+int prof_begin(psms_ctx *c);
+void prof_end(psms_ctx *c, int slot, double bytes);
+
+}  // namespace psms

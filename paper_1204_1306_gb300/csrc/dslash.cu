@@ -1,0 +1,260 @@
+// Wilson-Dirac hopping kernel, Eq. (Dw):
+//   H(psi)(x) = sum_mu { U(x,mu)(1 - s gamma_mu) psi(x+mu)
+//                      + U(x-mu,mu)^dagger (1 + s gamma_mu) psi(x-mu) },
+// s = +1 for D and -1 for D^dagger, antiperiodic in time.  D = A - H/2 with
+// A = 4 + m0.  One thread per output site; spin projection to half spinors
+// (rank-2 projectors), SU(3) x half-spinor, reconstruction.  Fields use the
+// structure-of-arrays even-odd block-major layout, so a warp reads each
+// component of 32 consecutive sites in one coalesced transaction.
+#include "kernels.hpp"
+
+namespace psms {
+
+template <class E>
+struct HopArgs {
+    Geom g;
+    const BlockInfo *binfo;
+    View<E> in, out, y, y2;
+    double a, a2, b;
+    const void *U;
+    long long U_bs;
+    int p, rank_lo, n_ranks, mode, dag;
+    const int *active;
+    double *partial;
+};
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NT / 32; ++i) t += sh[i];
+    }
+    return t;  // valid in thread 0
+}
+
+template <class S, class SL, int NT>
+__global__ void __launch_bounds__(NT) hop_kernel(const HopArgs<typename S::elem> a) {
+    using R = typename SL::R;
+    using E = typename S::elem;
+    using EL = typename SL::elem;
+    __shared__ double sh[NT / 32];
+    const int k = blockIdx.y;
+    if (a.active && !a.active[k]) {
+        if (a.partial && threadIdx.x == 0) a.partial[(long long)k * gridDim.x + blockIdx.x] = 0.0;
+        return;
+    }
+    const Geom &g = a.g;
+    const long long per_p = (long long)a.n_ranks * g.Vbh;
+    const long long total = (a.p < 0 ? 2 : 1) * per_p;
+    const long long t = (long long)blockIdx.x * NT + threadIdx.x;
+    double nrm = 0.0;
+    if (t < total) {
+        const int p = a.p < 0 ? (int)(t >= per_p) : a.p;
+        const long long tt = a.p < 0 ? t - p * per_p : t;
+        const int r = a.rank_lo + (int)(tt >> g.vbh_sh);
+        const int j = (int)(tt & (g.Vbh - 1));
+        int y[4];
+        const int ll = local_lex(g, p, j, y);
+        const BlockInfo &bi = a.binfo[r];
+        const long long s = (long long)p * g.Vh + (long long)r * g.Vbh + j;
+        const E *in = a.in.p + k * a.in.bs;
+        const EL *U = (const EL *)a.U + k * a.U_bs;
+        const R sg = a.dag ? R(-1) : R(1);
+        Spinor<R> acc;
+        zero(acc);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            long long sn;
+            int bs;
+            if (neighbour(g, bi, r, p, y, ll, mu, +1, a.mode, sn, bs)) {
+                Spinor<R> v = load_spinor_ro<S>(in, a.in.cs, sn - a.in.off);
+                const R tf = -sg;
+                Half<R> h = project(mu, tf, v);
+                if (bs < 0) {
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) h.c[q][c] = R(-1) * h.c[q][c];
+                }
+                SU3<R> u = load_link<SL>(U, g.V, mu, s);
+                reconstruct_add(mu, tf, su3_mul(u, h), acc);
+            }
+            if (neighbour(g, bi, r, p, y, ll, mu, -1, a.mode, sn, bs)) {
+                Spinor<R> v = load_spinor_ro<S>(in, a.in.cs, sn - a.in.off);
+                const R tb = sg;
+                Half<R> h = project(mu, tb, v);
+                if (bs < 0) {
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) h.c[q][c] = R(-1) * h.c[q][c];
+                }
+                SU3<R> u = load_link<SL>(U, g.V, mu, sn);
+                reconstruct_add(mu, tb, su3_dag_mul(u, h), acc);
+            }
+        }
+        const R cb = (R)a.b;
+        Spinor<R> o;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o.c[q][c] = cb * acc.c[q][c];
+        if (a.y.p) {
+            const R ca = (R)a.a;
+            Spinor<R> v = load_spinor<S>(a.y.p + k * a.y.bs, a.y.cs, s - a.y.off);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) o.c[q][c] = o.c[q][c] + ca * v.c[q][c];
+        }
+        if (a.y2.p) {
+            const R ca = (R)a.a2;
+            Spinor<R> v = load_spinor<S>(a.y2.p + k * a.y2.bs, a.y2.cs, s - a.y2.off);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) o.c[q][c] = o.c[q][c] + ca * v.c[q][c];
+        }
+        store_spinor<S>(a.out.p + k * a.out.bs, a.out.cs, s - a.out.off, o);
+        if (a.partial) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) nrm += (double)norm2(o.c[q][c]);
+        }
+    }
+    if (a.partial) {
+        double tot = block_sum<NT>(nrm, sh);
+        if (threadIdx.x == 0) a.partial[(long long)k * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
+static constexpr int HOP_NT = 128;
+
+int hop_ctas(psms_ctx *c, const HopCall &h) {
+    const int nr = h.n_ranks < 0 ? c->g.nblocks : h.n_ranks;
+    const long long total = (h.p < 0 ? 2LL : 1LL) * nr * c->g.Vbh;
+    return (int)((total + HOP_NT - 1) / HOP_NT);
+}
+
+template <class S, class SL>
+static int hop_launch_t(psms_ctx *c, const HopCall &h) {
+    using E = typename S::elem;
+    HopArgs<E> a;
+    a.g = c->g;
+    a.binfo = c->d_binfo;
+    auto cv = [](const View<void> &v) {
+        View<E> w;
+        w.p = (E *)v.p;
+        w.cs = v.cs;
+        w.off = v.off;
+        w.bs = v.bs;
+        return w;
+    };
+    a.in = cv(h.in);
+    a.out = cv(h.out);
+    a.y = cv(h.y);
+    a.y2 = cv(h.y2);
+    a.a = h.a;
+    a.a2 = h.a2;
+    a.b = h.b;
+    a.U = h.U;
+    a.U_bs = h.U_bs;
+    a.p = h.p;
+    a.rank_lo = h.rank_lo;
+    a.n_ranks = h.n_ranks < 0 ? c->g.nblocks : h.n_ranks;
+    a.mode = h.mode;
+    a.dag = h.dag;
+    a.active = h.active;
+    a.partial = h.partial;
+    const int nct = hop_ctas(c, h);
+    if (nct == 0 || h.n_sys == 0) return 0;
+    dim3 grid(nct, h.n_sys);
+    double bytes = 0;
+    int slot = -1;
+    if (c->prof) {
+        // algorithmic bytes: in + out (+ y, y2) spinors and 4 links per output site
+        const long long sites = (h.p < 0 ? 2LL : 1LL) * a.n_ranks * c->g.Vbh;
+        const double sp = 12.0 * sizeof(E), lk = 9.0 * sizeof(typename SL::elem);
+        bytes = (double)h.n_sys * sites * (2 * sp + (h.y.p ? sp : 0) + (h.y2.p ? sp : 0) + 4 * lk * (h.p < 0 ? 1 : 2));
+        slot = prof_begin(c);
+    }
+    hop_kernel<S, SL, HOP_NT><<<grid, HOP_NT, 0, c->stream>>>(a);
+    PSMS_LAUNCH_CHECK("hop_kernel");
+    if (slot >= 0) prof_end(c, slot, bytes);
+    return nct;
+}
+
+int hop_launch(psms_ctx *c, const HopCall &h) {
+    switch (h.prec) {
+        case P64: return hop_launch_t<Store<double>, Store<double>>(c, h);
+        case P32: return hop_launch_t<Store<float>, Store<float>>(c, h);
+        case PB16: return hop_launch_t<Store<__nv_bfloat16>, Store<float>>(c, h);
+    }
+    fail(PSMS_EINVAL, "hop_launch: bad precision");
+}
+
+// --- deterministic reductions ------------------------------------------------
+
+template <int NT>
+__global__ void __launch_bounds__(NT) reduce_partials_kernel(const double *partial, int n, double *out) {
+    __shared__ double sh[NT / 32];
+    const int k = blockIdx.x;
+    double v = 0;
+    for (int i = threadIdx.x; i < n; i += NT) v += partial[(long long)k * n + i];
+    double t = block_sum<NT>(v, sh);
+    if (threadIdx.x == 0) out[k] = t;
+}
+
+void reduce_partials(psms_ctx *c, const double *partial, int n, int n_sys, double *out) {
+    reduce_partials_kernel<256><<<n_sys, 256, 0, c->stream>>>(partial, n, out);
+    PSMS_LAUNCH_CHECK("reduce_partials");
+}
+
+template <class S, int NT>
+__global__ void __launch_bounds__(NT) norm2_kernel(View<typename S::elem> v, long long s_lo, long long n,
+                                                   double *partial) {
+    __shared__ double sh[NT / 32];
+    const int k = blockIdx.y;
+    double acc = 0;
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
+        const long long s = s_lo + i;
+        for (int q = 0; q < 12; ++q) acc += (double)norm2(S::ld(v.p + k * v.bs, q * v.cs + s - v.off));
+    }
+    double t = block_sum<NT>(acc, sh);
+    if (threadIdx.x == 0) partial[(long long)k * gridDim.x + blockIdx.x] = t;
+}
+
+void norm2_batch(psms_ctx *c, int prec, View<void> v, long long s_lo, long long n, int n_sys, double *out) {
+    const int NT = 256;
+    int nct = (int)std::min<long long>((n + NT - 1) / NT, 1024);
+    if (nct < 1) nct = 1;
+    double *partial = (double *)scratch(c, "norm2_partial", sizeof(double) * (size_t)nct * n_sys);
+    dim3 grid(nct, n_sys);
+    switch (prec) {
+        case P64: {
+            View<double2> w{(double2 *)v.p, v.cs, v.off, v.bs};
+            norm2_kernel<Store<double>, NT><<<grid, NT, 0, c->stream>>>(w, s_lo, n, partial);
+            break;
+        }
+        case P32: {
+            View<float2> w{(float2 *)v.p, v.cs, v.off, v.bs};
+            norm2_kernel<Store<float>, NT><<<grid, NT, 0, c->stream>>>(w, s_lo, n, partial);
+            break;
+        }
+        default: {
+            View<__nv_bfloat162> w{(__nv_bfloat162 *)v.p, v.cs, v.off, v.bs};
+            norm2_kernel<Store<__nv_bfloat16>, NT><<<grid, NT, 0, c->stream>>>(w, s_lo, n, partial);
+            break;
+        }
+    }
+    PSMS_LAUNCH_CHECK("norm2_kernel");
+    reduce_partials(c, partial, nct, n_sys, out);
+}
+
+}  // namespace psms

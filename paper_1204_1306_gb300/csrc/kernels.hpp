@@ -1,0 +1,44 @@
+// Kernel launch interfaces shared between the translation units.
+#pragma once
+
+#include "ctx.hpp"
+
+namespace psms {
+
+// A batch of fields in the structure-of-arrays layout: system k, component c,
+// internal site s live at p[k * bs + c * cs + (s - off)].  Full-lattice
+// fields have cs = V, off = 0; single-parity fields cs = V/2, off = parity*V/2.
+template <class E>
+struct View {
+    E *p = nullptr;
+    long long cs = 0, off = 0, bs = 0;
+};
+
+enum Prec : int { P64 = PSMS_PREC_F64, P32 = PSMS_PREC_F32, PB16 = PSMS_PREC_BF16 };
+
+// out = a*y + a2*y2 + b*H(in), H the hopping term of Eq. (Dw) (sum over the
+// 8 neighbours of U (1 -/+ gamma) psi), restricted by `mode`, for output
+// parity p (-1: both) on the blocks of rank [rank_lo, rank_lo + n_ranks).
+// Batched over gridDim.y = n_sys systems with per-system strides.  Optional
+// per-CTA partial sums of |out|^2 in partial[k * n_cta + cta].
+struct HopCall {
+    int prec = P64;  // storage of in/out/y/y2 (links: FP64 for P64, FP32 otherwise)
+    View<void> in, out, y, y2;
+    double a = 0, a2 = 0, b = 1;
+    const void *U = nullptr;
+    long long U_bs = 0;
+    int p = -1, rank_lo = 0, n_ranks = -1, mode = HOP_ALL, dag = 0, n_sys = 1;
+    const int *active = nullptr;
+    double *partial = nullptr;
+};
+// returns the number of CTAs per system (for the partial sums)
+int hop_launch(psms_ctx *c, const HopCall &h);
+int hop_ctas(psms_ctx *c, const HopCall &h);
+
+// deterministic reductions: sums partial[k * n + i] over i -> out[k]
+void reduce_partials(psms_ctx *c, const double *partial, int n, int n_sys, double *out);
+// sum_{c,s} |v|^2 per system over internal sites [s_lo, s_lo + n) (one parity
+// range or a whole field), FP64 result out[k]
+void norm2_batch(psms_ctx *c, int prec, View<void> v, long long s_lo, long long n, int n_sys, double *out);
+
+}  // namespace psms

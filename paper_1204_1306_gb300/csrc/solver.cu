@@ -1,0 +1,850 @@
+// Krylov solves of the Wilson-Dirac operator, Eq. (Dw), on the whole lattice
+// and on Dirichlet blocks (Sec. 3).  The paper leaves the solver open
+// ("inversions", Sec. 5); we use CG on the normal equations of the even-odd
+// Schur complement
+//     Dhat = A - D_oe D_eo / A = A - H_o H_e / (4A)     (odd sites),
+//     Dhat^dagger = A - H^dag_o H^dag_e / (4A),
+// inside an FP64 defect-correction loop on the true residual b - D x, with
+// the inner iterations in FP64 or FP32.
+//
+//  * block_solve_kernel: one CTA per (block, system); the whole solve,
+//    including the FP64 outer loop and convergence decisions, runs on the
+//    device with CTA-wide deterministic reductions.
+//  * solve_full_batch: whole-lattice solves of n_sys systems (each with its
+//    own gauge field) batched into every launch; per-system scalars live on
+//    the device; the host only polls convergence flags every few iterations.
+#include "kernels.hpp"
+#include "solver.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace psms {
+
+// ---------------------------------------------------------------------------
+// CTA-level helpers for the block solver
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ double cta_sum(double v, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int i = 0; i < NT / 32; ++i) t += sh[i];
+        sh[NT / 32] = t;
+    }
+    __syncthreads();
+    return sh[NT / 32];
+}
+
+// out_p = a*y_p + b*H^intra_p(in) on the block of rank r; returns this
+// thread's contribution to |out|^2.  Vectors are views (structure of arrays).
+template <class S, class SL, class SY>
+__device__ __forceinline__ double block_hop(const Geom &g, const BlockInfo &bi, int r, int p, int dag,
+                                            const typename S::elem *in, long long in_cs, long long in_off,
+                                            typename S::elem *out, long long out_cs, long long out_off,
+                                            const typename SY::elem *y, long long y_cs, long long y_off, double a,
+                                            double b, const typename SL::elem *U) {
+    using R = typename SL::R;
+    double nrm = 0;
+    const R sg = dag ? R(-1) : R(1);
+    for (int j = threadIdx.x; j < g.Vbh; j += blockDim.x) {
+        int yy[4];
+        const int ll = local_lex(g, p, j, yy);
+        const long long s = (long long)p * g.Vh + (long long)r * g.Vbh + j;
+        Spinor<R> acc;
+        zero(acc);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            long long sn;
+            int bs;
+            if (neighbour(g, bi, r, p, yy, ll, mu, +1, HOP_INTRA, sn, bs)) {
+                Spinor<R> v = load_spinor<S>(in, in_cs, sn - in_off);
+                const R tf = -sg;
+                Half<R> h = project(mu, tf, v);
+                SU3<R> u = load_link<SL>(U, g.V, mu, s);
+                reconstruct_add(mu, tf, su3_mul(u, h), acc);
+            }
+            if (neighbour(g, bi, r, p, yy, ll, mu, -1, HOP_INTRA, sn, bs)) {
+                Spinor<R> v = load_spinor<S>(in, in_cs, sn - in_off);
+                const R tb = sg;
+                Half<R> h = project(mu, tb, v);
+                SU3<R> u = load_link<SL>(U, g.V, mu, sn);
+                reconstruct_add(mu, tb, su3_dag_mul(u, h), acc);
+            }
+        }
+        Spinor<R> o;
+        const R cb = (R)b, ca = (R)a;
+        if (y) {
+            Spinor<typename SY::R> v = load_spinor<SY>(y, y_cs, s - y_off);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    o.c[q][c] = cb * acc.c[q][c] + ca * mk<R>((R)v.c[q][c].re, (R)v.c[q][c].im);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) o.c[q][c] = cb * acc.c[q][c];
+        }
+        store_spinor<S>(out, out_cs, s - out_off, o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) nrm += (double)norm2(o.c[q][c]);
+    }
+    return nrm;
+}
+
+template <class E>
+struct BlockVecs {
+    // inner-precision vectors of one system (views with the system offset applied)
+    E *rhs, *e;             // full layout (cs = V, off = 0)
+    E *bhat, *rho, *res, *pp, *q, *sv;  // odd halves (cs = Vh, off = Vh)
+    E *t;                   // even half (cs = Vh, off = 0)
+};
+
+struct BlockSolveArgs {
+    Geom g;
+    const BlockInfo *binfo;
+    double A;
+    int rank_lo, n_ranks;
+    View<double2> b, x;              // FP64 rhs / solution (full layout)
+    View<double2> r64;               // FP64 residual scratch (full layout)
+    const double2 *U64;
+    long long U64_bs;
+    const void *Uin;
+    long long Uin_bs;
+    void *vin;                       // inner scratch base
+    long long vin_bs;                // per-system stride of the inner scratch (elements)
+    double tol, delta;
+    int maxit, max_outer;
+    const int *sys_active;           // per system (nullable)
+    int *iters;                      // [k * n_ranks + r]
+    double *resid;                   // [k * n_ranks + r]
+    double *xnorm2;                  // [k * n_ranks + r] |x_block|^2 (nullable)
+    int *status;                     // [k * n_ranks + r]
+};
+
+template <class SV, class SL, int NT>
+__global__ void __launch_bounds__(NT) block_solve_kernel(const BlockSolveArgs a) {
+    using E = typename SV::elem;
+    using R = typename SL::R;
+    using S64 = Store<double>;
+    __shared__ double sh[NT / 32 + 1];
+    const Geom &g = a.g;
+    const int rl = blockIdx.x;
+    const int r = a.rank_lo + rl;
+    const int k = blockIdx.y;
+    const long long out_i = (long long)k * a.n_ranks + rl;
+    if (a.sys_active && !a.sys_active[k]) {
+        if (threadIdx.x == 0) {
+            a.iters[out_i] = 0;
+            a.status[out_i] = 0;
+        }
+        return;
+    }
+    const BlockInfo &bi = a.binfo[r];
+    const long long V = g.V, Vh = g.Vh;
+    const double2 *b = a.b.p + k * a.b.bs;
+    double2 *x = a.x.p + k * a.x.bs;
+    double2 *r64 = a.r64.p + k * a.r64.bs;
+    const double2 *U64 = a.U64 + k * a.U64_bs;
+    const typename SL::elem *Uin = (const typename SL::elem *)a.Uin + k * a.Uin_bs;
+    E *base = (E *)a.vin + k * a.vin_bs;
+    // inner scratch layout per system: rhs (V), e (V), 6 odd halves, 1 even half
+    BlockVecs<E> v;
+    v.rhs = base;
+    v.e = base + 12 * V;
+    v.bhat = base + 24 * V;
+    v.rho = v.bhat + 12 * Vh;
+    v.res = v.rho + 12 * Vh;
+    v.pp = v.res + 12 * Vh;
+    v.q = v.pp + 12 * Vh;
+    v.sv = v.q + 12 * Vh;
+    v.t = v.sv + 12 * Vh;
+    const long long blo[2] = {(long long)r * g.Vbh, Vh + (long long)r * g.Vbh};  // block start per parity
+    const double A = a.A;
+    const double c4 = -1.0 / (4.0 * A);
+
+    // x = 0, |b|^2
+    double bn = 0;
+    for (int p = 0; p < 2; ++p)
+        for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+            const long long s = blo[p] + j;
+            for (int q = 0; q < 12; ++q) {
+                x[q * a.x.cs + s - a.x.off] = make_double2(0, 0);
+                bn += (double)norm2(S64::ld(b, q * a.b.cs + s - a.b.off));
+            }
+        }
+    bn = cta_sum<NT>(bn, sh);
+    int total_it = 0, st = 0;
+    double rel = 0;
+    if (bn == 0.0) {
+        if (threadIdx.x == 0) {
+            a.iters[out_i] = 0;
+            a.resid[out_i] = 0;
+            a.status[out_i] = 0;
+            if (a.xnorm2) a.xnorm2[out_i] = 0;
+        }
+        return;
+    }
+    for (int outer = 0;; ++outer) {
+        // FP64 true residual r64 = b - D_b x  (both parities)
+        // r64_p = b_p + H_p(x_{1-p})/2, then subtract A x_p
+        double rn = 0;
+        __syncthreads();
+        for (int p = 0; p < 2; ++p) {
+            block_hop<S64, S64, S64>(g, bi, r, p, 0, x, a.x.cs, a.x.off, r64, a.r64.cs, a.r64.off, b, a.b.cs,
+                                     a.b.off, 1.0, 0.5, U64);
+        }
+        __syncthreads();
+        for (int p = 0; p < 2; ++p)
+            for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+                const long long s = blo[p] + j;
+                for (int q = 0; q < 12; ++q) {
+                    cpx<double> rv = S64::ld(r64, q * a.r64.cs + s - a.r64.off);
+                    cpx<double> xv = S64::ld(x, q * a.x.cs + s - a.x.off);
+                    rv = rv - A * xv;
+                    S64::st(r64, q * a.r64.cs + s - a.r64.off, rv);
+                    rn += norm2(rv);
+                }
+            }
+        rn = cta_sum<NT>(rn, sh);
+        rel = sqrt(rn / bn);
+        if (rel <= a.tol) break;
+        if (outer >= a.max_outer || total_it >= a.maxit) {
+            st = 1;
+            break;
+        }
+        // inner rhs = r64 / |r64| in inner precision
+        const double scale = 1.0 / sqrt(rn);
+        for (int p = 0; p < 2; ++p)
+            for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+                const long long s = blo[p] + j;
+                for (int q = 0; q < 12; ++q) {
+                    cpx<double> rv = S64::ld(r64, q * a.r64.cs + s - a.r64.off);
+                    SV::st(v.rhs, q * V + s, mk<R>((R)(rv.re * scale), (R)(rv.im * scale)));
+                }
+            }
+        __syncthreads();
+        // bhat_o = rhs_o + H_o(rhs_e)/(2A)
+        double bb = block_hop<SV, SL, SV>(g, bi, r, 1, 0, v.rhs, V, 0, v.bhat, Vh, Vh, v.rhs, V, 0, 1.0,
+                                          0.5 / A, Uin);
+        bb = cta_sum<NT>(bb, sh);
+        // e_o = 0, rho = bhat, res = Dhat^dag rho, p = res
+        for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+            const long long s = blo[1] + j;
+            for (int q = 0; q < 12; ++q) {
+                SV::st(v.e, q * V + s, mk<R>(0, 0));
+                SV::st(v.rho, q * Vh + s - Vh, SV::ld(v.bhat, q * Vh + s - Vh));
+            }
+        }
+        __syncthreads();
+        block_hop<SV, SL, SV>(g, bi, r, 0, 1, v.rho, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin);
+        __syncthreads();
+        double rr = block_hop<SV, SL, SV>(g, bi, r, 1, 1, v.t, Vh, 0, v.res, Vh, Vh, v.rho, Vh, Vh, A, c4, Uin);
+        rr = cta_sum<NT>(rr, sh);
+        for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+            const long long s = blo[1] + j - Vh;
+            for (int q = 0; q < 12; ++q) SV::st(v.pp, q * Vh + s, SV::ld(v.res, q * Vh + s));
+        }
+        __syncthreads();
+        const double target = a.delta * a.delta * bb;
+        int it = 0;
+        while (total_it + it < a.maxit) {
+            // q = Dhat p
+            block_hop<SV, SL, SV>(g, bi, r, 0, 0, v.pp, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin);
+            __syncthreads();
+            double qq = block_hop<SV, SL, SV>(g, bi, r, 1, 0, v.t, Vh, 0, v.q, Vh, Vh, v.pp, Vh, Vh, A, c4, Uin);
+            qq = cta_sum<NT>(qq, sh);
+            const R alpha = (R)(rr / qq);
+            double rhorho = 0;
+            for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+                const long long so = blo[1] + j;
+                const long long sh_ = so - Vh;
+                for (int q = 0; q < 12; ++q) {
+                    cpx<R> e = SV::ld(v.e, q * V + so);
+                    cpx<R> pv = SV::ld(v.pp, q * Vh + sh_);
+                    cpx<R> qv = SV::ld(v.q, q * Vh + sh_);
+                    cpx<R> ro = SV::ld(v.rho, q * Vh + sh_);
+                    e = e + alpha * pv;
+                    ro = ro - alpha * qv;
+                    SV::st(v.e, q * V + so, e);
+                    SV::st(v.rho, q * Vh + sh_, ro);
+                    rhorho += (double)norm2(ro);
+                }
+            }
+            rhorho = cta_sum<NT>(rhorho, sh);
+            ++it;
+            if (rhorho <= target) break;
+            // sv = Dhat^dag q
+            block_hop<SV, SL, SV>(g, bi, r, 0, 1, v.q, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin);
+            __syncthreads();
+            block_hop<SV, SL, SV>(g, bi, r, 1, 1, v.t, Vh, 0, v.sv, Vh, Vh, v.q, Vh, Vh, A, c4, Uin);
+            __syncthreads();
+            double rr_new = 0;
+            for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+                const long long sh_ = blo[1] + j - Vh;
+                for (int q = 0; q < 12; ++q) {
+                    cpx<R> rv = SV::ld(v.res, q * Vh + sh_);
+                    rv = rv - alpha * SV::ld(v.sv, q * Vh + sh_);
+                    SV::st(v.res, q * Vh + sh_, rv);
+                    rr_new += (double)norm2(rv);
+                }
+            }
+            rr_new = cta_sum<NT>(rr_new, sh);
+            const R beta = (R)(rr_new / rr);
+            rr = rr_new;
+            for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+                const long long sh_ = blo[1] + j - Vh;
+                for (int q = 0; q < 12; ++q) {
+                    cpx<R> pv = SV::ld(v.pp, q * Vh + sh_);
+                    SV::st(v.pp, q * Vh + sh_, SV::ld(v.res, q * Vh + sh_) + beta * pv);
+                }
+            }
+            __syncthreads();
+        }
+        total_it += it;
+        // e_e = (rhs_e + H_e(e_o)/2) / A
+        block_hop<SV, SL, SV>(g, bi, r, 0, 0, v.e, V, 0, v.e, V, 0, v.rhs, V, 0, 1.0 / A, 0.5 / A, Uin);
+        __syncthreads();
+        // x += e / scale (FP64)
+        const double unscale = sqrt(rn);
+        for (int p = 0; p < 2; ++p)
+            for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+                const long long s = blo[p] + j;
+                for (int q = 0; q < 12; ++q) {
+                    cpx<R> ev = SV::ld(v.e, q * V + s);
+                    cpx<double> xv = S64::ld(x, q * a.x.cs + s - a.x.off);
+                    xv = xv + unscale * mk<double>((double)ev.re, (double)ev.im);
+                    S64::st(x, q * a.x.cs + s - a.x.off, xv);
+                }
+            }
+        __syncthreads();
+    }
+    double xn = 0;
+    if (a.xnorm2) {
+        for (int p = 0; p < 2; ++p)
+            for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+                const long long s = blo[p] + j;
+                for (int q = 0; q < 12; ++q) xn += norm2(S64::ld(x, q * a.x.cs + s - a.x.off));
+            }
+        xn = cta_sum<NT>(xn, sh);
+    }
+    if (threadIdx.x == 0) {
+        a.iters[out_i] = total_it;
+        a.resid[out_i] = rel;
+        a.status[out_i] = st;
+        if (a.xnorm2) a.xnorm2[out_i] = xn;
+    }
+}
+
+void block_solve(psms_ctx *c, const BlockSolveReq &q) {
+    const Geom &g = c->g;
+    BlockSolveArgs a;
+    a.g = g;
+    a.binfo = c->d_binfo;
+    a.A = c->A;
+    a.rank_lo = q.rank_lo;
+    a.n_ranks = q.n_ranks;
+    a.b = q.b;
+    a.x = q.x;
+    const long long V = g.V;
+    const size_t full64 = (size_t)12 * V * sizeof(double2);
+    a.r64 = View<double2>{(double2 *)scratch(c, "bs_r64", full64 * q.n_sys), V, 0, 12 * V};
+    a.U64 = q.U64;
+    a.U64_bs = q.U64_bs;
+    const bool in64 = (q.inner_prec == P64);
+    const size_t esz = in64 ? sizeof(double2) : sizeof(float2);
+    const long long per_sys = 24 * V + 7 * 12 * (long long)g.Vh;  // elements
+    a.vin = scratch(c, "bs_inner", esz * (size_t)per_sys * q.n_sys);
+    a.vin_bs = per_sys;
+    a.Uin = in64 ? (const void *)q.U64 : (const void *)q.U32;
+    a.Uin_bs = q.U64_bs;  // same element count per field
+    a.tol = q.tol;
+    a.delta = in64 ? std::max(0.1 * q.tol, 1e-15) : 1e-6;
+    a.maxit = q.maxit;
+    a.max_outer = in64 ? 4 : 12;
+    a.sys_active = q.sys_active;
+    a.iters = q.iters;
+    a.resid = q.resid;
+    a.xnorm2 = q.xnorm2;
+    a.status = q.status;
+    dim3 grid(q.n_ranks, q.n_sys);
+    const int NT = 128;
+    if (in64)
+        block_solve_kernel<Store<double>, Store<double>, NT><<<grid, NT, 0, c->stream>>>(a);
+    else
+        block_solve_kernel<Store<float>, Store<float>, NT><<<grid, NT, 0, c->stream>>>(a);
+    PSMS_LAUNCH_CHECK("block_solve_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// whole-lattice batched solver
+// ---------------------------------------------------------------------------
+struct CGS {
+    double rr, alpha, beta, bb, target, rhorho;
+    int active, iters;
+};
+
+__global__ void cg_init_kernel(CGS *st, const double *bb, const double *rr, int n, double delta, const int *act,
+                               int *flags) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    CGS s;
+    s.bb = bb[k];
+    s.rr = rr[k];
+    s.target = delta * delta * bb[k];
+    s.alpha = s.beta = 0;
+    s.rhorho = bb[k];
+    s.active = act ? act[k] : 1;
+    if (s.bb == 0.0) s.active = 0;
+    s.iters = 0;
+    st[k] = s;
+    flags[k] = s.active;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) cg_alpha_kernel(CGS *st, const double *partial, int n) {
+    __shared__ double sh[NT / 32];
+    const int k = blockIdx.x;
+    if (!st[k].active) return;
+    double v = 0;
+    for (int i = threadIdx.x; i < n; i += NT) v += partial[(long long)k * n + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int i = 0; i < NT / 32; ++i) t += sh[i];
+        st[k].alpha = st[k].rr / t;
+    }
+}
+
+// stage 2: rr_new and rho^2 from two partial arrays -> beta, convergence
+template <int NT>
+__global__ void __launch_bounds__(NT) cg_beta_kernel(CGS *st, const double *p_rr, const double *p_rho, int n,
+                                                     int maxit, int *flags) {
+    __shared__ double sh[2][NT / 32];
+    const int k = blockIdx.x;
+    if (!st[k].active) return;
+    double v = 0, w = 0;
+    for (int i = threadIdx.x; i < n; i += NT) {
+        v += p_rr[(long long)k * n + i];
+        w += p_rho[(long long)k * n + i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+        w += __shfl_xor_sync(0xffffffffu, w, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = v;
+        sh[1][threadIdx.x >> 5] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0;
+        for (int i = 0; i < NT / 32; ++i) {
+            a += sh[0][i];
+            b += sh[1][i];
+        }
+        CGS s = st[k];
+        s.beta = a / s.rr;
+        s.rr = a;
+        s.rhorho = b;
+        s.iters += 1;
+        if (b <= s.target || s.iters >= maxit || !(b == b)) s.active = 0;
+        st[k] = s;
+        flags[k] = s.active;
+    }
+}
+
+// x += alpha p, rho -= alpha q, r -= alpha sv (odd halves), partial |r|^2, |rho|^2
+template <class S, int NT>
+__global__ void __launch_bounds__(NT) cg_update_kernel(const CGS *st, View<typename S::elem> e, View<typename S::elem> pp,
+                                                       View<typename S::elem> q, View<typename S::elem> rho,
+                                                       View<typename S::elem> res, View<typename S::elem> sv,
+                                                       long long s_lo, long long n, double *p_rr, double *p_rho,
+                                                       int skip_r) {
+    using R = typename S::R;
+    __shared__ double sh[2][NT / 32];
+    const int k = blockIdx.y;
+    if (!st[k].active) {
+        if (threadIdx.x == 0) {
+            p_rr[(long long)k * gridDim.x + blockIdx.x] = 0;
+            p_rho[(long long)k * gridDim.x + blockIdx.x] = 0;
+        }
+        return;
+    }
+    const R alpha = (R)st[k].alpha;
+    double a1 = 0, a2 = 0;
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
+    if (i < n) {
+        const long long s = s_lo + i;
+        for (int c = 0; c < 12; ++c) {
+            const long long ie = k * e.bs + c * e.cs + s - e.off;
+            const long long ip = k * pp.bs + c * pp.cs + s - pp.off;
+            cpx<R> ev = S::ld(e.p, ie) + alpha * S::ld(pp.p, ip);
+            S::st(e.p, ie, ev);
+            const long long iq = k * q.bs + c * q.cs + s - q.off;
+            const long long ir = k * rho.bs + c * rho.cs + s - rho.off;
+            cpx<R> ro = S::ld(rho.p, ir) - alpha * S::ld(q.p, iq);
+            S::st(rho.p, ir, ro);
+            a2 += (double)norm2(ro);
+            if (!skip_r) {
+                const long long is = k * sv.bs + c * sv.cs + s - sv.off;
+                const long long ires = k * res.bs + c * res.cs + s - res.off;
+                cpx<R> rv = S::ld(res.p, ires) - alpha * S::ld(sv.p, is);
+                S::st(res.p, ires, rv);
+                a1 += (double)norm2(rv);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = a1;
+        sh[1][threadIdx.x >> 5] = a2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0, t2 = 0;
+        for (int w = 0; w < NT / 32; ++w) {
+            t1 += sh[0][w];
+            t2 += sh[1][w];
+        }
+        p_rr[(long long)k * gridDim.x + blockIdx.x] = t1;
+        p_rho[(long long)k * gridDim.x + blockIdx.x] = t2;
+    }
+}
+
+// p = r + beta p
+template <class S, int NT>
+__global__ void __launch_bounds__(NT) cg_pupdate_kernel(const CGS *st, View<typename S::elem> pp,
+                                                        View<typename S::elem> res, long long s_lo, long long n) {
+    using R = typename S::R;
+    const int k = blockIdx.y;
+    if (!st[k].active) return;
+    const R beta = (R)st[k].beta;
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
+    if (i >= n) return;
+    const long long s = s_lo + i;
+    for (int c = 0; c < 12; ++c) {
+        const long long ip = k * pp.bs + c * pp.cs + s - pp.off;
+        const long long ir = k * res.bs + c * res.cs + s - res.off;
+        S::st(pp.p, ip, S::ld(res.p, ir) + beta * S::ld(pp.p, ip));
+    }
+}
+
+// copy / convert: dst = scale[k] * src (FP64 src), over sites [s_lo, s_lo+n)
+template <class SD, int NT>
+__global__ void __launch_bounds__(NT) scale_convert_kernel(View<typename SD::elem> dst, View<double2> src,
+                                                           const double *nrm2, int invert, const int *act,
+                                                           long long s_lo, long long n) {
+    const int k = blockIdx.y;
+    if (act && !act[k]) return;
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
+    if (i >= n) return;
+    double sc = 1.0;
+    if (nrm2) sc = invert ? 1.0 / sqrt(nrm2[k]) : sqrt(nrm2[k]);
+    const long long s = s_lo + i;
+    for (int c = 0; c < 12; ++c) {
+        double2 v = src.p[k * src.bs + c * src.cs + s - src.off];
+        SD::st(dst.p, k * dst.bs + c * dst.cs + s - dst.off,
+               mk<typename SD::R>((typename SD::R)(sc * v.x), (typename SD::R)(sc * v.y)));
+    }
+}
+
+// x (FP64) += sqrt(nrm2[k]) * e
+template <class SE, int NT>
+__global__ void __launch_bounds__(NT) accumulate_kernel(View<double2> x, View<typename SE::elem> e, const double *nrm2,
+                                                        const int *act, long long s_lo, long long n) {
+    const int k = blockIdx.y;
+    if (act && !act[k]) return;
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
+    if (i >= n) return;
+    const double sc = sqrt(nrm2[k]);
+    const long long s = s_lo + i;
+    for (int c = 0; c < 12; ++c) {
+        cpx<typename SE::R> ev = SE::ld(e.p, k * e.bs + c * e.cs + s - e.off);
+        double2 &xv = x.p[k * x.bs + c * x.cs + s - x.off];
+        xv.x += sc * (double)ev.re;
+        xv.y += sc * (double)ev.im;
+    }
+}
+
+__global__ void residual_flags_kernel(const double *rn, const double *bn, double tol, int *act, double *rel, int n) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double r = bn[k] > 0 ? sqrt(rn[k] / bn[k]) : 0.0;
+    rel[k] = r;
+    act[k] = (r > tol) ? 1 : 0;
+}
+
+__global__ void set_int_kernel(int *p, int v, int n) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) p[k] = v;
+}
+
+__global__ void iters_kernel(const CGS *st, int *out, int n) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] += st[k].iters;
+}
+
+template <class SV>
+static void inner_cg_full(psms_ctx *c, int n_sys, const void *Uin, long long U_bs, int prec, View<void> rhs,
+                          View<void> e, const int *act_in, double delta, int maxit, int *iters_acc) {
+    using E = typename SV::elem;
+    const Geom &g = c->g;
+    const long long V = g.V, Vh = g.Vh;
+    const double A = c->A, c4 = -1.0 / (4.0 * A);
+    const size_t esz = sizeof(E);
+    // odd-half vectors: bhat, rho, res, pp, q, sv ; even half: t
+    E *base = (E *)scratch(c, "fs_inner", esz * (size_t)(7 * 12 * Vh) * n_sys);
+    auto half = [&](int i, long long off) {
+        View<void> v;
+        v.p = base + (long long)i * 12 * Vh * n_sys;
+        v.cs = Vh;
+        v.off = off;
+        v.bs = 12 * Vh;
+        return v;
+    };
+    View<void> bhat = half(0, Vh), rho = half(1, Vh), res = half(2, Vh), pp = half(3, Vh), q = half(4, Vh),
+               sv = half(5, Vh), t = half(6, 0);
+    auto tv = [](View<void> v) { return View<E>{(E *)v.p, v.cs, v.off, v.bs}; };
+    CGS *st = (CGS *)scratch(c, "fs_cgs", sizeof(CGS) * n_sys);
+    int *flags = (int *)scratch(c, "fs_flags", sizeof(int) * n_sys);
+    double *bb = (double *)scratch(c, "fs_bb", sizeof(double) * n_sys);
+    double *rr0 = (double *)scratch(c, "fs_rr0", sizeof(double) * n_sys);
+
+    HopCall h;
+    h.prec = prec;
+    h.U = Uin;
+    h.U_bs = U_bs;
+    h.n_sys = n_sys;
+    h.active = act_in;
+    const int nct = hop_ctas(c, [&] { HopCall x; x.p = 1; return x; }());
+    double *p_a = (double *)scratch(c, "fs_pa", sizeof(double) * (size_t)nct * n_sys);
+    double *p_b = (double *)scratch(c, "fs_pb", sizeof(double) * (size_t)nct * n_sys);
+
+    // bhat_o = rhs_o + H_o(rhs_e)/(2A)
+    h.p = 1;
+    h.in = rhs;
+    h.out = bhat;
+    h.y = rhs;
+    h.a = 1.0;
+    h.b = 0.5 / A;
+    h.partial = p_a;
+    hop_launch(c, h);
+    reduce_partials(c, p_a, nct, n_sys, bb);
+    // e_o = 0 ; rho = bhat ; res = Dhat^dag rho ; pp = res
+    cudaMemsetAsync((char *)e.p, 0, esz * (size_t)12 * V * n_sys, c->stream);
+    cudaMemcpyAsync(rho.p, bhat.p, esz * (size_t)12 * Vh * n_sys, cudaMemcpyDeviceToDevice, c->stream);
+    h.y = View<void>();
+    h.partial = nullptr;
+    h.p = 0;
+    h.dag = 1;
+    h.in = rho;
+    h.out = t;
+    h.b = 1.0;
+    hop_launch(c, h);
+    h.p = 1;
+    h.in = t;
+    h.out = res;
+    h.y = rho;
+    h.a = A;
+    h.b = c4;
+    h.partial = p_a;
+    hop_launch(c, h);
+    reduce_partials(c, p_a, nct, n_sys, rr0);
+    cudaMemcpyAsync(pp.p, res.p, esz * (size_t)12 * Vh * n_sys, cudaMemcpyDeviceToDevice, c->stream);
+    cg_init_kernel<<<(n_sys + 63) / 64, 64, 0, c->stream>>>(st, bb, rr0, n_sys, delta, act_in, flags);
+    PSMS_LAUNCH_CHECK("cg_init");
+    const int NT = 256;
+    const long long n = Vh;
+    const int nb = (int)((n + NT - 1) / NT);
+    dim3 grid(nb, n_sys);
+    double *u_rr = (double *)scratch(c, "fs_urr", sizeof(double) * (size_t)nb * n_sys);
+    double *u_rho = (double *)scratch(c, "fs_urho", sizeof(double) * (size_t)nb * n_sys);
+    int it = 0;
+    int chunk = 8;
+    std::vector<int> hflags(n_sys);
+    h.active = flags;  // mirrors CGS.active
+    while (it < maxit) {
+        for (int i = 0; i < chunk && it < maxit; ++i, ++it) {
+            // q = Dhat p
+            h.dag = 0;
+            h.p = 0;
+            h.in = pp;
+            h.out = t;
+            h.y = View<void>();
+            h.a = 0;
+            h.b = 1.0;
+            h.partial = nullptr;
+            hop_launch(c, h);
+            h.p = 1;
+            h.in = t;
+            h.out = q;
+            h.y = pp;
+            h.a = A;
+            h.b = c4;
+            h.partial = p_a;
+            hop_launch(c, h);
+            cg_alpha_kernel<256><<<n_sys, 256, 0, c->stream>>>(st, p_a, nct);
+            // sv = Dhat^dag q
+            h.dag = 1;
+            h.p = 0;
+            h.in = q;
+            h.out = t;
+            h.y = View<void>();
+            h.a = 0;
+            h.b = 1.0;
+            h.partial = nullptr;
+            hop_launch(c, h);
+            h.p = 1;
+            h.in = t;
+            h.out = sv;
+            h.y = q;
+            h.a = A;
+            h.b = c4;
+            hop_launch(c, h);
+            cg_update_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, tv(e), tv(pp), tv(q), tv(rho), tv(res), tv(sv), Vh,
+                                                                 n, u_rr, u_rho, 0);
+            cg_beta_kernel<256><<<n_sys, 256, 0, c->stream>>>(st, u_rr, u_rho, nb, maxit, flags);
+            cg_pupdate_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, tv(pp), tv(res), Vh, n);
+            PSMS_LAUNCH_CHECK("cg iteration");
+        }
+        cuda_check(cudaMemcpyAsync(hflags.data(), flags, sizeof(int) * n_sys, cudaMemcpyDeviceToHost, c->stream),
+                   "cg flags");
+        cuda_check(cudaStreamSynchronize(c->stream), "cg sync");
+        bool any = false;
+        for (int k = 0; k < n_sys; ++k) any |= hflags[k] != 0;
+        if (!any) break;
+        chunk = std::min(chunk * 2, 64);
+    }
+    iters_kernel<<<(n_sys + 63) / 64, 64, 0, c->stream>>>(st, iters_acc, n_sys);
+    // e_e = (rhs_e + H_e(e_o)/2)/A
+    h.active = act_in;
+    h.dag = 0;
+    h.p = 0;
+    h.in = e;
+    h.out = e;
+    h.y = rhs;
+    h.a = 1.0 / A;
+    h.b = 0.5 / A;
+    h.partial = nullptr;
+    hop_launch(c, h);
+}
+
+void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info) {
+    const Geom &g = c->g;
+    const long long V = g.V;
+    const int n = q.n_sys;
+    double *bn = (double *)scratch(c, "fb_bn", sizeof(double) * n);
+    double *rn = (double *)scratch(c, "fb_rn", sizeof(double) * n);
+    double *rel = (double *)scratch(c, "fb_rel", sizeof(double) * n);
+    int *act = (int *)scratch(c, "fb_act", sizeof(int) * n);
+    int *iters = (int *)scratch(c, "fb_iters", sizeof(int) * n);
+    double2 *r64 = (double2 *)scratch(c, "fb_r64", sizeof(double2) * (size_t)12 * V * n);
+    View<void> b{q.b.p, q.b.cs, q.b.off, q.b.bs}, x{q.x.p, q.x.cs, q.x.off, q.x.bs};
+    View<void> r{r64, V, 0, 12 * V};
+    const bool in64 = q.inner_prec == P64;
+    const size_t esz = in64 ? sizeof(double2) : (q.inner_prec == P32 ? sizeof(float2) : sizeof(__nv_bfloat162));
+    void *rin_p = scratch(c, "fb_rin", esz * (size_t)12 * V * n);
+    void *ein_p = scratch(c, "fb_ein", esz * (size_t)12 * V * n);
+    View<void> rin{rin_p, V, 0, 12 * V}, ein{ein_p, V, 0, 12 * V};
+    norm2_batch(c, P64, b, 0, V, n, bn);
+    for (int k = 0; k < n; ++k)
+        cuda_check(cudaMemsetAsync((char *)q.x.p + sizeof(double2) * k * q.x.bs, 0, sizeof(double2) * 12 * V, c->stream),
+                   "zero x");
+    set_int_kernel<<<(n + 63) / 64, 64, 0, c->stream>>>(iters, 0, n);
+    const double delta = in64 ? std::max(0.1 * q.tol, 1e-15) : (q.inner_prec == P32 ? 2e-6 : 5e-3);
+    const int max_outer = in64 ? 6 : 30;
+    std::vector<int> hact(n);
+    int outer = 0;
+    const int NT = 256;
+    dim3 grid((unsigned)((V + NT - 1) / NT), n);
+    for (;; ++outer) {
+        // r = b - D x = b - A x + H(x)/2   (FP64, both parities)
+        HopCall h;
+        h.prec = P64;
+        h.U = q.U64;
+        h.U_bs = q.U64_bs;
+        h.n_sys = n;
+        h.p = -1;
+        h.in = x;
+        h.out = r;
+        h.y = b;
+        h.a = 1.0;
+        h.y2 = x;
+        h.a2 = -c->A;
+        h.b = 0.5;
+        hop_launch(c, h);
+        norm2_batch(c, P64, r, 0, V, n, rn);
+        residual_flags_kernel<<<(n + 63) / 64, 64, 0, c->stream>>>(rn, bn, q.tol, act, rel, n);
+        cuda_check(cudaMemcpyAsync(hact.data(), act, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream), "act");
+        cuda_check(cudaStreamSynchronize(c->stream), "solve sync");
+        bool any = false;
+        for (int k = 0; k < n; ++k) any |= hact[k] != 0;
+        if (!any || outer >= max_outer) break;
+        // inner rhs = r / |r|
+        View<double2> r2{r64, V, 0, 12 * V};
+        if (in64) {
+            scale_convert_kernel<Store<double>, NT><<<grid, NT, 0, c->stream>>>(
+                View<double2>{(double2 *)rin_p, V, 0, 12 * V}, r2, rn, 1, act, 0, V);
+            inner_cg_full<Store<double>>(c, n, q.U64, q.U64_bs, P64, rin, ein, act, delta, q.maxit, iters);
+            accumulate_kernel<Store<double>, NT><<<grid, NT, 0, c->stream>>>(
+                View<double2>{(double2 *)q.x.p, q.x.cs, q.x.off, q.x.bs}, View<double2>{(double2 *)ein_p, V, 0, 12 * V},
+                rn, act, 0, V);
+        } else if (q.inner_prec == P32) {
+            scale_convert_kernel<Store<float>, NT><<<grid, NT, 0, c->stream>>>(
+                View<float2>{(float2 *)rin_p, V, 0, 12 * V}, r2, rn, 1, act, 0, V);
+            inner_cg_full<Store<float>>(c, n, q.U32, q.U64_bs, P32, rin, ein, act, delta, q.maxit, iters);
+            accumulate_kernel<Store<float>, NT><<<grid, NT, 0, c->stream>>>(
+                View<double2>{(double2 *)q.x.p, q.x.cs, q.x.off, q.x.bs}, View<float2>{(float2 *)ein_p, V, 0, 12 * V},
+                rn, act, 0, V);
+        } else {
+            scale_convert_kernel<Store<__nv_bfloat16>, NT><<<grid, NT, 0, c->stream>>>(
+                View<__nv_bfloat162>{(__nv_bfloat162 *)rin_p, V, 0, 12 * V}, r2, rn, 1, act, 0, V);
+            inner_cg_full<Store<__nv_bfloat16>>(c, n, q.U32, q.U64_bs, PB16, rin, ein, act, delta, q.maxit, iters);
+            accumulate_kernel<Store<__nv_bfloat16>, NT><<<grid, NT, 0, c->stream>>>(
+                View<double2>{(double2 *)q.x.p, q.x.cs, q.x.off, q.x.bs},
+                View<__nv_bfloat162>{(__nv_bfloat162 *)ein_p, V, 0, 12 * V}, rn, act, 0, V);
+        }
+        PSMS_LAUNCH_CHECK("defect correction");
+    }
+    std::vector<double> hrel(n);
+    std::vector<int> hit(n);
+    cuda_check(cudaMemcpyAsync(hrel.data(), rel, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "rel");
+    cuda_check(cudaMemcpyAsync(hit.data(), iters, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream), "iters");
+    cuda_check(cudaStreamSynchronize(c->stream), "solve end");
+    double worst = 0;
+    long long tot = 0;
+    for (int k = 0; k < n; ++k) {
+        worst = std::max(worst, hrel[k]);
+        tot += hit[k];
+    }
+    if (info) {
+        info->outer_iters = outer;
+        info->inner_iters = tot;
+        info->true_residual = worst;
+        info->n_systems = n;
+    }
+    if (q.rel_out)
+        cuda_check(cudaMemcpyAsync(q.rel_out, rel, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "rel out");
+    if (!(worst <= q.tol)) fail(PSMS_ENOCONV, "whole-lattice solve missed its tolerance");
+}
+
+}  // namespace psms

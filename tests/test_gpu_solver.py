@@ -1,0 +1,91 @@
+"""GPU parity of the Krylov solves (whole lattice and Dirichlet blocks) with
+the oracle: the solution matches the oracle's CGNR solution and the true
+residual, recomputed with the oracle's D, meets the tolerance."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1204_1306_gb300 as ps
+from oracle import dirac, estimator, gauge, lattice, linalg
+from tests import seeded
+from tests.gpu_util import canonical, native, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("inner", [ps.PREC_F64, ps.PREC_F32, ps.PREC_BF16])
+def test_full_solve_parity(inner):
+    dims, block, kappa = (4, 4, 4, 4), (2, 2, 2, 2), 0.15
+    ctx = ps.psms_create(dims, block, kappa, 1)
+    ps.psms_gauge_init(ctx, 0, 0.3, 0x50534D53)
+    U = gauge.generate_links(dims, 0.3, 0x50534D53)
+    b = seeded.spinor(dims, 1)
+    x = torch.zeros_like(native(ctx, b))
+    info = ps.psms_solve(ctx, 0, ps.OP_FULL, native(ctx, b), x, 1e-13, 20000, inner)
+    got = canonical(ctx, x)
+    ref, _, _ = linalg.cgnr(lambda v: dirac.apply_D(U, v, kappa), lambda v: dirac.apply_D(U, v, kappa, dagger=True),
+                            b, tol=1e-14)
+    r = b - dirac.apply_D(U, got, kappa)
+    assert np.sqrt(linalg.norm2(r) / linalg.norm2(b)) <= 1e-13
+    assert info["true_residual"] <= 1e-13
+    assert rel_err(got, ref) < 1e-11
+
+
+def test_full_solve_16x4_config():
+    """16^4, kappa = 0.156, eps = 0.5 links: mixed FP32 inner iterations in FP64
+    defect correction to 1e-10 (true residual checked with the oracle's D)."""
+    dims, block, kappa = (16, 16, 16, 16), (4, 4, 4, 4), 0.156
+    ctx = ps.psms_create(dims, block, kappa, 1)
+    ps.psms_gauge_init(ctx, 0, 0.5, 0x50534D53 + 1)
+    U = gauge.generate_links(dims, 0.5, 0x50534D53 + 1)
+    b = seeded.spinor(dims, 2)
+    x = torch.zeros_like(native(ctx, b))
+    info = ps.psms_solve(ctx, 0, ps.OP_FULL, native(ctx, b), x, 1e-10, 20000, ps.PREC_F32)
+    got = canonical(ctx, x)
+    r = b - dirac.apply_D(U, got, kappa)
+    assert np.sqrt(linalg.norm2(r) / linalg.norm2(b)) <= 1e-10
+    assert info["outer_iters"] >= 1
+
+
+@pytest.mark.parametrize("inner", [ps.PREC_F64, ps.PREC_F32])
+@pytest.mark.parametrize("dims,block", [((4, 4, 4, 4), (2, 2, 2, 2)), ((8, 8, 8, 8), (4, 4, 4, 4)),
+                                        ((8, 8, 8, 8), (8, 8, 8, 4))])
+def test_block_solve_parity(dims, block, inner):
+    kappa = 0.156
+    geom = lattice.Geometry(dims, block)
+    ctx = ps.psms_create(dims, block, kappa, 1)
+    ps.psms_gauge_init(ctx, 0, 0.5, 5)
+    U = gauge.generate_links(dims, 0.5, 5)
+    b = seeded.spinor(dims, 6)
+    x = torch.zeros_like(native(ctx, b))
+    ps.psms_solve(ctx, 0, ps.OP_BLOCKS, native(ctx, b), x, 1e-13, 20000, inner)
+    got = canonical(ctx, x)
+    blocks = sorted({0, geom.n_blocks // 3, geom.n_blocks - 1})
+    ref = estimator.solve_blocks(U, b, geom, kappa, blocks, 1e-14)
+    for bb in blocks:
+        g = dirac.extract_block(got, geom, bb)
+        assert rel_err(g, dirac.extract_block(ref, geom, bb)) < 1e-11
+    # true residual of the whole block-diagonal system
+    r = b - dirac.apply_D(U, got, kappa, geom, mode="block")
+    assert np.sqrt(linalg.norm2(r) / linalg.norm2(b)) <= 1e-13
+    # single block: zero outside
+    x1 = torch.zeros_like(x)
+    ps.psms_solve(ctx, 0, blocks[-1], native(ctx, b), x1, 1e-13, 20000, inner)
+    g1 = canonical(ctx, x1)
+    mask = (geom.block_index == blocks[-1])[..., None, None]
+    assert np.abs(g1 * ~mask).max() == 0.0
+    assert rel_err(g1 * mask, ref * mask) < 1e-11
+
+
+def test_solver_reports_non_convergence():
+    dims, block = (4, 4, 4, 4), (2, 2, 2, 2)
+    ctx = ps.psms_create(dims, block, 0.15, 1)
+    ps.psms_gauge_init(ctx, 0, 0.3, 1)
+    b = seeded.spinor(dims, 3)
+    x = torch.zeros_like(native(ctx, b))
+    with pytest.raises(ps.PsmsError) as e:
+        ps.psms_solve(ctx, 0, ps.OP_FULL, native(ctx, b), x, 1e-13, 3, ps.PREC_F64)
+    assert e.value.status == 4
+    with pytest.raises(ps.PsmsError) as e:
+        ps.psms_solve(ctx, 0, ps.OP_BLOCKS, native(ctx, b), x, 1e-13, 2, ps.PREC_F64)
+    assert e.value.status == 4
