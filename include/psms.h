@@ -211,11 +211,18 @@ psms_status psms_logdet_ratio(psms_ctx *ctx, int level, int field_old, int field
 psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params *prm,
                              psms_filter_result *res, double *delta_block_out, int *accept_block_out);
 
-/* Profiling: when enabled, the context records CUDA events around its
- * Wilson-operator launches; read the count and summed milliseconds. */
+/* Profiling: when enabled, the context records CUDA events on its stream
+ * around every full-operator Wilson hop launch (enable = 1), or only those of
+ * storage precision p (enable = 10 + p); psms_profile_read returns the launch
+ * count, the summed milliseconds and the summed algorithmic bytes (spinors in
+ * and out, 4 links per output site of a both-parity launch, 8 of a
+ * single-parity launch). */
 psms_status psms_profile_enable(psms_ctx *ctx, int enable);
 psms_status psms_profile_read(psms_ctx *ctx, long long *launches, double *total_ms,
                               double *bytes_per_launch_sum);
+
+/* Number of CUDA kernels the library has launched in this process. */
+long long psms_kernel_launches(void);
 
 #ifdef __cplusplus
 }

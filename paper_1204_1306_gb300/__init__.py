@@ -111,6 +111,8 @@ def load_library(path=LIB_PATH):
     lib.psms_last_error.restype = ctypes.c_char_p
     lib.psms_spinor_bytes.argtypes = [_P, _I]
     lib.psms_spinor_bytes.restype = ctypes.c_size_t
+    lib.psms_kernel_launches.argtypes = []
+    lib.psms_kernel_launches.restype = ctypes.c_longlong
     _lib = lib
     return lib
 

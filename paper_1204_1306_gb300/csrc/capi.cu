@@ -12,6 +12,11 @@
 
 namespace psms {
 
+long long &launch_counter() {
+    static long long n = 0;
+    return n;
+}
+
 void *scratch(psms_ctx *c, const std::string &name, size_t bytes) {
     if (bytes == 0) bytes = 16;
     DevBuf &b = c->scratch[name];
@@ -595,11 +600,14 @@ psms_status psms_profile_enable(psms_ctx *ctx, int enable) {
     PSMS_TRY(ctx)
     prof_collect(ctx);
     ctx->prof = enable != 0;
+    ctx->prof_prec = enable >= 10 ? enable - 10 : -1;
     ctx->prof_launches = 0;
     ctx->prof_ms = 0;
     ctx->prof_bytes = 0;
     PSMS_CATCH(ctx)
 }
+
+long long psms_kernel_launches(void) { return launch_counter(); }
 
 psms_status psms_profile_read(psms_ctx *ctx, long long *launches, double *total_ms, double *bytes) {
     PSMS_TRY(ctx)

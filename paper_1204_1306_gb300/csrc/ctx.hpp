@@ -27,7 +27,9 @@ inline void cuda_check(cudaError_t e, const char *what) {
     }
 }
 
-#define PSMS_LAUNCH_CHECK(what) ::psms::cuda_check(cudaGetLastError(), what)
+// process-wide count of kernel launches issued by the library
+long long &launch_counter();
+#define PSMS_LAUNCH_CHECK(what) (++::psms::launch_counter(), ::psms::cuda_check(cudaGetLastError(), what))
 
 struct DevBuf {
     void *p = nullptr;
@@ -51,6 +53,7 @@ struct psms_ctx {
     std::map<std::string, psms::DevBuf> scratch;
     // profiling of Wilson-operator launches
     bool prof = false;
+    int prof_prec = -1;  // profile hop launches of this storage precision only (-1: all)
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, double>> prof_pending;  // (event pair index, bytes)
     long long prof_launches = 0;

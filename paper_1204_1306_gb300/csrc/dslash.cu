@@ -177,7 +177,7 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
     dim3 grid(nct, h.n_sys);
     double bytes = 0;
     int slot = -1;
-    if (c->prof) {
+    if (c->prof && h.mode == HOP_ALL && (c->prof_prec < 0 || c->prof_prec == h.prec)) {
         // algorithmic bytes: in + out (+ y, y2) spinors and 4 links per output site
         const long long sites = (h.p < 0 ? 2LL : 1LL) * a.n_ranks * c->g.Vbh;
         const double sp = 12.0 * sizeof(E), lk = 9.0 * sizeof(typename SL::elem);

@@ -16,6 +16,7 @@
 #include "gauge.hpp"
 #include "solver.hpp"
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -53,14 +54,14 @@ __device__ __forceinline__ void apply_P(const Geom &g, int r, const int y[4], Sp
 }
 
 __global__ void noise_kernel(Geom g, const BlockInfo *binfo, double2 *out, long long bs, uint64_t seed,
-                             uint64_t counter, uint64_t level, int proj) {
+                             uint64_t counter, uint64_t level, int proj, int i0) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.V) return;
     const uint64_t i = blockIdx.y;
     int p, r, j, y[4], x[4];
     decode(g, binfo, s, p, r, j, y, x);
     const uint64_t lex = (uint64_t)lex_index(g, x);
-    const uint64_t stream = (level << 32) | i;
+    const uint64_t stream = (level << 32) | (uint64_t)(i0 + i);
     Spinor<double> v;
     for (int jj = 0; jj < 6; ++jj) {
         uni4 u = uniforms(seed, TAG_NOISE, counter, stream, lex, (uint64_t)jj);
@@ -75,10 +76,11 @@ __global__ void noise_kernel(Geom g, const BlockInfo *binfo, double2 *out, long 
     store_spinor<Store<double>>(out + i * bs, g.V, s, v);
 }
 
-void noise(psms_ctx *c, double2 *out, int n, uint64_t seed, uint64_t counter, int level, int proj) {
+void noise(psms_ctx *c, double2 *out, int n, uint64_t seed, uint64_t counter, int level, int proj, int i0) {
     const int NT = 128;
     dim3 grid((unsigned)((c->g.V + NT - 1) / NT), n);
-    noise_kernel<<<grid, NT, 0, c->stream>>>(c->g, c->d_binfo, out, 12 * c->g.V, seed, counter, (uint64_t)level, proj);
+    noise_kernel<<<grid, NT, 0, c->stream>>>(c->g, c->d_binfo, out, 12 * c->g.V, seed, counter, (uint64_t)level, proj,
+                                             i0);
     PSMS_LAUNCH_CHECK("noise");
 }
 
@@ -130,13 +132,23 @@ __global__ void __launch_bounds__(NT) block_norm_kernel(Geom g, const double2 *v
     }
 }
 
-// delta[lex(r) * N + i] = a[i * nr + r] - b[i * nr + r]
-__global__ void block_delta_kernel(const BlockInfo *binfo, const double *a, const double *b, int nr, int N,
-                                   double *delta) {
+// delta[lex(r) * N + i0 + i] = a[i * nr + r] - b[i * nr + r], i < n
+__global__ void block_delta_kernel(const BlockInfo *binfo, const double *a, const double *b, int nr, int n, int N,
+                                   int i0, double *delta) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nr * N) return;
+    if (t >= nr * n) return;
     const int i = t / nr, r = t % nr;
-    delta[(long long)binfo[r].lex * N + i] = a[t] - b[t];
+    delta[(long long)binfo[r].lex * N + i0 + i] = a[t] - b[t];
+}
+
+// number of interpolation steps batched per launch, from a per-system
+// device-memory estimate (bytes per lattice site) and a 64 GB budget
+static int chunk_size(psms_ctx *c, int N, double bytes_per_site) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    double budget = std::min(64e9, 0.45 * (double)tot);
+    int k = (int)(budget / (bytes_per_site * (double)c->g.V));
+    return std::max(1, std::min(N, k));
 }
 
 static void check_status(psms_ctx *c, const int *d_status, int n, const char *what) {
@@ -154,19 +166,19 @@ struct Interp {
     long long bs;  // complex elements per field
 };
 
+// fields U_{i0} .. U_{i0+n} of Eq. (gfparam) (or U, U' in the independent mode)
 static Interp make_interp(psms_ctx *c, const double2 *U, const double2 *Up, int N, int mode, bool need32,
-                          const char *tag) {
+                          const char *tag, int i0, int n) {
     const long long nel = 36 * c->g.V;
     Interp it;
     it.bs = nel;
-    const int nf = (mode == PSMS_EST_INDEPENDENT) ? 2 : N + 1;
+    const int nf = (mode == PSMS_EST_INDEPENDENT) ? 2 : n + 1;
     it.u64 = (double2 *)scratch(c, std::string("interp64_") + tag, sizeof(double2) * nel * nf);
     it.u32 = need32 ? (float2 *)scratch(c, std::string("interp32_") + tag, sizeof(float2) * nel * nf) : nullptr;
     if (mode == PSMS_EST_INDEPENDENT) {
-        // field 0 = U, field 1 = U'
-        interpolate(c, U, Up, it.u64, it.u32, 1, 0, 2);
+        interpolate(c, U, Up, it.u64, it.u32, 1, 0, 2);  // field 0 = U, field 1 = U'
     } else {
-        interpolate(c, U, Up, it.u64, it.u32, N, 0, N + 1);
+        interpolate(c, U, Up, it.u64, it.u32, N, i0, n + 1);
     }
     return it;
 }
@@ -195,24 +207,24 @@ static Pair pair_of(const Interp &it, int mode) {
     return p;
 }
 
-long long block_level(psms_ctx *c, const double2 *U, const double2 *Up, int N, int mode, uint64_t seed,
-                      uint64_t counter, double tol, int inner, double *d_delta) {
+static long long block_level_chunk(psms_ctx *c, const double2 *U, const double2 *Up, int N, int i0, int n, int mode,
+                                   uint64_t seed, uint64_t counter, double tol, int inner, double *d_delta) {
     const Geom &g = c->g;
     const long long V = g.V;
     const long long fs = 12 * V;
     const int nr = g.nblocks;
-    Interp it = make_interp(c, U, Up, N, mode, inner != P64, "blk");
+    Interp it = make_interp(c, U, Up, N, mode, inner != P64, "blk", i0, n);
     Pair pr = pair_of(it, mode);
-    double2 *xi = (double2 *)scratch(c, "bl_xi", sizeof(double2) * fs * N);
-    double2 *eta = (double2 *)scratch(c, "bl_eta", sizeof(double2) * fs * N);
-    double2 *ysol = (double2 *)scratch(c, "bl_y", sizeof(double2) * fs * N);
-    noise(c, xi, N, seed, counter, PSMS_LEVEL_BLOCK, 0);
+    double2 *xi = (double2 *)scratch(c, "bl_xi", sizeof(double2) * fs * n);
+    double2 *eta = (double2 *)scratch(c, "bl_eta", sizeof(double2) * fs * n);
+    double2 *ysol = (double2 *)scratch(c, "bl_y", sizeof(double2) * fs * n);
+    noise(c, xi, n, seed, counter, PSMS_LEVEL_BLOCK, 0, i0);
     // eta_i = D_blk(U_i) xi_i = A xi - H_intra(xi)/2
     HopCall h;
     h.prec = P64;
     h.U = pr.a64;
     h.U_bs = pr.bs;
-    h.n_sys = N;
+    h.n_sys = n;
     h.p = -1;
     h.mode = HOP_INTRA;
     h.in = View<void>{xi, V, 0, fs};
@@ -221,15 +233,15 @@ long long block_level(psms_ctx *c, const double2 *U, const double2 *Up, int N, i
     h.a = c->A;
     h.b = -0.5;
     hop_launch(c, h);
-    int *iters = (int *)scratch(c, "bl_iters", sizeof(int) * nr * N);
-    double *resid = (double *)scratch(c, "bl_resid", sizeof(double) * nr * N);
-    double *xn = (double *)scratch(c, "bl_xn", sizeof(double) * nr * N);
-    double *xin = (double *)scratch(c, "bl_xin", sizeof(double) * nr * N);
-    int *status = (int *)scratch(c, "bl_status", sizeof(int) * nr * N);
+    int *iters = (int *)scratch(c, "bl_iters", sizeof(int) * nr * n);
+    double *resid = (double *)scratch(c, "bl_resid", sizeof(double) * nr * n);
+    double *xn = (double *)scratch(c, "bl_xn", sizeof(double) * nr * n);
+    double *xin = (double *)scratch(c, "bl_xin", sizeof(double) * nr * n);
+    int *status = (int *)scratch(c, "bl_status", sizeof(int) * nr * n);
     BlockSolveReq q;
     q.rank_lo = 0;
     q.n_ranks = nr;
-    q.n_sys = N;
+    q.n_sys = n;
     q.b = View<double2>{eta, V, 0, fs};
     q.x = View<double2>{ysol, V, 0, fs};
     q.U64 = pr.b64;
@@ -242,15 +254,25 @@ long long block_level(psms_ctx *c, const double2 *U, const double2 *Up, int N, i
     q.xnorm2 = xn;
     q.status = status;
     block_solve(c, q);
-    block_norm_kernel<128><<<dim3(nr, N), 128, 0, c->stream>>>(g, xi, fs, 0, nr, xin);
-    block_delta_kernel<<<(nr * N + 127) / 128, 128, 0, c->stream>>>(c->d_binfo, xn, xin, nr, N, d_delta);
-    PSMS_LAUNCH_CHECK("block_level");
-    check_status(c, status, nr * N, "block level");
-    std::vector<int> hit(nr * N);
-    cuda_check(cudaMemcpyAsync(hit.data(), iters, sizeof(int) * nr * N, cudaMemcpyDeviceToHost, c->stream), "iters");
+    block_norm_kernel<128><<<dim3(nr, n), 128, 0, c->stream>>>(g, xi, fs, 0, nr, xin);
+    PSMS_LAUNCH_CHECK("block_norm_kernel");
+    block_delta_kernel<<<(nr * n + 127) / 128, 128, 0, c->stream>>>(c->d_binfo, xn, xin, nr, n, N, i0, d_delta);
+    PSMS_LAUNCH_CHECK("block_delta_kernel");
+    check_status(c, status, nr * n, "block level");
+    std::vector<int> hit(nr * n);
+    cuda_check(cudaMemcpyAsync(hit.data(), iters, sizeof(int) * nr * n, cudaMemcpyDeviceToHost, c->stream), "iters");
     cuda_check(cudaStreamSynchronize(c->stream), "iters");
     long long tot = 0;
     for (int v : hit) tot += v;
+    return tot / nr;  // whole-lattice-equivalent iterations
+}
+
+long long block_level(psms_ctx *c, const double2 *U, const double2 *Up, int N, int mode, uint64_t seed,
+                      uint64_t counter, double tol, int inner, double *d_delta) {
+    const int ch = chunk_size(c, N, inner == P64 ? 2600.0 : 2100.0);
+    long long tot = 0;
+    for (int i0 = 0; i0 < N; i0 += ch)
+        tot += block_level_chunk(c, U, Up, N, i0, std::min(ch, N - i0), mode, seed, counter, tol, inner, d_delta);
     return tot;
 }
 
@@ -288,6 +310,7 @@ static long long one_minus_PQ(psms_ctx *c, const double2 *U64, const float2 *U32
         cuda_check(cudaStreamSynchronize(c->stream), "it");
         for (int w : hit) tot += w;
     };
+    // block iterations are returned in whole-lattice-equivalent units below
     HopCall h;
     h.prec = P64;
     h.U = U64;
@@ -313,7 +336,7 @@ static long long one_minus_PQ(psms_ctx *c, const double2 *U64, const float2 *U32
     solve_ranks(0, t1, t2);
     // v = xi - P t2 (t2 holds stale white-block values; P = 0 there)
     sub_proj(c, v, xi, t2, N);
-    return tot;
+    return tot / g.nblocks;
 }
 
 // w = (1 - P Q(U_{i+1}))^-1 v = v - P [D^-1 (0, D_wb v)]_black
@@ -353,29 +376,40 @@ static long long inv_one_minus_PQ(psms_ctx *c, const double2 *U64, const float2 
     return info.inner_iters;
 }
 
+static long long global_level_chunk(psms_ctx *c, const double2 *U, const double2 *Up, int N, int i0, int n,
+                                    int mode, uint64_t seed, uint64_t counter, double tol, int inner,
+                                    double *h_delta) {
+    const Geom &g = c->g;
+    const long long V = g.V, fs = 12 * V;
+    Interp it = make_interp(c, U, Up, N, mode, inner != P64, "glb", i0, n);
+    Pair pr = pair_of(it, mode);
+    double2 *xi = (double2 *)scratch(c, "gl_xi", sizeof(double2) * fs * n);
+    double2 *v = (double2 *)scratch(c, "gl_v", sizeof(double2) * fs * n);
+    double2 *w = (double2 *)scratch(c, "gl_w", sizeof(double2) * fs * n);
+    noise(c, xi, n, seed, counter, PSMS_LEVEL_GLOBAL, 1, i0);
+    long long tot = one_minus_PQ(c, pr.a64, pr.a32, pr.bs, n, xi, v, tol, inner);
+    tot += inv_one_minus_PQ(c, pr.b64, pr.b32, pr.bs, n, v, w, tol, inner);
+    double *nw = (double *)scratch(c, "gl_nw", sizeof(double) * n);
+    double *nx = (double *)scratch(c, "gl_nx", sizeof(double) * n);
+    norm2_batch(c, P64, View<void>{w, V, 0, fs}, 0, V, n, nw);
+    norm2_batch(c, P64, View<void>{xi, V, 0, fs}, 0, V, n, nx);
+    std::vector<double> a(n), b(n);
+    cuda_check(cudaMemcpyAsync(a.data(), nw, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "gl");
+    cuda_check(cudaMemcpyAsync(b.data(), nx, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "gl");
+    cuda_check(cudaStreamSynchronize(c->stream), "gl");
+    for (int i = 0; i < n; ++i) h_delta[i0 + i] = a[i] - b[i];
+    return tot;
+}
+
 long long global_level(psms_ctx *c, const double2 *U, const double2 *Up, int N, int mode, uint64_t seed,
                        uint64_t counter, double tol, int inner, double *d_delta) {
-    const Geom &g = c->g;
-    if (!g.coloured) fail(PSMS_EINVAL, "the Schur complement needs an even number of blocks in every direction");
-    const long long V = g.V, fs = 12 * V;
-    Interp it = make_interp(c, U, Up, N, mode, inner != P64, "glb");
-    Pair pr = pair_of(it, mode);
-    double2 *xi = (double2 *)scratch(c, "gl_xi", sizeof(double2) * fs * N);
-    double2 *v = (double2 *)scratch(c, "gl_v", sizeof(double2) * fs * N);
-    double2 *w = (double2 *)scratch(c, "gl_w", sizeof(double2) * fs * N);
-    noise(c, xi, N, seed, counter, PSMS_LEVEL_GLOBAL, 1);
-    long long tot = one_minus_PQ(c, pr.a64, pr.a32, pr.bs, N, xi, v, tol, inner);
-    tot += inv_one_minus_PQ(c, pr.b64, pr.b32, pr.bs, N, v, w, tol, inner);
-    double *nw = (double *)scratch(c, "gl_nw", sizeof(double) * N);
-    double *nx = (double *)scratch(c, "gl_nx", sizeof(double) * N);
-    norm2_batch(c, P64, View<void>{w, V, 0, fs}, 0, V, N, nw);
-    norm2_batch(c, P64, View<void>{xi, V, 0, fs}, 0, V, N, nx);
-    std::vector<double> a(N), b(N);
-    cuda_check(cudaMemcpyAsync(a.data(), nw, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream), "gl");
-    cuda_check(cudaMemcpyAsync(b.data(), nx, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream), "gl");
-    cuda_check(cudaStreamSynchronize(c->stream), "gl");
-    for (int i = 0; i < N; ++i) a[i] -= b[i];
-    cuda_check(cudaMemcpyAsync(d_delta, a.data(), sizeof(double) * N, cudaMemcpyHostToDevice, c->stream), "gl");
+    if (!c->g.coloured) fail(PSMS_EINVAL, "the Schur complement needs an even number of blocks in every direction");
+    const int ch = chunk_size(c, N, inner == P64 ? 4600.0 : 3700.0);
+    std::vector<double> h(N);
+    long long tot = 0;
+    for (int i0 = 0; i0 < N; i0 += ch)
+        tot += global_level_chunk(c, U, Up, N, i0, std::min(ch, N - i0), mode, seed, counter, tol, inner, h.data());
+    cuda_check(cudaMemcpyAsync(d_delta, h.data(), sizeof(double) * N, cudaMemcpyHostToDevice, c->stream), "gl");
     cuda_check(cudaStreamSynchronize(c->stream), "gl");
     return tot;
 }

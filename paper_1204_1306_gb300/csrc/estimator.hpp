@@ -6,7 +6,7 @@
 namespace psms {
 
 // noise fields xi_i (i = 0..n-1) for `level`, FP64 full layout, optional P projection
-void noise(psms_ctx *c, double2 *out, int n, uint64_t seed, uint64_t counter, int level, int proj);
+void noise(psms_ctx *c, double2 *out, int n, uint64_t seed, uint64_t counter, int level, int proj, int i0);
 // d_delta[b * N + i] (b = lexicographic block index); returns total inner iterations
 long long block_level(psms_ctx *c, const double2 *U, const double2 *Up, int N, int mode, uint64_t seed,
                       uint64_t counter, double tol, int inner, double *d_delta);

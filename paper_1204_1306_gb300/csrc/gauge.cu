@@ -330,8 +330,8 @@ int gauge_sweep(psms_ctx *c, double2 *U, int active_set, int n_iter, int n_or, d
             const Sub &q = subs[rev ? subs.size() - 1 - i : i];
             cm_update_kernel<<<nb, NT, 0, c->stream>>>(g, c->d_binfo, U, q.mu, q.p, q.colour, all, beta, kind, seed,
                                                        sid, failed);
+            PSMS_LAUNCH_CHECK("cm_update_kernel");
         }
-        PSMS_LAUNCH_CHECK("cm_update");
     };
     uint64_t s = sweep0;
     for (int it = 0; it < n_iter; ++it) {

@@ -703,6 +703,7 @@ static void inner_cg_full(psms_ctx *c, int n_sys, const void *Uin, long long U_b
             h.partial = p_a;
             hop_launch(c, h);
             cg_alpha_kernel<256><<<n_sys, 256, 0, c->stream>>>(st, p_a, nct);
+            PSMS_LAUNCH_CHECK("cg_alpha_kernel");
             // sv = Dhat^dag q
             h.dag = 1;
             h.p = 0;
@@ -722,7 +723,9 @@ static void inner_cg_full(psms_ctx *c, int n_sys, const void *Uin, long long U_b
             hop_launch(c, h);
             cg_update_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, tv(e), tv(pp), tv(q), tv(rho), tv(res), tv(sv), Vh,
                                                                  n, u_rr, u_rho, 0);
+            PSMS_LAUNCH_CHECK("cg_update_kernel");
             cg_beta_kernel<256><<<n_sys, 256, 0, c->stream>>>(st, u_rr, u_rho, nb, maxit, flags);
+            PSMS_LAUNCH_CHECK("cg_beta_kernel");
             cg_pupdate_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, tv(pp), tv(res), Vh, n);
             PSMS_LAUNCH_CHECK("cg iteration");
         }
@@ -735,6 +738,7 @@ static void inner_cg_full(psms_ctx *c, int n_sys, const void *Uin, long long U_b
         chunk = std::min(chunk * 2, 64);
     }
     iters_kernel<<<(n_sys + 63) / 64, 64, 0, c->stream>>>(st, iters_acc, n_sys);
+    PSMS_LAUNCH_CHECK("iters_kernel");
     // e_e = (rhs_e + H_e(e_o)/2)/A
     h.active = act_in;
     h.dag = 0;
@@ -770,6 +774,7 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
         cuda_check(cudaMemsetAsync((char *)q.x.p + sizeof(double2) * k * q.x.bs, 0, sizeof(double2) * 12 * V, c->stream),
                    "zero x");
     set_int_kernel<<<(n + 63) / 64, 64, 0, c->stream>>>(iters, 0, n);
+    PSMS_LAUNCH_CHECK("set_int_kernel");
     const double delta = in64 ? std::max(0.1 * q.tol, 1e-15) : (q.inner_prec == P32 ? 2e-6 : 5e-3);
     const int max_outer = in64 ? 6 : 30;
     std::vector<int> hact(n);
@@ -794,6 +799,7 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
         hop_launch(c, h);
         norm2_batch(c, P64, r, 0, V, n, rn);
         residual_flags_kernel<<<(n + 63) / 64, 64, 0, c->stream>>>(rn, bn, q.tol, act, rel, n);
+        PSMS_LAUNCH_CHECK("residual_flags_kernel");
         cuda_check(cudaMemcpyAsync(hact.data(), act, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream), "act");
         cuda_check(cudaStreamSynchronize(c->stream), "solve sync");
         bool any = false;
@@ -804,24 +810,30 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
         if (in64) {
             scale_convert_kernel<Store<double>, NT><<<grid, NT, 0, c->stream>>>(
                 View<double2>{(double2 *)rin_p, V, 0, 12 * V}, r2, rn, 1, act, 0, V);
+            PSMS_LAUNCH_CHECK("scale_convert_kernel");
             inner_cg_full<Store<double>>(c, n, q.U64, q.U64_bs, P64, rin, ein, act, delta, q.maxit, iters);
             accumulate_kernel<Store<double>, NT><<<grid, NT, 0, c->stream>>>(
                 View<double2>{(double2 *)q.x.p, q.x.cs, q.x.off, q.x.bs}, View<double2>{(double2 *)ein_p, V, 0, 12 * V},
                 rn, act, 0, V);
+            PSMS_LAUNCH_CHECK("accumulate_kernel");
         } else if (q.inner_prec == P32) {
             scale_convert_kernel<Store<float>, NT><<<grid, NT, 0, c->stream>>>(
                 View<float2>{(float2 *)rin_p, V, 0, 12 * V}, r2, rn, 1, act, 0, V);
+            PSMS_LAUNCH_CHECK("scale_convert_kernel");
             inner_cg_full<Store<float>>(c, n, q.U32, q.U64_bs, P32, rin, ein, act, delta, q.maxit, iters);
             accumulate_kernel<Store<float>, NT><<<grid, NT, 0, c->stream>>>(
                 View<double2>{(double2 *)q.x.p, q.x.cs, q.x.off, q.x.bs}, View<float2>{(float2 *)ein_p, V, 0, 12 * V},
                 rn, act, 0, V);
+            PSMS_LAUNCH_CHECK("accumulate_kernel");
         } else {
             scale_convert_kernel<Store<__nv_bfloat16>, NT><<<grid, NT, 0, c->stream>>>(
                 View<__nv_bfloat162>{(__nv_bfloat162 *)rin_p, V, 0, 12 * V}, r2, rn, 1, act, 0, V);
+            PSMS_LAUNCH_CHECK("scale_convert_kernel");
             inner_cg_full<Store<__nv_bfloat16>>(c, n, q.U32, q.U64_bs, PB16, rin, ein, act, delta, q.maxit, iters);
             accumulate_kernel<Store<__nv_bfloat16>, NT><<<grid, NT, 0, c->stream>>>(
                 View<double2>{(double2 *)q.x.p, q.x.cs, q.x.off, q.x.bs},
                 View<__nv_bfloat162>{(__nv_bfloat162 *)ein_p, V, 0, 12 * V}, rn, act, 0, V);
+            PSMS_LAUNCH_CHECK("accumulate_kernel");
         }
         PSMS_LAUNCH_CHECK("defect correction");
     }
