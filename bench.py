@@ -172,6 +172,26 @@ def measure_dw(ps, ctx, torch, reps=20):
     return out
 
 
+def dw_only(args):
+    """Stand-alone D_w on the workload lattice (about 4 GB on the device):
+    the small case used for Nsight Compute captures of the hop kernel."""
+    import torch
+
+    import paper_1204_1306_gb300 as ps
+    from paper_1204_1306_gb300 import build as _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    wl = WORKLOADS[args.workload]
+    ctx = ps.psms_create(wl["dims"], wl["block"], wl["kappa"], 1)
+    ps.psms_set_stream(ctx, torch.cuda.current_stream())
+    ps.psms_gauge_init(ctx, 0, wl["eps"], SEED + 4)
+    dw = measure_dw(ps, ctx, torch, reps=args.steps)
+    peak, kind = peaks()
+    print(json.dumps({"workload": args.workload, "dw": dw, "peak_gbs": peak, "peak_kind": kind,
+                      "frac": {k: round(v["GB/s"] / peak, 4) for k, v in dw.items()}}), flush=True)
+
+
 def our_arm(args):
     import torch
 
@@ -383,11 +403,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="32^3x64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dw-only", action="store_true", help="stand-alone D_w measurement only")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         reference_arm(args)
+    elif args.dw_only:
+        dw_only(args)
     else:
         our_arm(args)
 
