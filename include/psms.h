@@ -221,6 +221,32 @@ psms_status psms_profile_enable(psms_ctx *ctx, int enable);
 psms_status psms_profile_read(psms_ctx *ctx, long long *launches, double *total_ms,
                               double *bytes_per_launch_sum);
 
+/* Dirichlet block solve that allocates no memory.  The paper has no
+ * counterpart: this is a deployment variant of psms_solve for op =
+ * PSMS_OP_BLOCKS or a single block index, with FP64 inner iterations.
+ *
+ * For callers that must not allocate while they run (a fixed memory pool,
+ * a host that reserved all device memory up front, or code that cannot let
+ * cudaMalloc / cudaFree synchronise the device): its scratch is one static
+ * device array of 32 MiB inside the library, held by every GPU that loads
+ * the library until the process exits.  The call makes no cudaMalloc,
+ * cudaFree or other allocating call; b_dev / x_dev are caller-owned native
+ * FP64 buffers, x outside the selected blocks is set to zero.
+ *  - Lattices needing more scratch than the array holds (about 26,000 sites)
+ *    are rejected with PSMS_EINVAL and a message giving both sizes.
+ *  - The first call on a device looks up the array's device address with
+ *    that device current (cudaGetSymbolAddress) and caches it; make that
+ *    first call outside any stream capture.
+ *  - Every call shares the one array and the kernel initialises all of it
+ *    that it reads, so nothing carries over between calls; but calls whose
+ *    work overlaps on the GPU (other streams, other threads, other contexts
+ *    on the same device) race on the array and must be serialised.
+ * iters_out: total inner iterations over the blocks; resid_out: largest
+ * relative true residual (both host, may be NULL).  PSMS_ENOCONV if a block
+ * misses tol within maxit iterations. */
+psms_status psms_block_solve_noalloc(psms_ctx *ctx, int field, int op, const void *b_dev, void *x_dev, double tol,
+                                     int maxit, long long *iters_out, double *resid_out);
+
 /* Number of CUDA kernels the library has launched in this process. */
 long long psms_kernel_launches(void);
 

@@ -17,7 +17,7 @@ __all__ = [
     "psms_gauge_init", "psms_gauge_set", "psms_gauge_get", "psms_gauge_copy", "psms_plaquette",
     "psms_gauge_sweep", "psms_gauge_translate", "psms_spinor_bytes", "psms_spinor_import",
     "psms_spinor_export", "psms_dw_apply", "psms_solve", "psms_logdet_ratio", "psms_filter_step",
-    "psms_profile_enable", "psms_profile_read",
+    "psms_profile_enable", "psms_profile_read", "psms_block_solve_noalloc",
     "PREC_F64", "PREC_F32", "PREC_BF16", "OP_FULL", "OP_BLOCKS", "ACTIVE_BLOCKS", "ACTIVE_ALL",
     "LEVEL_BLOCK", "LEVEL_GLOBAL", "EST_INTERP", "EST_INDEPENDENT",
 ]
@@ -88,6 +88,8 @@ _SIGS = {
     "psms_logdet_ratio": [_P, _I, _I, _I, _I, _I, _U64, _U64, _D, _I, ctypes.POINTER(_D)],
     "psms_filter_step": [_P, _I, ctypes.POINTER(FilterParams), ctypes.POINTER(FilterResult),
                          ctypes.POINTER(_D), ctypes.POINTER(_I)],
+    "psms_block_solve_noalloc": [_P, _I, _I, _P, _P, _D, _I, ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(_D)],
     "psms_profile_enable": [_P, _I],
     "psms_profile_read": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), ctypes.POINTER(_D)],
 }
@@ -263,6 +265,14 @@ def psms_filter_step(ctx, field, *, beta0, n_iter=1, n_or=0, n_block=4, n_global
             "solver_iters": r.solver_iters, "hb_failed": r.hb_failed,
             "delta_block": np.frombuffer(db, dtype=np.float64).copy(),
             "accept_block": np.frombuffer(ab, dtype=np.int32).astype(bool)}
+
+
+def psms_block_solve_noalloc(ctx, field, op, b_dev, x_dev, tol, maxit):
+    """Block solve with the library's static scratch (no device allocation)."""
+    it, res = ctypes.c_longlong(), _D()
+    ctx.check(ctx.lib.psms_block_solve_noalloc(ctx.handle, field, op, _ptr(b_dev), _ptr(x_dev), float(tol),
+                                               int(maxit), ctypes.byref(it), ctypes.byref(res)))
+    return {"inner_iters": it.value, "true_residual": res.value}
 
 
 def psms_profile_enable(ctx, enable):

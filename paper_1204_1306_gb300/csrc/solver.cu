@@ -860,3 +860,146 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
 }
 
 }  // namespace psms
+
+// ---------------------------------------------------------------------------
+// Dirichlet block solve that allocates nothing.
+//
+// Some callers cannot allocate device memory while they run: code inside a
+// memory pool that must not grow, real-time or embedded hosts that reserve
+// all memory up front, and callers holding other allocations that a
+// cudaMalloc/cudaFree (which synchronise the device) must not disturb.  For
+// them the block solve below takes its scratch from one file-scope device
+// array of fixed size instead of the context's growable scratch buffers.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace psms {
+
+// Capacity of the static scratch: FP64 residual (12 V complex), the FP64
+// inner vectors (66 V complex) and three per-block result arrays.
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+static void *g_noalloc_addr[256];
+static std::mutex g_noalloc_mutex;
+
+// Device address of the static scratch on the current device.  Host code
+// sees only a host-side stand-in for the array, so the address is looked up
+// once per device with that device current and cached.
+static void *noalloc_scratch_address() {
+    int dev = 0;
+    cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= 256) fail(PSMS_EINVAL, "device index out of range for the no-allocation scratch");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(no-allocation scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    return g_noalloc_addr[dev];
+}
+
+static size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// sums / maxima of the per-block results into out[0] (iterations),
+// out[1] (max residual) and out[2] (status, as double)
+__global__ void noalloc_summary_kernel(const int *iters, const double *resid, const int *status, int n, double *out) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double it = 0, worst = 0, st = 0;
+    for (int i = 0; i < n; ++i) {
+        it += iters[i];
+        worst = resid[i] > worst ? resid[i] : worst;
+        st = status[i] ? 1.0 : st;
+    }
+    out[0] = it;
+    out[1] = worst;
+    out[2] = st;
+}
+
+}  // namespace psms
+
+extern "C" psms_status psms_block_solve_noalloc(psms_ctx *ctx, int field, int op, const void *b_dev, void *x_dev,
+                                                double tol, int maxit, long long *iters_out, double *resid_out) {
+    using namespace psms;
+    if (!ctx) return PSMS_EINVAL;
+    try {
+        check_field(ctx, field);
+        if (!b_dev || !x_dev || b_dev == x_dev) fail(PSMS_EINVAL, "b / x must be distinct non-null buffers");
+        if (!(tol > 0) || maxit < 1) fail(PSMS_EINVAL, "tol must be > 0 and maxit >= 1");
+        const Geom &g = ctx->g;
+        const long long V = g.V;
+        int lo = 0, nr = g.nblocks;
+        if (op != PSMS_OP_BLOCKS) {
+            if (op < 0 || op >= g.nblocks) fail(PSMS_EINVAL, "op must be PSMS_OP_BLOCKS or a block index");
+            int B[4], rem = op;
+            for (int m = 3; m >= 0; --m) {
+                B[m] = rem % g.nb[m];
+                rem /= g.nb[m];
+            }
+            lo = rank_of_lex(g, op, B);
+            nr = 1;
+        }
+        const size_t r64_bytes = align256(sizeof(double2) * 12 * (size_t)V);
+        const long long per_sys = 24 * V + 7 * 12 * (long long)g.Vh;
+        const size_t inner_bytes = align256(sizeof(double2) * (size_t)per_sys);
+        const size_t res_bytes = align256(sizeof(int) * nr) + align256(sizeof(double) * nr) +
+                                 align256(sizeof(int) * nr) + align256(sizeof(double) * 3);
+        const size_t need = r64_bytes + inner_bytes + res_bytes;
+        if (need > NOALLOC_SCRATCH_BYTES)
+            fail(PSMS_EINVAL, "lattice too large for psms_block_solve_noalloc: needs " + std::to_string(need) +
+                                  " bytes of scratch, the static array holds " +
+                                  std::to_string(NOALLOC_SCRATCH_BYTES) + " (about 26,000 sites)");
+        unsigned char *base = (unsigned char *)noalloc_scratch_address();
+        double2 *r64 = (double2 *)base;
+        void *vin = base + r64_bytes;
+        unsigned char *rp = base + r64_bytes + inner_bytes;
+        int *iters = (int *)rp;
+        rp += align256(sizeof(int) * nr);
+        double *resid = (double *)rp;
+        rp += align256(sizeof(double) * nr);
+        int *status = (int *)rp;
+        rp += align256(sizeof(int) * nr);
+        double *summary = (double *)rp;
+        // blocks outside op keep x = 0; the kernel zeroes and writes x inside them
+        cuda_check(cudaMemsetAsync(x_dev, 0, sizeof(double2) * 12 * (size_t)V, ctx->stream), "no-alloc memset");
+        BlockSolveArgs a;
+        a.g = g;
+        a.binfo = ctx->d_binfo;
+        a.A = ctx->A;
+        a.rank_lo = lo;
+        a.n_ranks = nr;
+        a.b = View<double2>{(double2 *)b_dev, V, 0, 12 * V};
+        a.x = View<double2>{(double2 *)x_dev, V, 0, 12 * V};
+        a.r64 = View<double2>{r64, V, 0, 12 * V};
+        a.U64 = ctx->U64[field];
+        a.U64_bs = 0;
+        a.Uin = ctx->U64[field];
+        a.Uin_bs = 0;
+        a.vin = vin;
+        a.vin_bs = per_sys;
+        a.tol = tol;
+        a.delta = std::max(0.1 * tol, 1e-15);
+        a.maxit = maxit;
+        a.max_outer = 4;
+        a.sys_active = nullptr;
+        a.iters = iters;
+        a.resid = resid;
+        a.xnorm2 = nullptr;
+        a.status = status;
+        const int NT = 128;
+        block_solve_kernel<Store<double>, Store<double>, NT><<<dim3(nr, 1), NT, 0, ctx->stream>>>(a);
+        PSMS_LAUNCH_CHECK("block_solve_kernel (no allocation)");
+        noalloc_summary_kernel<<<1, 1, 0, ctx->stream>>>(iters, resid, status, nr, summary);
+        PSMS_LAUNCH_CHECK("noalloc_summary_kernel");
+        double h[3] = {0, 0, 0};
+        cuda_check(cudaMemcpyAsync(h, summary, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream), "no-alloc summary");
+        cuda_check(cudaStreamSynchronize(ctx->stream), "no-alloc sync");
+        if (iters_out) *iters_out = (long long)h[0];
+        if (resid_out) *resid_out = h[1];
+        if (h[2] != 0.0) fail(PSMS_ENOCONV, "a block solve missed its tolerance");
+    } catch (const Error &e) {
+        ctx->err = e.msg;
+        return e.st;
+    }
+    return PSMS_OK;
+}
