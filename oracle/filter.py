@@ -47,6 +47,7 @@ class FilterParams:
     beta_global: float = 0.0
     tol: float = 1e-13
     global_level: bool = True
+    learned: object = None   # MLP parameter dict (oracle.mlp) or None
 
 
 def gaussian_acceptance(sigma2):
@@ -101,17 +102,38 @@ def per_block_action_change(U, Up, geom):
     return out
 
 
-def filter_step(U, geom, prm, seed, step):
-    """Returns (new field, record dict)."""
+def filter_step(U, geom, prm, seed, step, h_override=None):
+    """Returns (new field, record dict).
+
+    With prm.learned (per-block decisions only) a learned level precedes
+    level 1: h_b from the surrogate (or h_override, the values a device
+    computed, so that both sides decide on the same numbers), accepted with
+    min{1, exp(-h_b)} (counter (step, 3, b)); level 1 runs on the blocks that
+    passed, with Delta_b - h_b."""
     active = geom.active_links()
     Unew, _, failed = domain_sweep(U, geom, prm.beta0, prm.n_iter, prm.n_or, seed, step * SWEEP_STRIDE)
+    per_block = min(geom.block) >= 3
+    passed = np.ones(geom.n_blocks, dtype=bool)
+    h = np.zeros(geom.n_blocks)
+    rec_h = None
+    if prm.learned is not None:
+        from .mlp import antisym, domain_features
+        assert per_block
+        z = np.concatenate([domain_features(U, geom), domain_features(Unew, geom)], axis=1)
+        h = antisym(prm.learned, z) if h_override is None else np.asarray(h_override, dtype=np.float64)
+        passed = np.array([accept(h[b], philox.accept_uniform(seed, step, 3, b)) for b in range(geom.n_blocks)])
+        rec_h = h
 
-    d_blk = block_level(U, Unew, geom, prm.kappa, prm.n_block, seed, step, tol=prm.tol).sum(axis=1)
+    blocks = [b for b in range(geom.n_blocks) if passed[b]]
+    d_blk = np.zeros(geom.n_blocks)
+    if blocks:
+        d_all = block_level(U, Unew, geom, prm.kappa, prm.n_block, seed, step, tol=prm.tol, blocks=blocks)
+        d_blk[blocks] = d_all[blocks].sum(axis=1)
     if prm.beta_block != 0.0:
         d_blk = d_blk + prm.beta_block * per_block_action_change(U, Unew, geom)
-    per_block = min(geom.block) >= 3
+    d_blk = d_blk - h
     if per_block:
-        acc_b = np.array([accept(d_blk[b], philox.accept_uniform(seed, step, 1, b))
+        acc_b = np.array([passed[b] and accept(d_blk[b], philox.accept_uniform(seed, step, 1, b))
                           for b in range(geom.n_blocks)])
     else:
         a = accept(d_blk.sum(), philox.accept_uniform(seed, step, 1, 0))
@@ -121,7 +143,8 @@ def filter_step(U, geom, prm, seed, step):
     link_block_acc = acc_b[geom.block_index][..., None] & active
     Umid[link_block_acc] = Unew[link_block_acc]
 
-    rec = {"delta_block": d_blk, "accept_block": acc_b, "hb_failed": failed}
+    rec = {"delta_block": d_blk, "accept_block": acc_b, "hb_failed": failed, "h": rec_h,
+           "passed_learned": passed}
     Ufin = Umid
     if prm.global_level:
         dg = global_level(U, Umid, geom, prm.kappa, prm.n_global, seed, step, tol=prm.tol)

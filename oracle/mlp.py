@@ -18,7 +18,8 @@ for the planes k = (0,1), (0,2), (0,3), (1,2), (1,3), (2,3).
 
 Network input z = [f(U_b), f(U'_b)] (64), standardised with a mean / scale
 vector; h1 = relu(W1 z + b1), h2 = relu(W2 h1 + b2), n = w3 . h2 + b3;
-h = (n(f, f') - n(f', f)) / 2.  Loss: mean squared error to Delta_b.
+h = ys (n(f, f') - n(f', f)) / 2 with an output scale ys.  Loss: mean
+squared error to Delta_b.
 """
 import numpy as np
 
@@ -87,7 +88,7 @@ def init_params(seed, n_in=2 * N_FEAT, hidden=HIDDEN):
         "W1": g.standard_normal((hidden, n_in)) * np.sqrt(2.0 / n_in), "b1": np.zeros(hidden),
         "W2": g.standard_normal((hidden, hidden)) * np.sqrt(2.0 / hidden), "b2": np.zeros(hidden),
         "w3": g.standard_normal(hidden) * np.sqrt(1.0 / hidden), "b3": 0.0,
-        "mu": np.zeros(n_in), "sigma": np.ones(n_in),
+        "mu": np.zeros(n_in), "sigma": np.ones(n_in), "ys": 1.0,
     }
 
 
@@ -121,21 +122,99 @@ def swap(z):
 
 
 def antisym(p, z):
-    """h(z) = (n(f, f') - n(f', f)) / 2."""
+    """h(z) = ys (n(f, f') - n(f', f)) / 2."""
     a, _ = forward(p, z)
     b, _ = forward(p, swap(z))
-    return 0.5 * (a - b)
+    return p.get("ys", 1.0) * 0.5 * (a - b)
 
 
 def loss_and_grad(p, z, y):
     """Mean squared error of h against labels y and its gradient."""
+    ys = p.get("ys", 1.0)
     a, ca = forward(p, z)
     b, cb = forward(p, swap(z))
-    h = 0.5 * (a - b)
+    h = ys * 0.5 * (a - b)
     r = h - y
     loss = float(np.mean(r * r))
     dh = 2.0 * r / len(y)
-    ga = backward(p, ca, 0.5 * dh)
-    gb = backward(p, cb, -0.5 * dh)
+    ga = backward(p, ca, 0.5 * ys * dh)
+    gb = backward(p, cb, -0.5 * ys * dh)
     grads = {k: ga[k] + gb[k] for k in ga}
     return loss, grads
+
+
+# flat parameter block of the CUDA path: W1[256][64], b1, W2[256][256], b2,
+# w3, b3, mu[64], sigma[64], ys
+def unflatten(v):
+    v = np.asarray(v, dtype=np.float64)
+    o = 0
+
+    def take(n, shape=None):
+        nonlocal o
+        a = v[o:o + n]
+        o += n
+        return a.reshape(shape) if shape else a
+    p = {"W1": take(HIDDEN * 64, (HIDDEN, 64)), "b1": take(HIDDEN), "W2": take(HIDDEN * HIDDEN, (HIDDEN, HIDDEN)),
+         "b2": take(HIDDEN), "w3": take(HIDDEN), "b3": float(take(1)[0]), "mu": take(64), "sigma": take(64),
+         "ys": float(take(1)[0])}
+    return p
+
+
+def flatten_grads(g):
+    return np.concatenate([g["W1"].ravel(), g["b1"], g["W2"].ravel(), g["b2"], g["w3"], [g["b3"]]])
+
+
+# --- the device's precision --------------------------------------------------
+# The CUDA path rounds the standardised input, the weights W1, W2 and the
+# first hidden activation to BF16 (round to nearest even) and accumulates in
+# FP32; in the backward pass the GEMM operands D2, D1 and X are rounded to
+# BF16 as well.  These functions apply the same roundings (accumulating in
+# FP64), so that the device's arithmetic can be checked at its own precision;
+# the FP64 functions above remain the definition.
+
+def bf16(x):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+def forward_rounded(p, z):
+    x = _f32((_f32(z) - _f32(p["mu"])) / _f32(p["sigma"]))
+    h1 = np.maximum(bf16(x) @ bf16(p["W1"]).T + _f32(p["b1"]), 0.0)
+    h2 = np.maximum(bf16(h1) @ bf16(p["W2"]).T + _f32(p["b2"]), 0.0)
+    n = h2 @ _f32(p["w3"]) + float(np.float32(p["b3"]))
+    return n, (x, h1, h2)
+
+
+def antisym_rounded(p, z):
+    a, _ = forward_rounded(p, z)
+    b, _ = forward_rounded(p, swap(z))
+    return float(np.float32(p.get("ys", 1.0))) * 0.5 * (a - b)
+
+
+def loss_and_grad_rounded(p, z, y):
+    ys = float(np.float32(p.get("ys", 1.0)))
+    a, (xa, h1a, h2a) = forward_rounded(p, z)
+    b, (xb, h1b, h2b) = forward_rounded(p, swap(z))
+    h = ys * 0.5 * (a - b)
+    r = h - y
+    loss = float(np.mean(r * r))
+    d = ys * r / len(y)
+    dn = np.concatenate([d, -d])
+    X = np.concatenate([xa, xb])
+    H1 = np.concatenate([h1a, h1b])
+    H2 = np.concatenate([h2a, h2b])
+    g = {"w3": H2.T @ dn, "b3": float(dn.sum())}
+    D2 = np.outer(dn, _f32(p["w3"])) * (H2 > 0)
+    g["W2"] = bf16(D2).T @ bf16(H1)
+    g["b2"] = D2.sum(axis=0)
+    D1 = (bf16(D2) @ bf16(p["W2"])) * (H1 > 0)
+    g["W1"] = bf16(D1).T @ bf16(X)
+    g["b1"] = D1.sum(axis=0)
+    return loss, g

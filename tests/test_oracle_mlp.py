@@ -98,3 +98,18 @@ def test_surrogate_antisymmetric():
     p = mlp.init_params(3)
     z = np.random.default_rng(1).standard_normal((5, 64))
     assert np.allclose(mlp.antisym(p, z), -mlp.antisym(p, mlp.swap(z)))
+
+
+def test_bf16_rounding_model():
+    """bf16(): round to nearest even on the 16 dropped bits."""
+    assert mlp.bf16(1.0) == 1.0
+    assert mlp.bf16(1.0 + 2 ** -8) == 1.0 + 2 ** -7 or mlp.bf16(1.0 + 2 ** -8) == 1.0
+    assert mlp.bf16(1.0 + 2 ** -8) == 1.0           # tie -> even
+    assert mlp.bf16(1.0 + 3 * 2 ** -8) == 1.0 + 2 ** -6  # tie -> even (up)
+    assert mlp.bf16(1.0 + 2 ** -7) == 1.0 + 2 ** -7
+    x = np.random.default_rng(0).standard_normal(1000)
+    assert np.all(np.abs(mlp.bf16(x) - x) <= 2 ** -8 * np.abs(x))
+    p = mlp.init_params(2)
+    z = np.random.default_rng(3).standard_normal((20, 64))
+    a, b = mlp.antisym(p, z), mlp.antisym_rounded(p, z)
+    assert np.linalg.norm(a - b) <= 0.25 * np.linalg.norm(a)
