@@ -14,6 +14,8 @@ instead (bounded sample, extrapolated, see `reference_arm`).
 import argparse
 import json
 import math
+
+import numpy as np
 import os
 import statistics
 import subprocess
@@ -140,6 +142,108 @@ def allsum(ws, v):
     return float(t.item())
 
 
+def roofline_entry(kernel, n, ms, nbytes, peak, peak_kind):
+    """achieved = algorithmic bytes of the kernel's launches in the timed steps
+    / their summed CUDA-event durations (on the library's stream)."""
+    achieved = nbytes / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    return {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind, "launches": n,
+            "avg_launch_ms": round(ms / max(n, 1), 4), "total_ms": round(ms, 2)}
+
+
+def compare_16(ps, torch, steps=6, warmup=2):
+    """Config 2 scale (16^4, 4^4 domains, kappa 0.156, eps 0.5): the plain FP64
+    hierarchy against FP32-inner mixed precision and against mixed precision
+    with the learned level, on identical proposals and noise (N = 48 at the
+    block level, 12 at the global level, solves to 1e-12).  Reports accepted
+    updates/s (global accept with at least one block changed), accepted
+    blocks/s, and the largest estimate difference to the FP64 hierarchy."""
+    dims, block, kappa = (16, 16, 16, 16), (4, 4, 4, 4), 0.156
+    prm = dict(beta0=5.3, n_iter=1, n_or=1, n_block=48, n_global=12, tol=1e-12, seed=SEED + 1)
+    out = {}
+    ref = None
+    for name, inner, learned in (("plain_fp64", ps.PREC_F64, False), ("mixed", ps.PREC_F32, False),
+                                 ("learned_mixed", ps.PREC_F32, True)):
+        ctx = ps.psms_create(dims, block, kappa, 2)
+        ps.psms_set_stream(ctx, torch.cuda.current_stream())
+        ps.psms_gauge_init(ctx, 0, 0.5, SEED + 1)
+        ps.psms_gauge_sweep(ctx, 0, ps.ACTIVE_ALL, 4, 2, 5.3, SEED, 1 << 40)
+        train_s = 0.0
+        if learned:
+            t0 = time.perf_counter()
+            train_learned(ps, torch, ctx, 24)
+            train_s = time.perf_counter() - t0
+        recs = []
+        for i in range(warmup):
+            ps.psms_filter_step(ctx, 0, inner_prec=inner, learned=learned, step=10_000 + i, **prm)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(steps):
+            recs.append(ps.psms_filter_step(ctx, 0, inner_prec=inner, learned=learned, step=i, **prm))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        acc = sum(1 for r in recs if r["accept_global"] and r["n_accept_blocks"] > 0)
+        blocks = sum(r["n_accept_blocks"] for r in recs if r["accept_global"])
+        out[name] = {"s_per_step": wall / steps, "accepted_updates_per_s": acc / wall,
+                     "accepted_blocks_per_s": blocks / wall, "global_acceptance": acc / steps,
+                     "learned_pass": (sum(r["n_accept_learned"] for r in recs) / (steps * r["n_blocks"])
+                                      if learned else None), "train_s": train_s}
+        if name == "plain_fp64":
+            ref = recs
+        elif not learned:
+            # same proposals, same noise: differences are solver precision
+            db = max(float(np.abs(a["delta_block"] - b["delta_block"]).max()) for a, b in zip(recs, ref))
+            dg = max(abs(a["delta_global"] - b["delta_global"]) for a, b in zip(recs, ref))
+            out[name]["max_estimate_error_vs_fp64"] = max(db, dg)
+        ctx.close()
+    out["speedup_learned_mixed_vs_fp64"] = (out["plain_fp64"]["s_per_step"] /
+                                           max(out["learned_mixed"]["s_per_step"], 1e-12))
+    out["speedup_mixed_vs_fp64"] = out["plain_fp64"]["s_per_step"] / max(out["mixed"]["s_per_step"], 1e-12)
+    return out
+
+
+def train_learned(ps, torch, ctx, n_props, n_interp=48):
+    """Train the learned level on block log-det-ratio estimates the method
+    generates for domain-sweep proposals of the current field."""
+    nb = ps.psms_geometry_info(ctx)[0]
+    zs, ys = [], []
+    zb = torch.zeros(nb * 64, dtype=torch.float32, device="cuda")
+    for s in range(n_props):
+        ps.psms_gauge_copy(ctx, 1, 0)
+        ps.psms_gauge_sweep(ctx, 1, ps.ACTIVE_BLOCKS, 1, 1, 5.3, SEED, (s + 7) << 20)
+        d = ps.psms_logdet_ratio(ctx, ps.LEVEL_BLOCK, 0, 1, n_interp, ps.EST_INTERP, SEED, 50_000 + s, 1e-10,
+                                 ps.PREC_F32)
+        ps.psms_domain_features_pair(ctx, 0, 1, zb)
+        zs.append(zb.view(nb, 64).clone())
+        ys.append(torch.from_numpy(d.sum(axis=1)))
+    z = torch.cat(zs).contiguous()
+    y = torch.cat(ys).to("cuda").contiguous()
+    ps.psms_mlp_init(ctx, 7)
+    return ps.psms_mlp_train(ctx, z, y, len(y), epochs=60, batch=256, lr=1e-3, weight_decay=1e-4, seed=3)
+
+
+def measure_heatbath(ps, ctx, torch, wl, reps=3):
+    """Domain sweep (Sec. 6) on the active links: link updates per second
+    (HB and OR sweeps each update every active link once) and the FP64
+    arithmetic rate at about 3000 flop per link update (6 staples of 2 SU(3)
+    products, 3 SU(2) subgroup updates), against GB300's nominal FP64 peak."""
+    _, _, n_active = ps.psms_geometry_info(ctx)
+    n_iter, n_or = 1, 2
+    sweeps = n_iter * (2 + 2 * n_or)
+    ps.psms_gauge_copy(ctx, 1, 0)
+    ps.psms_gauge_sweep(ctx, 1, ps.ACTIVE_BLOCKS, n_iter, n_or, wl["beta"], SEED, 7 << 40)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(reps):
+        ps.psms_gauge_sweep(ctx, 1, ps.ACTIVE_BLOCKS, n_iter, n_or, wl["beta"], SEED, (8 + i) << 40)
+    torch.cuda.synchronize()
+    s = (time.perf_counter() - t0) / reps
+    ups = n_active * sweeps / s
+    return {"active_links": n_active, "sweeps_per_call": sweeps, "s_per_call": round(s, 4),
+            "link_updates_per_s": round(ups, 1), "fp64_gflops_est": round(ups * 3000 / 1e9, 1),
+            "fp64_peak_gflops_nominal": 1250.0, "bound": "alu"}
+
+
 def measure_dw(ps, ctx, torch, reps=20):
     """Stand-alone full-lattice D_w (Eq. (Dw)) per precision: GB/s of the
     algorithmic bytes and GFLOP/s at 1320 flop/site, CUDA events on the
@@ -192,6 +296,106 @@ def dw_only(args):
                       "frac": {k: round(v["GB/s"] / peak, 4) for k, v in dw.items()}}), flush=True)
 
 
+def solve_only(args):
+    """Whole-lattice and all-blocks solves of one system on the workload
+    lattice (FP32 inner iterations, FP64 defect correction to the workload
+    tolerance), with the solvers' algorithmic bytes per Krylov iteration:
+      block CG iteration (per block, FP32): 4 half hops over the block
+        (in, out, 8 links per output site; y on the second hop of a pair) and
+        the vector updates (12 half-vector passes) = 4416 B per half-block site;
+      whole-lattice CG iteration: the same per half-lattice site.
+    This is the small case for Nsight Compute captures of the solver kernels."""
+    import torch
+
+    import paper_1204_1306_gb300 as ps
+    from paper_1204_1306_gb300 import build as _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    wl = WORKLOADS[args.workload]
+    ctx = ps.psms_create(wl["dims"], wl["block"], wl["kappa"], 1)
+    ps.psms_set_stream(ctx, torch.cuda.current_stream())
+    ps.psms_gauge_init(ctx, 0, wl["eps"], SEED + 4)
+    V = ctx.V
+    canon = torch.randn(V * 24, dtype=torch.float64, device="cuda")
+    b = torch.empty(ps.psms_spinor_bytes(ctx, ps.PREC_F64), dtype=torch.uint8, device="cuda")
+    x = torch.zeros_like(b)
+    ps.psms_spinor_import(ctx, canon, b, ps.PREC_F64)
+    peak, kind = peaks()
+    out = {"workload": args.workload, "peak_gbs": peak, "peak_kind": kind}
+    per_site = 4416.0
+    for name, op in (("blocks", ps.OP_BLOCKS), ("full", ps.OP_FULL)):
+        for _ in range(max(1, args.warmup - 2)):
+            ps.psms_solve(ctx, 0, op, b, x, wl["tol"], 20000, ps.PREC_F32)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        info = ps.psms_solve(ctx, 0, op, b, x, wl["tol"], 20000, ps.PREC_F32)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        its = info["inner_iters"]
+        # block iterations are summed over the blocks: one block iteration
+        # covers Vb/2 half-block sites; a whole-lattice iteration covers V/2
+        nblk = 1
+        if op == ps.OP_BLOCKS:
+            nblk = int(np.prod([d // l for d, l in zip(wl["dims"], wl["block"])]))
+        half_sites = (V / 2) / nblk
+        gbs = its * half_sites * per_site / (ms * 1e-3) / 1e9
+        out[name] = {"ms": round(ms, 2), "inner_iters": its, "true_residual": info["true_residual"],
+                     "algorithmic_GB/s": round(gbs, 1), "frac": round(gbs / peak, 4)}
+    print(json.dumps(out), flush=True)
+
+
+def batch_only(args):
+    """Config 3: all 4^4 Dirichlet blocks x 16 noise vectors of three uneven
+    lattices (8^4, 12^4, 16^3 x 32; kappa 0.155, eps 0.5) in one persistent
+    graph-captured launch, FP32 inner / FP64 refinement to 1e-10, autotuned
+    schedule.  Reports the batch time, the mean time a CTA spends per system,
+    and the aggregate algorithmic GB/s (4416 B per half-block site per block
+    CG iteration, FP32)."""
+    import torch
+
+    import paper_1204_1306_gb300 as ps
+    from paper_1204_1306_gb300 import build as _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    n_rhs = 16
+    probs = []
+    for i, dims in enumerate(((8, 8, 8, 8), (12, 12, 12, 12), (32, 16, 16, 16))):
+        ctx = ps.psms_create(dims, (4, 4, 4, 4), 0.155, 1)
+        ps.psms_gauge_init(ctx, 0, 0.5, SEED + 2 + i)
+        nb = ps.psms_spinor_bytes(ctx, ps.PREC_F64)
+        b = torch.empty(n_rhs * nb, dtype=torch.uint8, device="cuda")
+        for k in range(n_rhs):
+            canon = torch.randn(ctx.V * 24, dtype=torch.float64, device="cuda")
+            ps.psms_spinor_import(ctx, canon, b[k * nb:(k + 1) * nb], ps.PREC_F64)
+        probs.append((ctx, 0, n_rhs, b, torch.zeros_like(b)))
+    torch.cuda.synchronize()
+    plan = ps.psms_block_plan_create(probs, 1e-10, 20000, ps.PREC_F32)
+    for _ in range(args.warmup):
+        plan.run()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    infos = [plan.run(stream) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    sched = plan.schedule()
+    items = infos[0]["n_systems"]
+    iters = infos[0]["inner_iters"]
+    gbs = iters * 128 * 4416.0 / (ms * 1e-3) / 1e9
+    peak, kind = peaks()
+    print(json.dumps({"workload": "config3: 8^4 + 12^4 + 16^3x32, 4^4 blocks x 16 noises", "systems": items,
+                      "batch_ms": round(ms, 3), "cta_ms_per_system": round(ms * sched["ctas"] / items, 4),
+                      "block_cg_iterations": iters, "algorithmic_GB/s": round(gbs, 1), "frac": round(gbs / peak, 4),
+                      "peak_gbs": peak, "peak_kind": kind, "schedule": sched,
+                      "true_residual": max(i["true_residual"] for i in infos)}), flush=True)
+
+
 def our_arm(args):
     import torch
 
@@ -241,6 +445,7 @@ def our_arm(args):
     ms = e0.elapsed_time(e1)
     n_launch = ps.load_library().psms_kernel_launches() - n_launch0
     hop_n, hop_ms, hop_bytes = ps.psms_profile_read(ctx)
+    blk_n, blk_ms, blk_bytes = ps.psms_profile_read_block(ctx)
     ps.psms_profile_enable(ctx, 0)
     ms_max = allmax(ws, ms)
     accepted = sum(1 for r in recs if r["accept_global"] and r["n_accept_blocks"] > 0)
@@ -272,11 +477,17 @@ def our_arm(args):
     link_bytes = V * 4 * 9 * 16
 
     dw = measure_dw(ps, ctx, torch)
+    hb = measure_heatbath(ps, ctx, torch, wl)
     peak, peak_kind = peaks()
-    hop_avg_ms = hop_ms / max(hop_n, 1)
-    achieved = (hop_bytes / max(hop_n, 1)) / (hop_avg_ms * 1e-3) / 1e9 if hop_n else 0.0
+    rl_hop = roofline_entry("hop_kernel<float> (Wilson hop of the FP32 inner Krylov iterations)", hop_n, hop_ms,
+                            hop_bytes, peak, peak_kind)
+    rl_blk = roofline_entry("block_solve_cluster_kernel<float> (persistent Dirichlet-block CG, FP32 inner)", blk_n,
+                            blk_ms, blk_bytes, peak, peak_kind)
+    # the dominant kernel of the step: the larger measured time
+    rl_main, rl_other = (rl_blk, rl_hop) if blk_ms >= hop_ms else (rl_hop, rl_blk)
     if rank != 0:
         return
+    compare = None if args.no_compare else compare_16(ps, torch)
     full_iters = sum(r["solver_iters"] for r in recs) / max(len(recs), 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -295,11 +506,10 @@ def our_arm(args):
         "delta_block_std": float(sum(float(r["delta_block"].std()) for r in recs) / len(recs)),
         "plaquette_start": plaq0,
         "dw": dict(dw, peak_gbs=peak, frac_bf16=round(dw["bf16"]["GB/s"] / peak, 4)),
-        "roofline": {"kernel": "hop_kernel<float> (Wilson hop of the FP32 inner Krylov iterations, all launches "
-                               "in the timed steps)", "bound": "hbm",
-                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
-                     "launches": hop_n, "avg_launch_ms": round(hop_avg_ms, 5)},
+        "roofline": rl_main,
+        "roofline_secondary": rl_other,
+        "compare_16^4": compare,
+        "heatbath": hb,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": link_bytes, "d2h_bytes_per_step": link_bytes},
         "gpu_launches": n_launch,
         "wall_s_timed": wall,
@@ -403,7 +613,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="32^3x64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the 16^4 plain / mixed / learned comparison")
     ap.add_argument("--dw-only", action="store_true", help="stand-alone D_w measurement only")
+    ap.add_argument("--solve-only", action="store_true", help="single-system solver measurement only")
+    ap.add_argument("--batch-only", action="store_true", help="config-3 multi-lattice batched block solves")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -411,6 +624,10 @@ def main():
         reference_arm(args)
     elif args.dw_only:
         dw_only(args)
+    elif args.solve_only:
+        solve_only(args)
+    elif args.batch_only:
+        batch_only(args)
     else:
         our_arm(args)
 

@@ -115,6 +115,7 @@ typedef struct {
     int inner_prec;        /* psms_prec of the inner Krylov iterations         */
     uint64_t seed;
     uint64_t step;         /* filter step counter (RNG counter base)           */
+    int learned;           /* 1: insert the learned level before level 1       */
 } psms_filter_params;
 
 typedef struct {
@@ -126,7 +127,18 @@ typedef struct {
     double delta_block_sum;
     long long solver_iters;
     int hb_failed;
+    int n_accept_learned;  /* blocks passing the learned level (-1: no level)  */
 } psms_filter_result;
+
+typedef struct {
+    int epochs;
+    int batch;             /* minibatch size                                   */
+    double lr;             /* AdamW step size                                  */
+    double beta1, beta2, eps;
+    double weight_decay;
+    int normalise;         /* 1: set input mean / scale and label scale from the data */
+    uint64_t seed;         /* minibatch shuffling                              */
+} psms_train_params;
 
 /* ---- context ------------------------------------------------------------ */
 
@@ -211,6 +223,78 @@ psms_status psms_logdet_ratio(psms_ctx *ctx, int level, int field_old, int field
 psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params *prm,
                              psms_filter_result *res, double *delta_block_out, int *accept_block_out);
 
+/* ---- batched block solves over several lattices ---------------------------
+ * All Dirichlet blocks x all right-hand sides of several lattices (each its
+ * own context, possibly of different sizes; same device) solved by one
+ * persistent launch (Sec. 3: the block levels are independent per block):
+ * CTAs take (lattice, block, system) items from an atomic counter; every
+ * item runs the even-odd CGNR with its FP64 defect correction on the device.
+ * psms_block_plan_create allocates the scratch, autotunes the schedule
+ * (persistent grid of 1..4 CTAs per SM x three work orders, each timed once
+ * on the given inputs; the results do not depend on the schedule) and
+ * captures the tuned launch sequence in a CUDA graph.  psms_block_plan_run
+ * replays the graph on `stream` (refreshing FP32 link copies first) and
+ * returns the summed inner iterations and the worst relative residual.
+ * Problem i: b_dev / x_dev hold n_rhs native FP64 fields back to back; the
+ * pointers and fields are fixed at plan creation. */
+typedef struct {
+    psms_ctx *ctx;
+    int field;
+    int n_rhs;
+    const void *b_dev;
+    void *x_dev;
+} psms_block_problem;
+typedef struct psms_block_plan psms_block_plan;
+psms_status psms_block_plan_create(const psms_block_problem *probs, int n_probs, double tol, int maxit,
+                                   int inner_prec, psms_block_plan **out);
+psms_status psms_block_plan_run(psms_block_plan *plan, void *cuda_stream, psms_solve_info *info);
+/* The tuned schedule: persistent CTAs, work order (0 lattice-major,
+ * 1 system-major, 2 round-robin over lattices), its tuning time in ms. */
+psms_status psms_block_plan_schedule(const psms_block_plan *plan, int *ctas, int *order, double *tuned_ms);
+psms_status psms_block_plan_destroy(psms_block_plan *plan);
+
+/* ---- learned delayed-acceptance level ------------------------------------
+ * The paper has no learned level; it is inserted through the mechanism of
+ * App. C (an auxiliary action whose coefficients sum to zero over the later
+ * levels): a deterministic antisymmetric surrogate h_b(U, U') of the block
+ * log det ratio is accepted with min{1, exp(-h_b)} per block (u from key
+ * (seed, 4), counter (step, 3, block, 0)), and level 1 then uses
+ * Delta_b - h_b, so the chain stays exact whatever the network predicts.
+ *
+ * Features (32 per block, float, out[b * 32 + k], b lexicographic): mean and
+ * population variance of ReTr U_p / 3 over the plaquettes inside the block
+ * per plane (mu,nu) = (0,1),(0,2),(0,3),(1,2),(1,3),(2,3) (k = 0..5, 6..11),
+ * mean Tr F_{mu nu}^2 of the clover field strength over sites whose four
+ * leaves lie inside the block (k = 12..17), zeros (k = 18..31). */
+psms_status psms_domain_features(psms_ctx *ctx, int field, float *out_dev);
+/* Network input rows of a proposal field_old -> field_new, out[b * 64 + k]:
+ * k < 32 features of the old field, k >= 32 of the new one, and in slots 18
+ * and 50 (both halves) the distance of Sec. 4.2, Eq. (sprodgf), restricted
+ * to the block: sum over the block's links of ReTr(1 - U^dagger U') / (12 *
+ * number of links).  This is the input the filter step's learned level uses. */
+psms_status psms_domain_features_pair(psms_ctx *ctx, int field_old, int field_new, float *out_dev);
+/* MLP 64 -> 256 -> 256 -> 1 (ReLU), BF16 tensor-core GEMMs with FP32
+ * accumulation, FP32 master parameters.  Input z = [f(U_b), f(U'_b)],
+ * standardised by per-column mean / scale (both halves share them);
+ * h = ys * (n(z) - n(swap z)) / 2.  Parameters: He-normal from Philox
+ * key (seed, 6). */
+psms_status psms_mlp_init(psms_ctx *ctx, uint64_t seed);
+/* Number of floats of the parameter block: W1[256][64], b1[256],
+ * W2[256][256], b2[256], w3[256], b3, mu[64], sigma[64], ys. */
+size_t psms_mlp_param_count(void);
+/* Copy the parameter block to (set = 0) or from (set = 1) host memory. */
+psms_status psms_mlp_params(psms_ctx *ctx, float *host, int set);
+/* h for n rows of 64 features (device in / out). */
+psms_status psms_mlp_predict(psms_ctx *ctx, const float *feats_dev, int n, float *h_dev);
+/* Mean squared error of h against labels and its gradient (the first
+ * W1..b3 entries of the parameter block) into grad_host (may be NULL). */
+psms_status psms_mlp_grad(psms_ctx *ctx, const float *feats_dev, const double *labels_dev, int n, float *grad_host,
+                          double *loss);
+/* AdamW training on (feats, labels) for tp->epochs epochs of shuffled
+ * minibatches; loss_per_epoch[e] (host, may be NULL) = mean minibatch MSE. */
+psms_status psms_mlp_train(psms_ctx *ctx, const float *feats_dev, const double *labels_dev, int n,
+                           const psms_train_params *tp, double *loss_per_epoch);
+
 /* Profiling: when enabled, the context records CUDA events on its stream
  * around every full-operator Wilson hop launch (enable = 1), or only those of
  * storage precision p (enable = 10 + p); psms_profile_read returns the launch
@@ -220,6 +304,10 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
 psms_status psms_profile_enable(psms_ctx *ctx, int enable);
 psms_status psms_profile_read(psms_ctx *ctx, long long *launches, double *total_ms,
                               double *bytes_per_launch_sum);
+/* The same for the block-solver launches while profiling is enabled: count,
+ * summed milliseconds and algorithmic bytes (per block-CG iteration and
+ * half-block site: 4416 B with FP32 inner iterations, 8832 B with FP64). */
+psms_status psms_profile_read_block(psms_ctx *ctx, long long *launches, double *total_ms, double *bytes);
 
 /* Dirichlet block solve that allocates no memory.  The paper has no
  * counterpart: this is a deployment variant of psms_solve for op =
@@ -246,6 +334,25 @@ psms_status psms_profile_read(psms_ctx *ctx, long long *launches, double *total_
  * misses tol within maxit iterations. */
 psms_status psms_block_solve_noalloc(psms_ctx *ctx, int field, int op, const void *b_dev, void *x_dev, double tol,
                                      int maxit, long long *iters_out, double *resid_out);
+
+/* ---- checkpoint / resume ----------------------------------------------------
+ * The chain state: the FP64 gauge field of slot `field` (canonical layout),
+ * the caller's filter-step counter and seed, and the learned level's
+ * parameters if present.  All random numbers are counter-based (Philox keyed
+ * by seed, counters from the step), so a chain resumed from a checkpoint
+ * continues bit-identically.  Loading checks the lattice, blocks and kappa
+ * (PSMS_EINVAL on mismatch or a damaged file). */
+psms_status psms_checkpoint_save(psms_ctx *ctx, int field, const char *path, uint64_t step, uint64_t seed);
+psms_status psms_checkpoint_load(psms_ctx *ctx, int field, const char *path, uint64_t *step, uint64_t *seed);
+
+/* Autotuning of launch variants (on by default).  The hop kernel's register
+ * cap and the block solver's (cluster size, register cap) are timed on
+ * their first use per shape and the fastest kept; every variant computes
+ * the same result.  block_variant >= 0 forces block-solver variant
+ * (cluster size, min CTAs per SM) = (1,1),(1,4),(2,1),(2,4),(4,1),(4,4),
+ * (8,1),(8,4) for index 0..7 (falling back to 0 when the block is too small
+ * for the cluster); -1 restores the tuned choice.  Clears the tuning cache. */
+psms_status psms_autotune(psms_ctx *ctx, int enable, int block_variant);
 
 /* Number of CUDA kernels the library has launched in this process. */
 long long psms_kernel_launches(void);

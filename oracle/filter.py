@@ -117,9 +117,9 @@ def filter_step(U, geom, prm, seed, step, h_override=None):
     h = np.zeros(geom.n_blocks)
     rec_h = None
     if prm.learned is not None:
-        from .mlp import antisym, domain_features
+        from .mlp import antisym, pair_features
         assert per_block
-        z = np.concatenate([domain_features(U, geom), domain_features(Unew, geom)], axis=1)
+        z = pair_features(U, Unew, geom)
         h = antisym(prm.learned, z) if h_override is None else np.asarray(h_override, dtype=np.float64)
         passed = np.array([accept(h[b], philox.accept_uniform(seed, step, 3, b)) for b in range(geom.n_blocks)])
         rec_h = h

@@ -80,6 +80,20 @@ def domain_features(U, geom):
     return f
 
 
+def pair_features(U, Up, geom):
+    """Rows [f(U_b), f(U'_b)] with the block distance of Eq. (sprodgf),
+    d_b = sum over the links starting in b of ReTr(1 - U^dagger U') / (12 * n_links),
+    in slot 18 of both halves."""
+    z = np.concatenate([domain_features(U, geom), domain_features(Up, geom)], axis=1)
+    tr = np.real(np.einsum("...ab,...ab->...", np.conj(U), Up))       # ReTr(U^dagger U') per link
+    per_site = np.sum(3.0 - tr, axis=-1)
+    d = np.bincount(geom.block_index.reshape(-1), weights=per_site.reshape(-1), minlength=geom.n_blocks)
+    d = d / (12.0 * 4 * geom.Vb)
+    z[:, 18] = d
+    z[:, N_FEAT + 18] = d
+    return z
+
+
 def init_params(seed, n_in=2 * N_FEAT, hidden=HIDDEN):
     """He-normal weights, zero biases (the GPU path draws its own; parity
     tests pass parameters explicitly)."""

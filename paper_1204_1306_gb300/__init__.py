@@ -17,7 +17,11 @@ __all__ = [
     "psms_gauge_init", "psms_gauge_set", "psms_gauge_get", "psms_gauge_copy", "psms_plaquette",
     "psms_gauge_sweep", "psms_gauge_translate", "psms_spinor_bytes", "psms_spinor_import",
     "psms_spinor_export", "psms_dw_apply", "psms_solve", "psms_logdet_ratio", "psms_filter_step",
-    "psms_profile_enable", "psms_profile_read", "psms_block_solve_noalloc",
+    "psms_profile_enable", "psms_profile_read", "psms_block_solve_noalloc", "psms_domain_features",
+    "psms_mlp_init", "psms_mlp_param_count", "psms_mlp_params", "psms_mlp_predict", "psms_mlp_grad",
+    "psms_mlp_train", "psms_block_plan_create", "psms_block_plan_run", "psms_block_plan_schedule",
+    "psms_block_plan_destroy", "BlockPlan", "psms_autotune", "psms_profile_read_block",
+    "psms_domain_features_pair", "psms_checkpoint_save", "psms_checkpoint_load",
     "PREC_F64", "PREC_F32", "PREC_BF16", "OP_FULL", "OP_BLOCKS", "ACTIVE_BLOCKS", "ACTIVE_ALL",
     "LEVEL_BLOCK", "LEVEL_GLOBAL", "EST_INTERP", "EST_INDEPENDENT",
 ]
@@ -54,14 +58,26 @@ class FilterParams(ctypes.Structure):
     _fields_ = [("beta0", ctypes.c_double), ("n_iter", ctypes.c_int), ("n_or", ctypes.c_int),
                 ("n_block", ctypes.c_int), ("beta_block", ctypes.c_double), ("n_global", ctypes.c_int),
                 ("beta_global", ctypes.c_double), ("global_level", ctypes.c_int), ("tol", ctypes.c_double),
-                ("inner_prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("step", ctypes.c_uint64)]
+                ("inner_prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("step", ctypes.c_uint64),
+                ("learned", ctypes.c_int)]
 
 
 class FilterResult(ctypes.Structure):
     _fields_ = [("n_blocks", ctypes.c_int), ("n_accept_blocks", ctypes.c_int), ("accept_global", ctypes.c_int),
                 ("shift", ctypes.c_int * 4), ("delta_global", ctypes.c_double),
                 ("delta_block_sum", ctypes.c_double), ("solver_iters", ctypes.c_longlong),
-                ("hb_failed", ctypes.c_int)]
+                ("hb_failed", ctypes.c_int), ("n_accept_learned", ctypes.c_int)]
+
+
+class BlockProblem(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("field", ctypes.c_int), ("n_rhs", ctypes.c_int),
+                ("b_dev", ctypes.c_void_p), ("x_dev", ctypes.c_void_p)]
+
+
+class TrainParams(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("weight_decay", ctypes.c_double), ("normalise", ctypes.c_int), ("seed", ctypes.c_uint64)]
 
 
 _P = ctypes.c_void_p
@@ -90,6 +106,21 @@ _SIGS = {
                          ctypes.POINTER(_D), ctypes.POINTER(_I)],
     "psms_block_solve_noalloc": [_P, _I, _I, _P, _P, _D, _I, ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(_D)],
+    "psms_block_plan_create": [ctypes.POINTER(BlockProblem), _I, _D, _I, _I, ctypes.POINTER(_P)],
+    "psms_block_plan_run": [_P, _P, ctypes.POINTER(SolveInfo)],
+    "psms_block_plan_schedule": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)],
+    "psms_block_plan_destroy": [_P],
+    "psms_domain_features": [_P, _I, _P],
+    "psms_domain_features_pair": [_P, _I, _I, _P],
+    "psms_mlp_init": [_P, _U64],
+    "psms_mlp_params": [_P, ctypes.POINTER(ctypes.c_float), _I],
+    "psms_mlp_predict": [_P, _P, _I, _P],
+    "psms_mlp_grad": [_P, _P, _P, _I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_D)],
+    "psms_mlp_train": [_P, _P, _P, _I, ctypes.POINTER(TrainParams), ctypes.POINTER(_D)],
+    "psms_autotune": [_P, _I, _I],
+    "psms_checkpoint_save": [_P, _I, ctypes.c_char_p, _U64, _U64],
+    "psms_checkpoint_load": [_P, _I, ctypes.c_char_p, ctypes.POINTER(_U64), ctypes.POINTER(_U64)],
+    "psms_profile_read_block": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), ctypes.POINTER(_D)],
     "psms_profile_enable": [_P, _I],
     "psms_profile_read": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), ctypes.POINTER(_D)],
 }
@@ -113,6 +144,8 @@ def load_library(path=LIB_PATH):
     lib.psms_last_error.restype = ctypes.c_char_p
     lib.psms_spinor_bytes.argtypes = [_P, _I]
     lib.psms_spinor_bytes.restype = ctypes.c_size_t
+    lib.psms_mlp_param_count.argtypes = []
+    lib.psms_mlp_param_count.restype = ctypes.c_size_t
     lib.psms_kernel_launches.argtypes = []
     lib.psms_kernel_launches.restype = ctypes.c_longlong
     _lib = lib
@@ -252,9 +285,11 @@ def psms_logdet_ratio(ctx, level, field_old, field_new, n, mode, seed, counter, 
 
 
 def psms_filter_step(ctx, field, *, beta0, n_iter=1, n_or=0, n_block=4, n_global=4, beta_block=0.0,
-                     beta_global=0.0, global_level=True, tol=1e-10, inner_prec=PREC_F64, seed=0, step=0):
+                     beta_global=0.0, global_level=True, tol=1e-10, inner_prec=PREC_F64, seed=0, step=0,
+                     learned=False):
     p = FilterParams(float(beta0), int(n_iter), int(n_or), int(n_block), float(beta_block), int(n_global),
-                     float(beta_global), int(bool(global_level)), float(tol), int(inner_prec), int(seed), int(step))
+                     float(beta_global), int(bool(global_level)), float(tol), int(inner_prec), int(seed), int(step),
+                     int(bool(learned)))
     r = FilterResult()
     nb = int(np.prod([d // b for d, b in zip(ctx.dims, ctx.block)]))
     db = (_D * nb)()
@@ -262,7 +297,7 @@ def psms_filter_step(ctx, field, *, beta0, n_iter=1, n_or=0, n_block=4, n_global
     ctx.check(ctx.lib.psms_filter_step(ctx.handle, field, ctypes.byref(p), ctypes.byref(r), db, ab))
     return {"n_blocks": r.n_blocks, "n_accept_blocks": r.n_accept_blocks, "accept_global": bool(r.accept_global),
             "shift": tuple(r.shift), "delta_global": r.delta_global, "delta_block_sum": r.delta_block_sum,
-            "solver_iters": r.solver_iters, "hb_failed": r.hb_failed,
+            "solver_iters": r.solver_iters, "hb_failed": r.hb_failed, "n_accept_learned": r.n_accept_learned,
             "delta_block": np.frombuffer(db, dtype=np.float64).copy(),
             "accept_block": np.frombuffer(ab, dtype=np.int32).astype(bool)}
 
@@ -273,6 +308,133 @@ def psms_block_solve_noalloc(ctx, field, op, b_dev, x_dev, tol, maxit):
     ctx.check(ctx.lib.psms_block_solve_noalloc(ctx.handle, field, op, _ptr(b_dev), _ptr(x_dev), float(tol),
                                                int(maxit), ctypes.byref(it), ctypes.byref(res)))
     return {"inner_iters": it.value, "true_residual": res.value}
+
+
+class BlockPlan:
+    """Owns a psms_block_plan (see psms_block_plan_create)."""
+
+    def __init__(self, problems, tol, maxit, inner_prec):
+        self.lib = load_library()
+        self.keep = problems
+        arr = (BlockProblem * len(problems))()
+        for i, (ctx, field, n_rhs, b, x) in enumerate(problems):
+            arr[i] = BlockProblem(ctx.handle, int(field), int(n_rhs), _ptr(b), _ptr(x))
+        h = _P()
+        st = self.lib.psms_block_plan_create(arr, len(problems), float(tol), int(maxit), int(inner_prec),
+                                             ctypes.byref(h))
+        if st:
+            raise PsmsError(st, self.lib.psms_last_error(problems[0][0].handle).decode())
+        self.handle = h
+
+    def run(self, stream=None):
+        raw = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        info = SolveInfo()
+        st = self.lib.psms_block_plan_run(self.handle, _P(raw), ctypes.byref(info))
+        if st:
+            raise PsmsError(st, "psms_block_plan_run failed")
+        return {"inner_iters": info.inner_iters, "true_residual": info.true_residual, "n_systems": info.n_systems}
+
+    def schedule(self):
+        a, b, c = _I(), _I(), _D()
+        self.lib.psms_block_plan_schedule(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        return {"ctas": a.value, "order": b.value, "tuned_ms": c.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.psms_block_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def psms_block_plan_create(problems, tol, maxit, inner_prec):
+    """problems: list of (ctx, field, n_rhs, b_dev, x_dev)."""
+    return BlockPlan(problems, tol, maxit, inner_prec)
+
+
+def psms_block_plan_run(plan, stream=None):
+    return plan.run(stream)
+
+
+def psms_block_plan_schedule(plan):
+    return plan.schedule()
+
+
+def psms_block_plan_destroy(plan):
+    plan.close()
+
+
+def psms_domain_features(ctx, field, out_dev):
+    ctx.check(ctx.lib.psms_domain_features(ctx.handle, field, _ptr(out_dev)))
+
+
+def psms_domain_features_pair(ctx, field_old, field_new, out_dev):
+    ctx.check(ctx.lib.psms_domain_features_pair(ctx.handle, field_old, field_new, _ptr(out_dev)))
+
+
+def psms_mlp_init(ctx, seed):
+    ctx.check(ctx.lib.psms_mlp_init(ctx.handle, int(seed)))
+
+
+def psms_mlp_param_count():
+    return int(load_library().psms_mlp_param_count())
+
+
+def psms_mlp_params(ctx, values=None):
+    """Get (values None) or set the flat FP32 parameter block."""
+    n = psms_mlp_param_count()
+    buf = (ctypes.c_float * n)()
+    if values is not None:
+        buf[:] = [float(v) for v in np.asarray(values, dtype=np.float32)]
+        ctx.check(ctx.lib.psms_mlp_params(ctx.handle, buf, 1))
+        return None
+    ctx.check(ctx.lib.psms_mlp_params(ctx.handle, buf, 0))
+    return np.frombuffer(buf, dtype=np.float32).copy()
+
+
+def psms_mlp_predict(ctx, feats_dev, n, h_dev):
+    ctx.check(ctx.lib.psms_mlp_predict(ctx.handle, _ptr(feats_dev), int(n), _ptr(h_dev)))
+
+
+def psms_mlp_grad(ctx, feats_dev, labels_dev, n):
+    n_train = psms_mlp_param_count() - 129
+    g = (ctypes.c_float * n_train)()
+    loss = _D()
+    ctx.check(ctx.lib.psms_mlp_grad(ctx.handle, _ptr(feats_dev), _ptr(labels_dev), int(n), g, ctypes.byref(loss)))
+    return loss.value, np.frombuffer(g, dtype=np.float32).copy()
+
+
+def psms_mlp_train(ctx, feats_dev, labels_dev, n, *, epochs=10, batch=256, lr=1e-3, beta1=0.9, beta2=0.999,
+                   eps=1e-8, weight_decay=1e-4, normalise=True, seed=0):
+    tp = TrainParams(int(epochs), int(batch), float(lr), float(beta1), float(beta2), float(eps), float(weight_decay),
+                     int(bool(normalise)), int(seed))
+    out = (_D * epochs)()
+    ctx.check(ctx.lib.psms_mlp_train(ctx.handle, _ptr(feats_dev), _ptr(labels_dev), int(n), ctypes.byref(tp), out))
+    return np.frombuffer(out, dtype=np.float64).copy()
+
+
+def psms_profile_read_block(ctx):
+    n, ms, by = ctypes.c_longlong(), _D(), _D()
+    ctx.check(ctx.lib.psms_profile_read_block(ctx.handle, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
+    return n.value, ms.value, by.value
+
+
+def psms_checkpoint_save(ctx, field, path, step, seed):
+    ctx.check(ctx.lib.psms_checkpoint_save(ctx.handle, field, str(path).encode(), int(step), int(seed)))
+
+
+def psms_checkpoint_load(ctx, field, path):
+    st, sd = _U64(), _U64()
+    ctx.check(ctx.lib.psms_checkpoint_load(ctx.handle, field, str(path).encode(), ctypes.byref(st), ctypes.byref(sd)))
+    return st.value, sd.value
+
+
+def psms_autotune(ctx, enable=True, block_variant=-1):
+    ctx.check(ctx.lib.psms_autotune(ctx.handle, int(bool(enable)), int(block_variant)))
 
 
 def psms_profile_enable(ctx, enable):

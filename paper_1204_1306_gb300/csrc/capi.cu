@@ -1,13 +1,16 @@
 // C ABI of the library (declared in include/psms.h): context management and
 // the entry points.  Every entry point catches internal errors and returns a
 // psms_status; the message is kept in the context.
+#include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "estimator.hpp"
 #include "gauge.hpp"
+#include "mlp.hpp"
 #include "solver.hpp"
 
 namespace psms {
@@ -64,17 +67,87 @@ void prof_end(psms_ctx *c, int slot, double bytes) {
     c->prof_pending[slot].second = bytes;
 }
 
+unsigned long long *prof_counter(psms_ctx *c, int slot) {
+    if (slot >= c->prof_cap) {
+        // grow the per-launch site counters (profiling mode only)
+        std::vector<unsigned long long> keep(c->prof_cap);
+        if (c->prof_cap) {
+            cuda_check(cudaStreamSynchronize(c->stream), "prof sync");
+            cuda_check(cudaMemcpy(keep.data(), c->d_prof_sites, sizeof(unsigned long long) * c->prof_cap,
+                                  cudaMemcpyDeviceToHost),
+                       "prof copy");
+            cudaFree(c->d_prof_sites);
+        }
+        int cap = std::max(4096, 2 * c->prof_cap);
+        cuda_check(cudaMalloc(&c->d_prof_sites, sizeof(unsigned long long) * cap), "prof alloc");
+        cuda_check(cudaMemset(c->d_prof_sites, 0, sizeof(unsigned long long) * cap), "prof memset");
+        if (c->prof_cap)
+            cuda_check(cudaMemcpy(c->d_prof_sites, keep.data(), sizeof(unsigned long long) * c->prof_cap,
+                                  cudaMemcpyHostToDevice),
+                       "prof copy");
+        c->prof_cap = cap;
+    }
+    return c->d_prof_sites + slot;
+}
+
+int prof_block_begin(psms_ctx *c) {
+    const int slot = (int)c->prof_b_pending.size();
+    while ((int)c->ev_pool_b.size() < 2 * (slot + 1)) {
+        cudaEvent_t e;
+        cuda_check(cudaEventCreate(&e), "event create");
+        c->ev_pool_b.push_back(e);
+    }
+    cuda_check(cudaEventRecord(c->ev_pool_b[2 * slot], c->stream), "event record");
+    c->prof_b_pending.push_back({slot, 0.0});
+    return slot;
+}
+
+void prof_block_end(psms_ctx *c, int slot) {
+    cuda_check(cudaEventRecord(c->ev_pool_b[2 * slot + 1], c->stream), "event record");
+    c->last_block_slot = slot;
+}
+
+// algorithmic bytes of one block-CG iteration per half-block site: 4 half
+// hops (in, out, 8 links per output site, y on the second hop of each pair)
+// and 12 half-vector passes = 4416 B in FP32, twice that in FP64
+void prof_block_bytes(psms_ctx *c, long long block_iters, int inner_prec) {
+    if (!c->prof || c->last_block_slot < 0) return;
+    const double per = (inner_prec == P64 ? 8832.0 : 4416.0) * c->g.Vbh;
+    c->prof_b_pending[c->last_block_slot].second += per * (double)block_iters;
+    c->last_block_slot = -1;
+}
+
 static void prof_collect(psms_ctx *c) {
     if (c->prof_pending.empty()) return;
     cuda_check(cudaStreamSynchronize(c->stream), "prof sync");
-    for (auto &pp : c->prof_pending) {
+    const int n = (int)c->prof_pending.size();
+    std::vector<unsigned long long> sites(n);
+    cuda_check(cudaMemcpy(sites.data(), c->d_prof_sites, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost),
+               "prof sites");
+    for (int i = 0; i < n; ++i) {
+        const auto &pp = c->prof_pending[i];
         float ms = 0;
         cuda_check(cudaEventElapsedTime(&ms, c->ev_pool[2 * pp.first], c->ev_pool[2 * pp.first + 1]), "elapsed");
         c->prof_ms += ms;
-        c->prof_bytes += pp.second;
+        c->prof_bytes += pp.second * (double)sites[i];
         c->prof_launches += 1;
     }
+    cuda_check(cudaMemset(c->d_prof_sites, 0, sizeof(unsigned long long) * c->prof_cap), "prof reset");
     c->prof_pending.clear();
+}
+
+static void prof_collect_block(psms_ctx *c) {
+    if (c->prof_b_pending.empty()) return;
+    cuda_check(cudaStreamSynchronize(c->stream), "prof sync");
+    for (auto &pp : c->prof_b_pending) {
+        float ms = 0;
+        cuda_check(cudaEventElapsedTime(&ms, c->ev_pool_b[2 * pp.first], c->ev_pool_b[2 * pp.first + 1]), "elapsed");
+        c->prof_b_ms += ms;
+        c->prof_b_bytes += pp.second;
+        c->prof_b_launches += 1;
+    }
+    c->prof_b_pending.clear();
+    c->last_block_slot = -1;
 }
 
 __global__ void unit_links_kernel(double2 *U, long long V) {
@@ -154,7 +227,10 @@ static void free_ctx(psms_ctx *c) {
     for (auto &kv : c->scratch)
         if (kv.second.p) cudaFree(kv.second.p);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (auto e : c->ev_pool_b) cudaEventDestroy(e);
+    if (c->d_prof_sites) cudaFree(c->d_prof_sites);
     if (c->d_binfo) cudaFree(c->d_binfo);
+    if (c->mlp && c->mlp_free) c->mlp_free(c->mlp);
     delete c;
 }
 
@@ -461,6 +537,7 @@ psms_status psms_solve(psms_ctx *ctx, int field, int op, const void *b, void *x,
             worst = std::max(worst, hr[i]);
             bad |= hs[i];
         }
+        prof_block_bytes(ctx, tot, inner_prec);
         if (info) {
             info->outer_iters = 0;
             info->inner_iters = tot;
@@ -516,18 +593,45 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
     const int failed = gauge_sweep(ctx, prop, PSMS_ACTIVE_BLOCKS, prm->n_iter, prm->n_or, prm->beta0, prm->seed,
                                    prm->step << 20);
     if (failed) fail(PSMS_EHEATBATH, "an SU(2) heatbath draw hit its attempt limit");
-    // level 1: block det ratios
     const int nb = g.nblocks, N1 = prm->n_block;
-    double *d_db = (double *)scratch(ctx, "fs_dblk", sizeof(double) * nb * N1);
-    long long iters = block_level(ctx, old, prop, N1, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol,
-                                  prm->inner_prec, d_db);
     bool per_block = true;
     for (int m = 0; m < 4; ++m) per_block &= g.l[m] >= 3;
+    if (prm->beta_block != 0.0) fail(PSMS_EINVAL, "beta_block != 0 is not supported");
+    // learned level (before level 1): h_b, accept with min{1, exp(-h_b)}
+    const int *d_mask = nullptr;
+    double *d_h = nullptr;
+    int n_learned = -1;
+    if (prm->learned) {
+        if (!per_block) fail(PSMS_EINVAL, "the learned level needs per-block decisions (block extents >= 3)");
+        if (!ctx->mlp) fail(PSMS_EINVAL, "the learned level needs a trained MLP (psms_mlp_init / psms_mlp_train)");
+        float *z = (float *)scratch(ctx, "fs_feat", sizeof(float) * nb * 2 * N_FEAT);
+        pair_features(ctx, old, prop, z);
+        float *hf = (float *)scratch(ctx, "fs_hf", sizeof(float) * nb);
+        mlp_predict(ctx, z, nb, hf);
+        d_h = (double *)scratch(ctx, "fs_h", sizeof(double) * nb);
+        float_to_double(ctx, hf, d_h, nb);
+        int *d_acc3 = (int *)scratch(ctx, "fs_acc3", sizeof(int) * nb);
+        double *d_hs = (double *)scratch(ctx, "fs_hsum", sizeof(double) * (nb + 1));
+        decide(ctx, d_h, nb, 1, 1, prm->seed, prm->step, 3, 0.0, nullptr, 0.0, d_hs, d_acc3);
+        std::vector<int> h3(nb);
+        cuda_check(cudaMemcpyAsync(h3.data(), d_acc3, sizeof(int) * nb, cudaMemcpyDeviceToHost, ctx->stream), "l3");
+        cuda_check(cudaStreamSynchronize(ctx->stream), "l3");
+        n_learned = 0;
+        for (int v : h3) n_learned += v;
+        d_mask = d_acc3;
+    }
+    // level 1: block det ratios (blocks that passed the learned level)
+    double *d_db = (double *)scratch(ctx, "fs_dblk", sizeof(double) * nb * N1);
+    long long iters = 0;
+    if (n_learned != 0)
+        iters = block_level(ctx, old, prop, N1, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol, prm->inner_prec,
+                            d_db, d_mask);
+    else
+        cuda_check(cudaMemsetAsync(d_db, 0, sizeof(double) * nb * N1, ctx->stream), "dblk");
     double *d_dsum = (double *)scratch(ctx, "fs_dsum", sizeof(double) * (nb + 1));
     int *d_acc = (int *)scratch(ctx, "fs_acc", sizeof(int) * nb);
-    if (prm->beta_block != 0.0) fail(PSMS_EINVAL, "beta_block != 0 is not supported");
-    decide(ctx, d_db, nb, N1, per_block ? 1 : 0, prm->seed, prm->step, PSMS_LEVEL_BLOCK, 0.0, nullptr, 0.0, d_dsum,
-           d_acc);
+    decide(ctx, d_db, nb, N1, per_block ? 1 : 0, prm->seed, prm->step, PSMS_LEVEL_BLOCK, 0.0, d_h, -1.0, d_dsum,
+           d_acc, d_mask);
     merge_blocks(ctx, old, prop, mid, d_acc);
     std::vector<double> hd(nb + 1);
     std::vector<int> ha(nb);
@@ -540,11 +644,12 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         nacc += ha[b];
         dsum += hd[b];
     }
-    // level 2: global Schur det ratio
+    // level 2: global Schur det ratio (a field equal to the old one has
+    // Delta = 0 exactly: every M_i is the identity)
     double dglob = 0;
     int accg = 1;
     double2 *fin = mid;
-    if (prm->global_level) {
+    if (prm->global_level && nacc > 0) {
         const int N2 = prm->n_global;
         double *d_dg = (double *)scratch(ctx, "fs_dg", sizeof(double) * N2);
         iters += global_level(ctx, old, mid, N2, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol, prm->inner_prec,
@@ -588,6 +693,7 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         res->delta_block_sum = per_block ? dsum : hd[nb];
         res->solver_iters = iters;
         res->hb_failed = failed;
+        res->n_accept_learned = n_learned;
     }
     if (delta_block_out)
         for (int b = 0; b < nb; ++b) delta_block_out[b] = hd[b];
@@ -599,15 +705,116 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
 psms_status psms_profile_enable(psms_ctx *ctx, int enable) {
     PSMS_TRY(ctx)
     prof_collect(ctx);
+    prof_collect_block(ctx);
     ctx->prof = enable != 0;
     ctx->prof_prec = enable >= 10 ? enable - 10 : -1;
     ctx->prof_launches = 0;
     ctx->prof_ms = 0;
     ctx->prof_bytes = 0;
+    ctx->prof_b_launches = 0;
+    ctx->prof_b_ms = 0;
+    ctx->prof_b_bytes = 0;
     PSMS_CATCH(ctx)
 }
 
 long long psms_kernel_launches(void) { return launch_counter(); }
+
+// checkpoint file: magic, version, dims[4], block[4], kappa, step, seed,
+// has_mlp, then the FP64 links in the canonical layout, then (if has_mlp)
+// the MLP parameter block as float32
+static const char PSMS_MAGIC[8] = {'P', 'S', 'M', 'S', 'C', 'K', 'P', '1'};
+
+psms_status psms_checkpoint_save(psms_ctx *ctx, int field, const char *path, uint64_t step, uint64_t seed) {
+    PSMS_TRY(ctx)
+    check_field(ctx, field);
+    if (!path) fail(PSMS_EINVAL, "null path");
+    const long long n = 36 * ctx->g.V;
+    std::vector<double2> host(n);
+    double2 *canon = (double2 *)scratch(ctx, "ckpt", sizeof(double2) * n);
+    gauge_canonical(ctx, canon, ctx->U64[field], 0);
+    cuda_check(cudaMemcpyAsync(host.data(), canon, sizeof(double2) * n, cudaMemcpyDeviceToHost, ctx->stream), "ckpt");
+    std::vector<float> mlp;
+    if (ctx->mlp) {
+        mlp.resize(psms_mlp_param_count());
+        psms_status st = psms_mlp_params(ctx, mlp.data(), 0);
+        if (st) return st;
+    }
+    cuda_check(cudaStreamSynchronize(ctx->stream), "ckpt");
+    FILE *f = std::fopen(path, "wb");
+    if (!f) fail(PSMS_EINVAL, std::string("cannot open ") + path);
+    int hdr[10] = {1, ctx->g.L[0], ctx->g.L[1], ctx->g.L[2], ctx->g.L[3], ctx->g.l[0], ctx->g.l[1], ctx->g.l[2],
+                   ctx->g.l[3], mlp.empty() ? 0 : 1};
+    bool ok = std::fwrite(PSMS_MAGIC, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(int), 10, f) == 10 &&
+              std::fwrite(&ctx->kappa, sizeof(double), 1, f) == 1 && std::fwrite(&step, sizeof(step), 1, f) == 1 &&
+              std::fwrite(&seed, sizeof(seed), 1, f) == 1 &&
+              std::fwrite(host.data(), sizeof(double2), n, f) == (size_t)n &&
+              (mlp.empty() || std::fwrite(mlp.data(), sizeof(float), mlp.size(), f) == mlp.size());
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) fail(PSMS_EINVAL, std::string("write failed: ") + path);
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_checkpoint_load(psms_ctx *ctx, int field, const char *path, uint64_t *step, uint64_t *seed) {
+    PSMS_TRY(ctx)
+    check_field(ctx, field);
+    if (!path) fail(PSMS_EINVAL, "null path");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) fail(PSMS_EINVAL, std::string("cannot open ") + path);
+    char magic[8];
+    int hdr[10];
+    double kappa = 0;
+    uint64_t st_step = 0, st_seed = 0;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, PSMS_MAGIC, 8) == 0 &&
+              std::fread(hdr, sizeof(int), 10, f) == 10 && std::fread(&kappa, sizeof(double), 1, f) == 1 &&
+              std::fread(&st_step, sizeof(st_step), 1, f) == 1 && std::fread(&st_seed, sizeof(st_seed), 1, f) == 1;
+    for (int m = 0; ok && m < 4; ++m) ok = hdr[1 + m] == ctx->g.L[m] && hdr[5 + m] == ctx->g.l[m];
+    ok = ok && hdr[0] == 1 && kappa == ctx->kappa;
+    if (!ok) {
+        std::fclose(f);
+        fail(PSMS_EINVAL, "checkpoint does not match this context (format, lattice, blocks or kappa)");
+    }
+    const long long n = 36 * ctx->g.V;
+    std::vector<double2> host(n);
+    ok = std::fread(host.data(), sizeof(double2), n, f) == (size_t)n;
+    std::vector<float> mlp;
+    if (ok && hdr[9]) {
+        mlp.resize(psms_mlp_param_count());
+        ok = std::fread(mlp.data(), sizeof(float), mlp.size(), f) == mlp.size();
+    }
+    std::fclose(f);
+    if (!ok) fail(PSMS_EINVAL, "truncated checkpoint");
+    double2 *canon = (double2 *)scratch(ctx, "ckpt", sizeof(double2) * n);
+    cuda_check(cudaMemcpyAsync(canon, host.data(), sizeof(double2) * n, cudaMemcpyHostToDevice, ctx->stream), "ckpt");
+    gauge_canonical(ctx, canon, ctx->U64[field], 1);
+    touch_field(ctx, field);
+    cuda_check(cudaStreamSynchronize(ctx->stream), "ckpt");
+    if (!mlp.empty()) {
+        psms_status st = psms_mlp_params(ctx, mlp.data(), 1);
+        if (st) return st;
+    }
+    if (step) *step = st_step;
+    if (seed) *seed = st_seed;
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_profile_read_block(psms_ctx *ctx, long long *launches, double *total_ms, double *bytes) {
+    PSMS_TRY(ctx)
+    prof_collect_block(ctx);
+    if (launches) *launches = ctx->prof_b_launches;
+    if (total_ms) *total_ms = ctx->prof_b_ms;
+    if (bytes) *bytes = ctx->prof_b_bytes;
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_autotune(psms_ctx *ctx, int enable, int block_variant) {
+    PSMS_TRY(ctx)
+    if (block_variant < -1 || block_variant > 7) fail(PSMS_EINVAL, "block_variant must be -1 or 0..7");
+    ctx->autotune = enable != 0;
+    ctx->forced_block_variant = block_variant;
+    ctx->block_variant.clear();
+    for (auto &row : ctx->hop_variant) row[0] = row[1] = -1;
+    PSMS_CATCH(ctx)
+}
 
 psms_status psms_profile_read(psms_ctx *ctx, long long *launches, double *total_ms, double *bytes) {
     PSMS_TRY(ctx)

@@ -216,8 +216,13 @@ __host__ __device__ __forceinline__ bool link_active(const Geom &g, const int y[
 }
 
 // ---------------------------------------------------------------------------
-// precision-generic field access (structure of arrays: component c of site s
-// at base[c * cs + s]; links: U[mu][e][s], e = 3a + b, stride V)
+// precision-generic field access.  A field of `cs` sites stores component c
+// (c = 3 spin + colour) of site s at element idx(c, cs, s): components are
+// grouped in 16-byte units of 2^VSH complex numbers (FP64: 1, FP32: 2,
+// BF16: 4), unit u of site s at unit index u * cs + s, so that a thread
+// loads a whole spinor with 12, 6 or 3 vector loads and a warp's loads of
+// one unit are contiguous.  FP64 links: U[mu][e][s]; FP32 links: per mu four
+// 16-byte units (e = 0..7) then one 8-byte element (e = 8).
 // ---------------------------------------------------------------------------
 template <class T>
 struct Store;
@@ -226,7 +231,9 @@ template <>
 struct Store<double> {
     using elem = double2;
     using R = double;
-    static __device__ __forceinline__ cpx<double> ld(const elem *p, long long i) {
+    static constexpr int VSH = 0;
+    static __host__ __device__ __forceinline__ long long idx(int c, long long cs, long long s) { return c * cs + s; }
+    static __device__ __forceinline__ cpx<double> ldi(const elem *p, long long i) {
         double2 v = p[i];
         return {v.x, v.y};
     }
@@ -235,14 +242,24 @@ struct Store<double> {
         double2 v = __ldg(p + i);
         return {v.x, v.y};
     }
-    static __device__ __forceinline__ void st(elem *p, long long i, cpx<double> v) { p[i] = make_double2(v.re, v.im); }
+    static __device__ __forceinline__ void sti(elem *p, long long i, cpx<double> v) { p[i] = make_double2(v.re, v.im); }
+    static __device__ __forceinline__ cpx<double> ld(const elem *p, int c, long long cs, long long s) {
+        return ldi(p, idx(c, cs, s));
+    }
+    static __device__ __forceinline__ void st(elem *p, int c, long long cs, long long s, cpx<double> v) {
+        sti(p, idx(c, cs, s), v);
+    }
 };
 
 template <>
 struct Store<float> {
     using elem = float2;
     using R = float;
-    static __device__ __forceinline__ cpx<float> ld(const elem *p, long long i) {
+    static constexpr int VSH = 1;
+    static __host__ __device__ __forceinline__ long long idx(int c, long long cs, long long s) {
+        return (((long long)(c >> 1)) * cs + s) * 2 + (c & 1);
+    }
+    static __device__ __forceinline__ cpx<float> ldi(const elem *p, long long i) {
         float2 v = p[i];
         return {v.x, v.y};
     }
@@ -250,14 +267,24 @@ struct Store<float> {
         float2 v = __ldg(p + i);
         return {v.x, v.y};
     }
-    static __device__ __forceinline__ void st(elem *p, long long i, cpx<float> v) { p[i] = make_float2(v.re, v.im); }
+    static __device__ __forceinline__ void sti(elem *p, long long i, cpx<float> v) { p[i] = make_float2(v.re, v.im); }
+    static __device__ __forceinline__ cpx<float> ld(const elem *p, int c, long long cs, long long s) {
+        return ldi(p, idx(c, cs, s));
+    }
+    static __device__ __forceinline__ void st(elem *p, int c, long long cs, long long s, cpx<float> v) {
+        sti(p, idx(c, cs, s), v);
+    }
 };
 
 template <>
 struct Store<__nv_bfloat16> {
     using elem = __nv_bfloat162;
     using R = float;
-    static __device__ __forceinline__ cpx<float> ld(const elem *p, long long i) {
+    static constexpr int VSH = 2;
+    static __host__ __device__ __forceinline__ long long idx(int c, long long cs, long long s) {
+        return (((long long)(c >> 2)) * cs + s) * 4 + (c & 3);
+    }
+    static __device__ __forceinline__ cpx<float> ldi(const elem *p, long long i) {
         float2 v = __bfloat1622float2(p[i]);
         return {v.x, v.y};
     }
@@ -265,10 +292,27 @@ struct Store<__nv_bfloat16> {
         float2 v = __bfloat1622float2(__ldg(p + i));
         return {v.x, v.y};
     }
-    static __device__ __forceinline__ void st(elem *p, long long i, cpx<float> v) {
+    static __device__ __forceinline__ void sti(elem *p, long long i, cpx<float> v) {
         p[i] = __floats2bfloat162_rn(v.re, v.im);
     }
+    static __device__ __forceinline__ cpx<float> ld(const elem *p, int c, long long cs, long long s) {
+        return ldi(p, idx(c, cs, s));
+    }
+    static __device__ __forceinline__ void st(elem *p, int c, long long cs, long long s, cpx<float> v) {
+        sti(p, idx(c, cs, s), v);
+    }
 };
+
+// element index of link entry e of direction mu at site s
+template <class S>
+__host__ __device__ __forceinline__ long long link_idx(long long V, int mu, int e, long long s) {
+    if constexpr (S::VSH == 0) {
+        return ((long long)mu * 9 + e) * V + s;
+    } else {
+        const long long base = (long long)mu * 9 * V;
+        return e < 8 ? base + 2 * ((long long)(e >> 1) * V + s) + (e & 1) : base + 8 * V + s;
+    }
+}
 
 template <class R>
 struct Spinor {
@@ -283,43 +327,98 @@ struct SU3 {
     cpx<R> e[3][3];
 };
 
-template <class S>
-__device__ __forceinline__ Spinor<typename S::R> load_spinor(const typename S::elem *p, long long cs, long long s) {
+__device__ __forceinline__ cpx<float> bf_lo(uint32_t w) {
+    return {__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u)};
+}
+
+// whole spinor of site s with 16-byte vector loads (RO: read-only cache path)
+template <class S, bool RO>
+__device__ __forceinline__ Spinor<typename S::R> load_spinor_v(const typename S::elem *p, long long cs, long long s) {
     Spinor<typename S::R> v;
+    if constexpr (S::VSH == 0) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 12; ++c) v.c[c / 3][c % 3] = RO ? S::ldro(p, c * cs + s) : S::ldi(p, c * cs + s);
+    } else if constexpr (S::VSH == 1) {
+        const float4 *q = reinterpret_cast<const float4 *>(p);
 #pragma unroll
-        for (int b = 0; b < 3; ++b) v.c[a][b] = S::ld(p, (3 * a + b) * cs + s);
+        for (int u = 0; u < 6; ++u) {
+            const float4 w = RO ? __ldg(q + u * cs + s) : q[u * cs + s];
+            v.c[(2 * u) / 3][(2 * u) % 3] = {w.x, w.y};
+            v.c[(2 * u + 1) / 3][(2 * u + 1) % 3] = {w.z, w.w};
+        }
+    } else {
+        const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            const uint4 w = RO ? __ldg(q + u * cs + s) : q[u * cs + s];
+            const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int m = 0; m < 4; ++m) v.c[(4 * u + m) / 3][(4 * u + m) % 3] = bf_lo(ww[m]);
+        }
+    }
     return v;
 }
 
 template <class S>
+__device__ __forceinline__ Spinor<typename S::R> load_spinor(const typename S::elem *p, long long cs, long long s) {
+    return load_spinor_v<S, false>(p, cs, s);
+}
+
+template <class S>
 __device__ __forceinline__ Spinor<typename S::R> load_spinor_ro(const typename S::elem *p, long long cs, long long s) {
-    Spinor<typename S::R> v;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) v.c[a][b] = S::ldro(p, (3 * a + b) * cs + s);
-    return v;
+    return load_spinor_v<S, true>(p, cs, s);
 }
 
 template <class S>
 __device__ __forceinline__ void store_spinor(typename S::elem *p, long long cs, long long s,
                                              const Spinor<typename S::R> &v) {
+    if constexpr (S::VSH == 0) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 12; ++c) S::sti(p, c * cs + s, v.c[c / 3][c % 3]);
+    } else if constexpr (S::VSH == 1) {
+        float4 *q = reinterpret_cast<float4 *>(p);
 #pragma unroll
-        for (int b = 0; b < 3; ++b) S::st(p, (3 * a + b) * cs + s, v.c[a][b]);
+        for (int u = 0; u < 6; ++u) {
+            const cpx<float> a = v.c[(2 * u) / 3][(2 * u) % 3], b = v.c[(2 * u + 1) / 3][(2 * u + 1) % 3];
+            q[u * cs + s] = make_float4(a.re, a.im, b.re, b.im);
+        }
+    } else {
+        uint4 *q = reinterpret_cast<uint4 *>(p);
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            uint32_t ww[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const cpx<float> a = v.c[(4 * u + m) / 3][(4 * u + m) % 3];
+                __nv_bfloat162 h = __floats2bfloat162_rn(a.re, a.im);
+                ww[m] = *reinterpret_cast<uint32_t *>(&h);
+            }
+            q[u * cs + s] = make_uint4(ww[0], ww[1], ww[2], ww[3]);
+        }
+    }
 }
 
 template <class S>
 __device__ __forceinline__ SU3<typename S::R> load_link(const typename S::elem *U, long long V, int mu, long long s) {
     SU3<typename S::R> u;
-    const typename S::elem *q = U + (long long)mu * 9 * V + s;
+    if constexpr (S::VSH == 0) {
+        const typename S::elem *q = U + (long long)mu * 9 * V + s;
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+        for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) u.e[a][b] = S::ldro(q, (3 * a + b) * V);
+            for (int b = 0; b < 3; ++b) u.e[a][b] = S::ldro(q, (3 * a + b) * V);
+    } else {
+        const float2 *base = reinterpret_cast<const float2 *>(U) + (long long)mu * 9 * V;
+        const float4 *q = reinterpret_cast<const float4 *>(base);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 w = __ldg(q + k * V + s);
+            u.e[(2 * k) / 3][(2 * k) % 3] = {w.x, w.y};
+            u.e[(2 * k + 1) / 3][(2 * k + 1) % 3] = {w.z, w.w};
+        }
+        const float2 w = __ldg(base + 8 * V + s);
+        u.e[2][2] = {w.x, w.y};
+    }
     return u;
 }
 

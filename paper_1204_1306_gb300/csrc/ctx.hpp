@@ -55,9 +55,26 @@ struct psms_ctx {
     bool prof = false;
     int prof_prec = -1;  // profile hop launches of this storage precision only (-1: all)
     std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<int, double>> prof_pending;  // (event pair index, bytes)
+    std::vector<std::pair<int, double>> prof_pending;  // (event pair index, bytes per output site)
+    unsigned long long *d_prof_sites = nullptr;         // per pending launch: active output sites
+    int prof_cap = 0;
     long long prof_launches = 0;
+    // autotuned hop-kernel variant per (storage precision, both parities)
+    int hop_variant[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
+    bool autotune = true;
+    // autotuned block-solver variant per (precision, block size, batched)
+    std::map<long long, int> block_variant;
+    int forced_block_variant = -1;
+    // learned level: MLP state (owned, freed with mlp_free)
+    void *mlp = nullptr;
+    void (*mlp_free)(void *) = nullptr;
     double prof_ms = 0, prof_bytes = 0;
+    // profiling of block-solver launches: (event pair, algorithmic bytes)
+    std::vector<cudaEvent_t> ev_pool_b;
+    std::vector<std::pair<int, double>> prof_b_pending;
+    int last_block_slot = -1;
+    long long prof_b_launches = 0;
+    double prof_b_ms = 0, prof_b_bytes = 0;
 };
 
 namespace psms {
@@ -71,6 +88,12 @@ void check_field(psms_ctx *c, int f);
 
 // profiling hooks around Wilson-operator launches
 int prof_begin(psms_ctx *c);
-void prof_end(psms_ctx *c, int slot, double bytes);
+void prof_end(psms_ctx *c, int slot, double bytes_per_site);
+unsigned long long *prof_counter(psms_ctx *c, int slot);
+// block-solver launches: events around the launch; bytes set afterwards from
+// the iterations the solve reports
+int prof_block_begin(psms_ctx *c);
+void prof_block_end(psms_ctx *c, int slot);
+void prof_block_bytes(psms_ctx *c, long long block_iters, int inner_prec);
 
 }  // namespace psms

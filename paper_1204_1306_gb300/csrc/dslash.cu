@@ -21,6 +21,7 @@ struct HopArgs {
     int p, rank_lo, n_ranks, mode, dag;
     const int *active;
     double *partial;
+    unsigned long long *prof_sites;  // profiling: output sites of active systems
 };
 
 template <int NT>
@@ -37,8 +38,8 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return t;  // valid in thread 0
 }
 
-template <class S, class SL, int NT>
-__global__ void __launch_bounds__(NT) hop_kernel(const HopArgs<typename S::elem> a) {
+template <class S, class SL, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S::elem> a) {
     using R = typename SL::R;
     using E = typename S::elem;
     using EL = typename SL::elem;
@@ -52,12 +53,37 @@ __global__ void __launch_bounds__(NT) hop_kernel(const HopArgs<typename S::elem>
     const long long per_p = (long long)a.n_ranks * g.Vbh;
     const long long total = (a.p < 0 ? 2 : 1) * per_p;
     const long long t = (long long)blockIdx.x * NT + threadIdx.x;
+    if (a.prof_sites && threadIdx.x == 0) {
+        const long long first = (long long)blockIdx.x * NT;
+        const long long n = total - first < NT ? total - first : NT;
+        atomicAdd(a.prof_sites, (unsigned long long)n);
+    }
     double nrm = 0.0;
     if (t < total) {
-        const int p = a.p < 0 ? (int)(t >= per_p) : a.p;
-        const long long tt = a.p < 0 ? t - p * per_p : t;
-        const int r = a.rank_lo + (int)(tt >> g.vbh_sh);
-        const int j = (int)(tt & (g.Vbh - 1));
+        // both parities: block-major order (block, parity, site) so that the
+        // two endpoints of a block's links are processed close in time and
+        // each link is fetched from HBM about once per launch
+        int p, r, j;
+        if (a.p < 0) {
+            r = a.rank_lo + (int)(t >> (g.vbh_sh + 1));
+            p = (int)((t >> g.vbh_sh) & 1);
+            j = (int)(t & (g.Vbh - 1));
+            if (a.n_ranks == g.nblocks) {
+                // whole lattice: walk the blocks in lexicographic order, so
+                // that a block's neighbours (opposite colour) are processed
+                // soon after it and face data is still in L2
+                int B[4], rem = r;
+                for (int m = 3; m >= 0; --m) {
+                    B[m] = rem % g.nb[m];
+                    rem /= g.nb[m];
+                }
+                r = rank_of_lex(g, r, B);
+            }
+        } else {
+            p = a.p;
+            r = a.rank_lo + (int)(t >> g.vbh_sh);
+            j = (int)(t & (g.Vbh - 1));
+        }
         int y[4];
         const int ll = local_lex(g, p, j, y);
         const BlockInfo &bi = a.binfo[r];
@@ -172,19 +198,60 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
     a.dag = h.dag;
     a.active = h.active;
     a.partial = h.partial;
+    a.prof_sites = nullptr;
     const int nct = hop_ctas(c, h);
     if (nct == 0 || h.n_sys == 0) return 0;
     dim3 grid(nct, h.n_sys);
     double bytes = 0;
     int slot = -1;
     if (c->prof && h.mode == HOP_ALL && (c->prof_prec < 0 || c->prof_prec == h.prec)) {
-        // algorithmic bytes: in + out (+ y, y2) spinors and 4 links per output site
-        const long long sites = (h.p < 0 ? 2LL : 1LL) * a.n_ranks * c->g.Vbh;
+        // algorithmic bytes per output site of an active system: in + out
+        // (+ y, y2) spinors and 4 links (both parities) or 8 (one parity);
+        // the device counts the output sites of the systems still active
         const double sp = 12.0 * sizeof(E), lk = 9.0 * sizeof(typename SL::elem);
-        bytes = (double)h.n_sys * sites * (2 * sp + (h.y.p ? sp : 0) + (h.y2.p ? sp : 0) + 4 * lk * (h.p < 0 ? 1 : 2));
+        bytes = 2 * sp + (h.y.p ? sp : 0) + (h.y2.p ? sp : 0) + 4 * lk * (h.p < 0 ? 1 : 2);
         slot = prof_begin(c);
+        a.prof_sites = prof_counter(c, slot);
     }
-    hop_kernel<S, SL, HOP_NT><<<grid, HOP_NT, 0, c->stream>>>(a);
+    // Register cap (minimum resident CTAs per SM) chosen by the autotuner:
+    // on the first launch of each (precision, parity shape) every variant is
+    // timed twice with CUDA events and the fastest is kept.  All variants do
+    // identical arithmetic; a launch is idempotent (out is a function of in, y,
+    // y2, U only), so the extra tuning launches leave the result unchanged.
+    using KFn = void (*)(const HopArgs<E>);
+    constexpr bool f32 = sizeof(typename SL::R) == 4;
+    static const KFn variants32[] = {hop_kernel<S, SL, HOP_NT, 2>, hop_kernel<S, SL, HOP_NT, 6>,
+                                     hop_kernel<S, SL, HOP_NT, 7>, hop_kernel<S, SL, HOP_NT, 8>};
+    static const KFn variants64[] = {hop_kernel<S, SL, HOP_NT, 2>};
+    const KFn *vars = f32 ? variants32 : variants64;
+    const int nvar = f32 ? 4 : 1;
+    int &choice = c->hop_variant[h.prec][h.p < 0 ? 1 : 0];
+    if (choice < 0 && c->autotune && nvar > 1 && slot < 0) {
+        cudaEvent_t e0, e1;
+        cuda_check(cudaEventCreate(&e0), "tune event");
+        cuda_check(cudaEventCreate(&e1), "tune event");
+        float best = 1e30f;
+        for (int v = 0; v < nvar; ++v) {
+            vars[v]<<<grid, HOP_NT, 0, c->stream>>>(a);
+            cuda_check(cudaEventRecord(e0, c->stream), "tune record");
+            vars[v]<<<grid, HOP_NT, 0, c->stream>>>(a);
+            vars[v]<<<grid, HOP_NT, 0, c->stream>>>(a);
+            cuda_check(cudaEventRecord(e1, c->stream), "tune record");
+            cuda_check(cudaEventSynchronize(e1), "tune sync");
+            launch_counter() += 3;
+            float ms = 0;
+            cuda_check(cudaEventElapsedTime(&ms, e0, e1), "tune elapsed");
+            if (ms < best) {
+                best = ms;
+                choice = v;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        PSMS_LAUNCH_CHECK("hop_kernel (autotune)");
+    }
+    const int v = (choice >= 0 && choice < nvar) ? choice : (f32 ? 1 : 0);
+    vars[v]<<<grid, HOP_NT, 0, c->stream>>>(a);
     PSMS_LAUNCH_CHECK("hop_kernel");
     if (slot >= 0) prof_end(c, slot, bytes);
     return nct;
@@ -224,7 +291,7 @@ __global__ void __launch_bounds__(NT) norm2_kernel(View<typename S::elem> v, lon
     double acc = 0;
     for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
         const long long s = s_lo + i;
-        for (int q = 0; q < 12; ++q) acc += (double)norm2(S::ld(v.p + k * v.bs, q * v.cs + s - v.off));
+        for (int q = 0; q < 12; ++q) acc += (double)norm2(S::ld(v.p + k * v.bs, q, v.cs, s - v.off));
     }
     double t = block_sum<NT>(acc, sh);
     if (threadIdx.x == 0) partial[(long long)k * gridDim.x + blockIdx.x] = t;

@@ -208,7 +208,8 @@ static Pair pair_of(const Interp &it, int mode) {
 }
 
 static long long block_level_chunk(psms_ctx *c, const double2 *U, const double2 *Up, int N, int i0, int n, int mode,
-                                   uint64_t seed, uint64_t counter, double tol, int inner, double *d_delta) {
+                                   uint64_t seed, uint64_t counter, double tol, int inner, double *d_delta,
+                                   const int *d_mask) {
     const Geom &g = c->g;
     const long long V = g.V;
     const long long fs = 12 * V;
@@ -253,6 +254,7 @@ static long long block_level_chunk(psms_ctx *c, const double2 *U, const double2 
     q.resid = resid;
     q.xnorm2 = xn;
     q.status = status;
+    q.block_active = d_mask;
     block_solve(c, q);
     block_norm_kernel<128><<<dim3(nr, n), 128, 0, c->stream>>>(g, xi, fs, 0, nr, xin);
     PSMS_LAUNCH_CHECK("block_norm_kernel");
@@ -264,15 +266,17 @@ static long long block_level_chunk(psms_ctx *c, const double2 *U, const double2 
     cuda_check(cudaStreamSynchronize(c->stream), "iters");
     long long tot = 0;
     for (int v : hit) tot += v;
+    prof_block_bytes(c, tot, inner);
     return tot / nr;  // whole-lattice-equivalent iterations
 }
 
 long long block_level(psms_ctx *c, const double2 *U, const double2 *Up, int N, int mode, uint64_t seed,
-                      uint64_t counter, double tol, int inner, double *d_delta) {
+                      uint64_t counter, double tol, int inner, double *d_delta, const int *d_mask) {
     const int ch = chunk_size(c, N, inner == P64 ? 2600.0 : 2100.0);
     long long tot = 0;
     for (int i0 = 0; i0 < N; i0 += ch)
-        tot += block_level_chunk(c, U, Up, N, i0, std::min(ch, N - i0), mode, seed, counter, tol, inner, d_delta);
+        tot += block_level_chunk(c, U, Up, N, i0, std::min(ch, N - i0), mode, seed, counter, tol, inner, d_delta,
+                                 d_mask);
     return tot;
 }
 
@@ -308,7 +312,10 @@ static long long one_minus_PQ(psms_ctx *c, const double2 *U64, const float2 *U32
         check_status(c, status, nbh * N, "Schur block solve");
         cuda_check(cudaMemcpyAsync(hit.data(), iters, sizeof(int) * nbh * N, cudaMemcpyDeviceToHost, c->stream), "it");
         cuda_check(cudaStreamSynchronize(c->stream), "it");
-        for (int w : hit) tot += w;
+        long long here = 0;
+        for (int w : hit) here += w;
+        prof_block_bytes(c, here, inner);
+        tot += here;
     };
     // block iterations are returned in whole-lattice-equivalent units below
     HopCall h;
@@ -420,7 +427,7 @@ long long global_level(psms_ctx *c, const double2 *U, const double2 *Up, int N, 
 // ---------------------------------------------------------------------------
 __global__ void accept_kernel(const double *delta, int nb, int N, int per_block, uint64_t seed, uint64_t step,
                               uint64_t level, double extra_sum, const double *extra_per_block, double coef,
-                              double *dsum_out, int *acc) {
+                              double *dsum_out, int *acc, const int *mask) {
     if (per_block) {
         const int b = blockIdx.x * blockDim.x + threadIdx.x;
         if (b >= nb) return;
@@ -429,6 +436,7 @@ __global__ void accept_kernel(const double *delta, int nb, int N, int per_block,
         if (extra_per_block) d += coef * extra_per_block[b];
         const double u = uniforms(seed, TAG_ACCEPT, step, level, (uint64_t)b, 0).u[0];
         acc[b] = (d <= 0.0 || u < exp(-d)) ? 1 : 0;
+        if (mask && !mask[b]) acc[b] = 0;
         dsum_out[b] = d;
     } else {
         if (blockIdx.x != 0 || threadIdx.x != 0) return;
@@ -449,10 +457,20 @@ __global__ void accept_kernel(const double *delta, int nb, int N, int per_block,
 }
 
 void decide(psms_ctx *c, const double *d_delta, int nb, int N, int per_block, uint64_t seed, uint64_t step, int level,
-            double extra_sum, const double *d_extra_pb, double coef, double *d_dsum, int *d_acc) {
+            double extra_sum, const double *d_extra_pb, double coef, double *d_dsum, int *d_acc, const int *d_mask) {
     accept_kernel<<<(nb + 127) / 128, 128, 0, c->stream>>>(d_delta, nb, N, per_block, seed, step, (uint64_t)level,
-                                                           extra_sum, d_extra_pb, coef, d_dsum, d_acc);
+                                                           extra_sum, d_extra_pb, coef, d_dsum, d_acc, d_mask);
     PSMS_LAUNCH_CHECK("accept");
+}
+
+__global__ void f2d_kernel(const float *a, double *b, int n) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) b[t] = (double)a[t];
+}
+
+void float_to_double(psms_ctx *c, const float *a, double *b, int n) {
+    f2d_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(a, b, n);
+    PSMS_LAUNCH_CHECK("f2d");
 }
 
 }  // namespace psms

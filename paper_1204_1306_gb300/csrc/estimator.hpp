@@ -9,13 +9,16 @@ namespace psms {
 void noise(psms_ctx *c, double2 *out, int n, uint64_t seed, uint64_t counter, int level, int proj, int i0);
 // d_delta[b * N + i] (b = lexicographic block index); returns total inner iterations
 long long block_level(psms_ctx *c, const double2 *U, const double2 *Up, int N, int mode, uint64_t seed,
-                      uint64_t counter, double tol, int inner, double *d_delta);
+                      uint64_t counter, double tol, int inner, double *d_delta, const int *d_block_mask = nullptr);
 // d_delta[i]
 long long global_level(psms_ctx *c, const double2 *U, const double2 *Up, int N, int mode, uint64_t seed,
                        uint64_t counter, double tol, int inner, double *d_delta);
 // accept decisions: per block (or one decision on the sum), d_dsum[b] = Delta_b
 // (+ d_dsum[nb] = total when not per block)
 void decide(psms_ctx *c, const double *d_delta, int nb, int N, int per_block, uint64_t seed, uint64_t step, int level,
-            double extra_sum, const double *d_extra_pb, double coef, double *d_dsum, int *d_acc);
+            double extra_sum, const double *d_extra_pb, double coef, double *d_dsum, int *d_acc,
+            const int *d_mask = nullptr);
+// h (float, per block) -> FP64 copy
+void float_to_double(psms_ctx *c, const float *a, double *b, int n);
 
 }  // namespace psms

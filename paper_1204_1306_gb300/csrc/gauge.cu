@@ -408,8 +408,15 @@ void translate(psms_ctx *c, const double2 *src, double2 *dst, const int sh[4]) {
 }
 
 // out_i = ((N - i)/N) U + (i/N) U', i = i0 .. i0 + n - 1, FP64 and optional FP32
+// FP32 link element index of the FP64 element t = (mu * 9 + e) * V + s
+__device__ __forceinline__ long long f32_link_index(long long t, long long V) {
+    const long long s = t % V;
+    const long long me = t / V;
+    return link_idx<Store<float>>(V, (int)(me / 9), (int)(me % 9), s);
+}
+
 __global__ void interp_kernel(const double2 *U, const double2 *Up, double2 *out64, float2 *out32, long long n_el, int N,
-                              int i0) {
+                              int i0, long long V) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_el) return;
     const int i = i0 + blockIdx.y;
@@ -417,24 +424,24 @@ __global__ void interp_kernel(const double2 *U, const double2 *Up, double2 *out6
     const double2 u = U[t], v = Up[t];
     const double2 w = make_double2(a * u.x + b * v.x, a * u.y + b * v.y);
     if (out64) out64[(long long)blockIdx.y * n_el + t] = w;
-    if (out32) out32[(long long)blockIdx.y * n_el + t] = make_float2((float)w.x, (float)w.y);
+    if (out32) out32[(long long)blockIdx.y * n_el + f32_link_index(t, V)] = make_float2((float)w.x, (float)w.y);
 }
 
 void interpolate(psms_ctx *c, const double2 *U, const double2 *Up, double2 *out64, float2 *out32, int N, int i0,
                  int n) {
     const long long n_el = 36 * c->g.V;
     dim3 grid((unsigned)((n_el + 255) / 256), n);
-    interp_kernel<<<grid, 256, 0, c->stream>>>(U, Up, out64, out32, n_el, N, i0);
+    interp_kernel<<<grid, 256, 0, c->stream>>>(U, Up, out64, out32, n_el, N, i0, c->g.V);
     PSMS_LAUNCH_CHECK("interpolate");
 }
 
-__global__ void to_f32_kernel(const double2 *a, float2 *b, long long n) {
+__global__ void to_f32_kernel(const double2 *a, float2 *b, long long n, long long V) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) b[t] = make_float2((float)a[t].x, (float)a[t].y);
+    if (t < n) b[f32_link_index(t, V)] = make_float2((float)a[t].x, (float)a[t].y);
 }
 
 void links_to_f32(psms_ctx *c, const double2 *a, float2 *b, long long n_el) {
-    to_f32_kernel<<<(unsigned)((n_el + 255) / 256), 256, 0, c->stream>>>(a, b, n_el);
+    to_f32_kernel<<<(unsigned)((n_el + 255) / 256), 256, 0, c->stream>>>(a, b, n_el, c->g.V);
     PSMS_LAUNCH_CHECK("links_to_f32");
 }
 
@@ -507,9 +514,9 @@ __global__ void spinor_canon_kernel(Geom g, const double2 *canon, typename S::el
     for (int c = 0; c < 12; ++c) {
         if (to_native) {
             double2 v = canon[lex * 12 + c];
-            S::st(nat, c * g.V + s, mk<R>((R)v.x, (R)v.y));
+            S::st(nat, c, g.V, s, mk<R>((R)v.x, (R)v.y));
         } else {
-            cpx<R> v = S::ld(nat, c * g.V + s);
+            cpx<R> v = S::ld(nat, c, g.V, s);
             ((double2 *)canon)[lex * 12 + c] = make_double2((double)v.re, (double)v.im);
         }
     }

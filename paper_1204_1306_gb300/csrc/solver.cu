@@ -16,8 +16,11 @@
 #include "kernels.hpp"
 #include "solver.hpp"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <vector>
 
 namespace psms {
@@ -42,6 +45,38 @@ __device__ __forceinline__ double cta_sum(double v, double *sh) {
     return sh[NT / 32];
 }
 
+// Sum over the CTAs of a thread-block cluster (CL CTAs share one Dirichlet
+// block): each CTA reduces its part, the partials are read from every CTA's
+// shared memory (distributed shared memory) in rank order, so every CTA gets
+// the same deterministic total.
+template <int NT, int CL>
+__device__ __forceinline__ double cl_sum(double v, double *sh) {
+    const double t = cta_sum<NT>(v, sh);
+    if constexpr (CL == 1) {
+        return t;
+    } else {
+        namespace cg = cooperative_groups;
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        double tot = 0;
+        for (int q = 0; q < CL; ++q) tot += *cl.map_shared_rank(&sh[NT / 32], q);
+        cl.sync();
+        return tot;
+    }
+}
+
+// barrier between dependent phases: the CTA, or the whole cluster (release /
+// acquire at cluster scope makes the global-memory writes of one CTA visible
+// to the others)
+template <int CL>
+__device__ __forceinline__ void bar() {
+    if constexpr (CL == 1) {
+        __syncthreads();
+    } else {
+        cooperative_groups::this_cluster().sync();
+    }
+}
+
 // out_p = a*y_p + b*H^intra_p(in) on the block of rank r; returns this
 // thread's contribution to |out|^2.  Vectors are views (structure of arrays).
 template <class S, class SL, class SY>
@@ -49,11 +84,11 @@ __device__ __forceinline__ double block_hop(const Geom &g, const BlockInfo &bi, 
                                             const typename S::elem *in, long long in_cs, long long in_off,
                                             typename S::elem *out, long long out_cs, long long out_off,
                                             const typename SY::elem *y, long long y_cs, long long y_off, double a,
-                                            double b, const typename SL::elem *U) {
+                                            double b, const typename SL::elem *U, int jlo, int jhi) {
     using R = typename SL::R;
     double nrm = 0;
     const R sg = dag ? R(-1) : R(1);
-    for (int j = threadIdx.x; j < g.Vbh; j += blockDim.x) {
+    for (int j = jlo + threadIdx.x; j < jhi; j += blockDim.x) {
         int yy[4];
         const int ll = local_lex(g, p, j, yy);
         const long long s = (long long)p * g.Vh + (long long)r * g.Vbh + j;
@@ -126,31 +161,38 @@ struct BlockSolveArgs {
     double tol, delta;
     int maxit, max_outer;
     const int *sys_active;           // per system (nullable)
+    const int *block_active;         // per lexicographic block (nullable)
     int *iters;                      // [k * n_ranks + r]
     double *resid;                   // [k * n_ranks + r]
     double *xnorm2;                  // [k * n_ranks + r] |x_block|^2 (nullable)
     int *status;                     // [k * n_ranks + r]
 };
 
-template <class SV, class SL, int NT>
-__global__ void __launch_bounds__(NT) block_solve_kernel(const BlockSolveArgs a) {
+// The whole solve of one (block rl, system k) item by CL CTAs (a thread-block
+// cluster, CL = 1: one CTA) of NT threads; CTA rank q of the cluster works on
+// the sites j in [q Vbh/CL, (q+1) Vbh/CL) of each parity.
+template <class SV, class SL, int NT, int CL>
+__device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const int k, double *sh) {
     using E = typename SV::elem;
     using R = typename SL::R;
     using S64 = Store<double>;
-    __shared__ double sh[NT / 32 + 1];
     const Geom &g = a.g;
-    const int rl = blockIdx.x;
     const int r = a.rank_lo + rl;
-    const int k = blockIdx.y;
+    int crank = 0;
+    if constexpr (CL > 1) crank = (int)cooperative_groups::this_cluster().block_rank();
+    const int jlo = crank * (g.Vbh / CL), jhi = jlo + g.Vbh / CL;
+    const bool lead = (threadIdx.x == 0) && (crank == 0);
     const long long out_i = (long long)k * a.n_ranks + rl;
-    if (a.sys_active && !a.sys_active[k]) {
-        if (threadIdx.x == 0) {
+    const BlockInfo &bi = a.binfo[r];
+    if ((a.sys_active && !a.sys_active[k]) || (a.block_active && !a.block_active[bi.lex])) {
+        if (lead) {
             a.iters[out_i] = 0;
+            a.resid[out_i] = 0;
             a.status[out_i] = 0;
+            if (a.xnorm2) a.xnorm2[out_i] = 0;
         }
         return;
     }
-    const BlockInfo &bi = a.binfo[r];
     const long long V = g.V, Vh = g.Vh;
     const double2 *b = a.b.p + k * a.b.bs;
     double2 *x = a.x.p + k * a.x.bs;
@@ -176,18 +218,18 @@ __global__ void __launch_bounds__(NT) block_solve_kernel(const BlockSolveArgs a)
     // x = 0, |b|^2
     double bn = 0;
     for (int p = 0; p < 2; ++p)
-        for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+        for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
             const long long s = blo[p] + j;
             for (int q = 0; q < 12; ++q) {
                 x[q * a.x.cs + s - a.x.off] = make_double2(0, 0);
-                bn += (double)norm2(S64::ld(b, q * a.b.cs + s - a.b.off));
+                bn += (double)norm2(S64::ld(b, q, a.b.cs, s - a.b.off));
             }
         }
-    bn = cta_sum<NT>(bn, sh);
+    bn = cl_sum<NT, CL>(bn, sh);
     int total_it = 0, st = 0;
     double rel = 0;
     if (bn == 0.0) {
-        if (threadIdx.x == 0) {
+        if (lead) {
             a.iters[out_i] = 0;
             a.resid[out_i] = 0;
             a.status[out_i] = 0;
@@ -199,24 +241,24 @@ __global__ void __launch_bounds__(NT) block_solve_kernel(const BlockSolveArgs a)
         // FP64 true residual r64 = b - D_b x  (both parities)
         // r64_p = b_p + H_p(x_{1-p})/2, then subtract A x_p
         double rn = 0;
-        __syncthreads();
+        bar<CL>();
         for (int p = 0; p < 2; ++p) {
             block_hop<S64, S64, S64>(g, bi, r, p, 0, x, a.x.cs, a.x.off, r64, a.r64.cs, a.r64.off, b, a.b.cs,
-                                     a.b.off, 1.0, 0.5, U64);
+                                     a.b.off, 1.0, 0.5, U64, jlo, jhi);
         }
-        __syncthreads();
+        bar<CL>();
         for (int p = 0; p < 2; ++p)
-            for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+            for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
                 const long long s = blo[p] + j;
                 for (int q = 0; q < 12; ++q) {
-                    cpx<double> rv = S64::ld(r64, q * a.r64.cs + s - a.r64.off);
-                    cpx<double> xv = S64::ld(x, q * a.x.cs + s - a.x.off);
+                    cpx<double> rv = S64::ld(r64, q, a.r64.cs, s - a.r64.off);
+                    cpx<double> xv = S64::ld(x, q, a.x.cs, s - a.x.off);
                     rv = rv - A * xv;
-                    S64::st(r64, q * a.r64.cs + s - a.r64.off, rv);
+                    S64::st(r64, q, a.r64.cs, s - a.r64.off, rv);
                     rn += norm2(rv);
                 }
             }
-        rn = cta_sum<NT>(rn, sh);
+        rn = cl_sum<NT, CL>(rn, sh);
         rel = sqrt(rn / bn);
         if (rel <= a.tol) break;
         if (outer >= a.max_outer || total_it >= a.maxit) {
@@ -226,123 +268,176 @@ __global__ void __launch_bounds__(NT) block_solve_kernel(const BlockSolveArgs a)
         // inner rhs = r64 / |r64| in inner precision
         const double scale = 1.0 / sqrt(rn);
         for (int p = 0; p < 2; ++p)
-            for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+            for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
                 const long long s = blo[p] + j;
                 for (int q = 0; q < 12; ++q) {
-                    cpx<double> rv = S64::ld(r64, q * a.r64.cs + s - a.r64.off);
-                    SV::st(v.rhs, q * V + s, mk<R>((R)(rv.re * scale), (R)(rv.im * scale)));
+                    cpx<double> rv = S64::ld(r64, q, a.r64.cs, s - a.r64.off);
+                    SV::st(v.rhs, q, V, s, mk<R>((R)(rv.re * scale), (R)(rv.im * scale)));
                 }
             }
-        __syncthreads();
+        bar<CL>();
         // bhat_o = rhs_o + H_o(rhs_e)/(2A)
         double bb = block_hop<SV, SL, SV>(g, bi, r, 1, 0, v.rhs, V, 0, v.bhat, Vh, Vh, v.rhs, V, 0, 1.0,
-                                          0.5 / A, Uin);
-        bb = cta_sum<NT>(bb, sh);
+                                          0.5 / A, Uin, jlo, jhi);
+        bb = cl_sum<NT, CL>(bb, sh);
         // e_o = 0, rho = bhat, res = Dhat^dag rho, p = res
-        for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+        for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
             const long long s = blo[1] + j;
             for (int q = 0; q < 12; ++q) {
-                SV::st(v.e, q * V + s, mk<R>(0, 0));
-                SV::st(v.rho, q * Vh + s - Vh, SV::ld(v.bhat, q * Vh + s - Vh));
+                SV::st(v.e, q, V, s, mk<R>(0, 0));
+                SV::st(v.rho, q, Vh, s - Vh, SV::ld(v.bhat, q, Vh, s - Vh));
             }
         }
-        __syncthreads();
-        block_hop<SV, SL, SV>(g, bi, r, 0, 1, v.rho, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin);
-        __syncthreads();
-        double rr = block_hop<SV, SL, SV>(g, bi, r, 1, 1, v.t, Vh, 0, v.res, Vh, Vh, v.rho, Vh, Vh, A, c4, Uin);
-        rr = cta_sum<NT>(rr, sh);
-        for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+        bar<CL>();
+        block_hop<SV, SL, SV>(g, bi, r, 0, 1, v.rho, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin, jlo, jhi);
+        bar<CL>();
+        double rr = block_hop<SV, SL, SV>(g, bi, r, 1, 1, v.t, Vh, 0, v.res, Vh, Vh, v.rho, Vh, Vh, A, c4, Uin, jlo, jhi);
+        rr = cl_sum<NT, CL>(rr, sh);
+        for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
             const long long s = blo[1] + j - Vh;
-            for (int q = 0; q < 12; ++q) SV::st(v.pp, q * Vh + s, SV::ld(v.res, q * Vh + s));
+            for (int q = 0; q < 12; ++q) SV::st(v.pp, q, Vh, s, SV::ld(v.res, q, Vh, s));
         }
-        __syncthreads();
+        bar<CL>();
         const double target = a.delta * a.delta * bb;
         int it = 0;
         while (total_it + it < a.maxit) {
             // q = Dhat p
-            block_hop<SV, SL, SV>(g, bi, r, 0, 0, v.pp, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin);
-            __syncthreads();
-            double qq = block_hop<SV, SL, SV>(g, bi, r, 1, 0, v.t, Vh, 0, v.q, Vh, Vh, v.pp, Vh, Vh, A, c4, Uin);
-            qq = cta_sum<NT>(qq, sh);
+            block_hop<SV, SL, SV>(g, bi, r, 0, 0, v.pp, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin, jlo, jhi);
+            bar<CL>();
+            double qq = block_hop<SV, SL, SV>(g, bi, r, 1, 0, v.t, Vh, 0, v.q, Vh, Vh, v.pp, Vh, Vh, A, c4, Uin, jlo, jhi);
+            qq = cl_sum<NT, CL>(qq, sh);
             const R alpha = (R)(rr / qq);
             double rhorho = 0;
-            for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+            for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
                 const long long so = blo[1] + j;
                 const long long sh_ = so - Vh;
                 for (int q = 0; q < 12; ++q) {
-                    cpx<R> e = SV::ld(v.e, q * V + so);
-                    cpx<R> pv = SV::ld(v.pp, q * Vh + sh_);
-                    cpx<R> qv = SV::ld(v.q, q * Vh + sh_);
-                    cpx<R> ro = SV::ld(v.rho, q * Vh + sh_);
+                    cpx<R> e = SV::ld(v.e, q, V, so);
+                    cpx<R> pv = SV::ld(v.pp, q, Vh, sh_);
+                    cpx<R> qv = SV::ld(v.q, q, Vh, sh_);
+                    cpx<R> ro = SV::ld(v.rho, q, Vh, sh_);
                     e = e + alpha * pv;
                     ro = ro - alpha * qv;
-                    SV::st(v.e, q * V + so, e);
-                    SV::st(v.rho, q * Vh + sh_, ro);
+                    SV::st(v.e, q, V, so, e);
+                    SV::st(v.rho, q, Vh, sh_, ro);
                     rhorho += (double)norm2(ro);
                 }
             }
-            rhorho = cta_sum<NT>(rhorho, sh);
+            rhorho = cl_sum<NT, CL>(rhorho, sh);
             ++it;
             if (rhorho <= target) break;
             // sv = Dhat^dag q
-            block_hop<SV, SL, SV>(g, bi, r, 0, 1, v.q, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin);
-            __syncthreads();
-            block_hop<SV, SL, SV>(g, bi, r, 1, 1, v.t, Vh, 0, v.sv, Vh, Vh, v.q, Vh, Vh, A, c4, Uin);
-            __syncthreads();
+            block_hop<SV, SL, SV>(g, bi, r, 0, 1, v.q, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin, jlo, jhi);
+            bar<CL>();
+            block_hop<SV, SL, SV>(g, bi, r, 1, 1, v.t, Vh, 0, v.sv, Vh, Vh, v.q, Vh, Vh, A, c4, Uin, jlo, jhi);
+            bar<CL>();
             double rr_new = 0;
-            for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+            for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
                 const long long sh_ = blo[1] + j - Vh;
                 for (int q = 0; q < 12; ++q) {
-                    cpx<R> rv = SV::ld(v.res, q * Vh + sh_);
-                    rv = rv - alpha * SV::ld(v.sv, q * Vh + sh_);
-                    SV::st(v.res, q * Vh + sh_, rv);
+                    cpx<R> rv = SV::ld(v.res, q, Vh, sh_);
+                    rv = rv - alpha * SV::ld(v.sv, q, Vh, sh_);
+                    SV::st(v.res, q, Vh, sh_, rv);
                     rr_new += (double)norm2(rv);
                 }
             }
-            rr_new = cta_sum<NT>(rr_new, sh);
+            rr_new = cl_sum<NT, CL>(rr_new, sh);
             const R beta = (R)(rr_new / rr);
             rr = rr_new;
-            for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+            for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
                 const long long sh_ = blo[1] + j - Vh;
                 for (int q = 0; q < 12; ++q) {
-                    cpx<R> pv = SV::ld(v.pp, q * Vh + sh_);
-                    SV::st(v.pp, q * Vh + sh_, SV::ld(v.res, q * Vh + sh_) + beta * pv);
+                    cpx<R> pv = SV::ld(v.pp, q, Vh, sh_);
+                    SV::st(v.pp, q, Vh, sh_, SV::ld(v.res, q, Vh, sh_) + beta * pv);
                 }
             }
-            __syncthreads();
+            bar<CL>();
         }
         total_it += it;
         // e_e = (rhs_e + H_e(e_o)/2) / A
-        block_hop<SV, SL, SV>(g, bi, r, 0, 0, v.e, V, 0, v.e, V, 0, v.rhs, V, 0, 1.0 / A, 0.5 / A, Uin);
-        __syncthreads();
+        block_hop<SV, SL, SV>(g, bi, r, 0, 0, v.e, V, 0, v.e, V, 0, v.rhs, V, 0, 1.0 / A, 0.5 / A, Uin, jlo, jhi);
+        bar<CL>();
         // x += e / scale (FP64)
         const double unscale = sqrt(rn);
         for (int p = 0; p < 2; ++p)
-            for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+            for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
                 const long long s = blo[p] + j;
                 for (int q = 0; q < 12; ++q) {
-                    cpx<R> ev = SV::ld(v.e, q * V + s);
-                    cpx<double> xv = S64::ld(x, q * a.x.cs + s - a.x.off);
+                    cpx<R> ev = SV::ld(v.e, q, V, s);
+                    cpx<double> xv = S64::ld(x, q, a.x.cs, s - a.x.off);
                     xv = xv + unscale * mk<double>((double)ev.re, (double)ev.im);
-                    S64::st(x, q * a.x.cs + s - a.x.off, xv);
+                    S64::st(x, q, a.x.cs, s - a.x.off, xv);
                 }
             }
-        __syncthreads();
+        bar<CL>();
     }
     double xn = 0;
     if (a.xnorm2) {
         for (int p = 0; p < 2; ++p)
-            for (int j = threadIdx.x; j < g.Vbh; j += NT) {
+            for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
                 const long long s = blo[p] + j;
-                for (int q = 0; q < 12; ++q) xn += norm2(S64::ld(x, q * a.x.cs + s - a.x.off));
+                for (int q = 0; q < 12; ++q) xn += norm2(S64::ld(x, q, a.x.cs, s - a.x.off));
             }
-        xn = cta_sum<NT>(xn, sh);
+        xn = cl_sum<NT, CL>(xn, sh);
     }
-    if (threadIdx.x == 0) {
+    if (lead) {
         a.iters[out_i] = total_it;
         a.resid[out_i] = rel;
         a.status[out_i] = st;
         if (a.xnorm2) a.xnorm2[out_i] = xn;
+    }
+}
+
+// one CTA per (block, system): grid (n_ranks, n_sys)
+template <class SV, class SL, int NT>
+__global__ void __launch_bounds__(NT) block_solve_kernel(const BlockSolveArgs a) {
+    __shared__ double sh[NT / 32 + 1];
+    block_solve_item<SV, SL, NT, 1>(a, blockIdx.x, blockIdx.y, sh);
+}
+
+// CL CTAs (one cluster) per (block, system): grid (n_ranks * CL, n_sys),
+// cluster dimension (CL, 1, 1); MINB resident CTAs per SM caps registers
+template <class SV, class SL, int NT, int CL, int MINB>
+__global__ void __launch_bounds__(NT, MINB) block_solve_cluster_kernel(const BlockSolveArgs a) {
+    __shared__ double sh[NT / 32 + 1];
+    block_solve_item<SV, SL, NT, CL>(a, blockIdx.x / CL, blockIdx.y, sh);
+}
+
+template <class SV, class SL, int CL, int MINB>
+static void launch_block_cl(psms_ctx *c, const BlockSolveArgs &a, int n_ranks, int n_sys) {
+    constexpr int NT = 128;
+    if constexpr (CL == 1) {
+        block_solve_cluster_kernel<SV, SL, NT, 1, MINB><<<dim3(n_ranks, n_sys), NT, 0, c->stream>>>(a);
+        PSMS_LAUNCH_CHECK("block_solve_cluster_kernel");
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(n_ranks * CL, n_sys, 1);
+        cfg.blockDim = dim3(NT, 1, 1);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = c->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cuda_check(cudaLaunchKernelEx(&cfg, block_solve_cluster_kernel<SV, SL, NT, CL, MINB>, a), "cluster launch");
+        PSMS_LAUNCH_CHECK("block_solve_cluster_kernel");
+    }
+}
+
+template <class SV, class SL>
+static void launch_block_variant(psms_ctx *c, const BlockSolveArgs &a, int n_ranks, int n_sys, int cl, int minb) {
+    switch (cl * 10 + minb) {
+        case 11: launch_block_cl<SV, SL, 1, 1>(c, a, n_ranks, n_sys); break;
+        case 14: launch_block_cl<SV, SL, 1, 4>(c, a, n_ranks, n_sys); break;
+        case 21: launch_block_cl<SV, SL, 2, 1>(c, a, n_ranks, n_sys); break;
+        case 24: launch_block_cl<SV, SL, 2, 4>(c, a, n_ranks, n_sys); break;
+        case 41: launch_block_cl<SV, SL, 4, 1>(c, a, n_ranks, n_sys); break;
+        case 44: launch_block_cl<SV, SL, 4, 4>(c, a, n_ranks, n_sys); break;
+        case 81: launch_block_cl<SV, SL, 8, 1>(c, a, n_ranks, n_sys); break;
+        default: launch_block_cl<SV, SL, 8, 4>(c, a, n_ranks, n_sys); break;
     }
 }
 
@@ -373,17 +468,58 @@ void block_solve(psms_ctx *c, const BlockSolveReq &q) {
     a.maxit = q.maxit;
     a.max_outer = in64 ? 4 : 12;
     a.sys_active = q.sys_active;
+    a.block_active = q.block_active;
     a.iters = q.iters;
     a.resid = q.resid;
     a.xnorm2 = q.xnorm2;
     a.status = q.status;
-    dim3 grid(q.n_ranks, q.n_sys);
-    const int NT = 128;
-    if (in64)
-        block_solve_kernel<Store<double>, Store<double>, NT><<<grid, NT, 0, c->stream>>>(a);
-    else
-        block_solve_kernel<Store<float>, Store<float>, NT><<<grid, NT, 0, c->stream>>>(a);
-    PSMS_LAUNCH_CHECK("block_solve_kernel");
+    // Variants (cluster size CL, min CTAs per SM): one block solved by CL
+    // CTAs of a thread-block cluster.  The autotuner times every admissible
+    // variant once on the first solve of each (precision, block size,
+    // batched or not) and keeps the fastest; a solve is idempotent (x is set
+    // from b), so the tuning runs leave the result unchanged.
+    struct Var {
+        int cl, minb;
+    };
+    static const Var vars[] = {{1, 1}, {1, 4}, {2, 1}, {2, 4}, {4, 1}, {4, 4}, {8, 1}, {8, 4}};
+    const int nvar = 8;
+    auto admissible = [&](int v) { return vars[v].cl == 1 || g.Vbh / vars[v].cl >= 128; };
+    auto launch = [&](int v) {
+        if (in64)
+            launch_block_variant<Store<double>, Store<double>>(c, a, q.n_ranks, q.n_sys, vars[v].cl, vars[v].minb);
+        else
+            launch_block_variant<Store<float>, Store<float>>(c, a, q.n_ranks, q.n_sys, vars[v].cl, vars[v].minb);
+    };
+    const long long key = ((long long)q.inner_prec << 40) | ((long long)g.Vbh << 8) | (q.n_sys > 1 ? 1 : 0);
+    auto it = c->block_variant.find(key);
+    int choice = it == c->block_variant.end() ? -1 : it->second;
+    if (c->forced_block_variant >= 0) choice = admissible(c->forced_block_variant) ? c->forced_block_variant : 0;
+    if (choice < 0 && c->autotune) {
+        cudaEvent_t e0, e1;
+        cuda_check(cudaEventCreate(&e0), "tune event");
+        cuda_check(cudaEventCreate(&e1), "tune event");
+        float best = 1e30f;
+        for (int v = 0; v < nvar; ++v) {
+            if (!admissible(v)) continue;
+            cuda_check(cudaEventRecord(e0, c->stream), "tune record");
+            launch(v);
+            cuda_check(cudaEventRecord(e1, c->stream), "tune record");
+            cuda_check(cudaEventSynchronize(e1), "tune sync");
+            float ms = 0;
+            cuda_check(cudaEventElapsedTime(&ms, e0, e1), "tune elapsed");
+            if (ms < best) {
+                best = ms;
+                choice = v;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    if (choice < 0) choice = 0;
+    if (c->forced_block_variant < 0) c->block_variant[key] = choice;
+    const int slot = c->prof ? prof_block_begin(c) : -1;
+    launch(choice);
+    if (slot >= 0) prof_block_end(c, slot);
 }
 
 // ---------------------------------------------------------------------------
@@ -491,20 +627,20 @@ __global__ void __launch_bounds__(NT) cg_update_kernel(const CGS *st, View<typen
     if (i < n) {
         const long long s = s_lo + i;
         for (int c = 0; c < 12; ++c) {
-            const long long ie = k * e.bs + c * e.cs + s - e.off;
-            const long long ip = k * pp.bs + c * pp.cs + s - pp.off;
-            cpx<R> ev = S::ld(e.p, ie) + alpha * S::ld(pp.p, ip);
-            S::st(e.p, ie, ev);
-            const long long iq = k * q.bs + c * q.cs + s - q.off;
-            const long long ir = k * rho.bs + c * rho.cs + s - rho.off;
-            cpx<R> ro = S::ld(rho.p, ir) - alpha * S::ld(q.p, iq);
-            S::st(rho.p, ir, ro);
+            const long long ie = k * e.bs + S::idx(c, e.cs, s - e.off);
+            const long long ip = k * pp.bs + S::idx(c, pp.cs, s - pp.off);
+            cpx<R> ev = S::ldi(e.p, ie) + alpha * S::ldi(pp.p, ip);
+            S::sti(e.p, ie, ev);
+            const long long iq = k * q.bs + S::idx(c, q.cs, s - q.off);
+            const long long ir = k * rho.bs + S::idx(c, rho.cs, s - rho.off);
+            cpx<R> ro = S::ldi(rho.p, ir) - alpha * S::ldi(q.p, iq);
+            S::sti(rho.p, ir, ro);
             a2 += (double)norm2(ro);
             if (!skip_r) {
-                const long long is = k * sv.bs + c * sv.cs + s - sv.off;
-                const long long ires = k * res.bs + c * res.cs + s - res.off;
-                cpx<R> rv = S::ld(res.p, ires) - alpha * S::ld(sv.p, is);
-                S::st(res.p, ires, rv);
+                const long long is = k * sv.bs + S::idx(c, sv.cs, s - sv.off);
+                const long long ires = k * res.bs + S::idx(c, res.cs, s - res.off);
+                cpx<R> rv = S::ldi(res.p, ires) - alpha * S::ldi(sv.p, is);
+                S::sti(res.p, ires, rv);
                 a1 += (double)norm2(rv);
             }
         }
@@ -542,9 +678,9 @@ __global__ void __launch_bounds__(NT) cg_pupdate_kernel(const CGS *st, View<type
     if (i >= n) return;
     const long long s = s_lo + i;
     for (int c = 0; c < 12; ++c) {
-        const long long ip = k * pp.bs + c * pp.cs + s - pp.off;
-        const long long ir = k * res.bs + c * res.cs + s - res.off;
-        S::st(pp.p, ip, S::ld(res.p, ir) + beta * S::ld(pp.p, ip));
+        const long long ip = k * pp.bs + S::idx(c, pp.cs, s - pp.off);
+        const long long ir = k * res.bs + S::idx(c, res.cs, s - res.off);
+        S::sti(pp.p, ip, S::ldi(res.p, ir) + beta * S::ldi(pp.p, ip));
     }
 }
 
@@ -562,7 +698,7 @@ __global__ void __launch_bounds__(NT) scale_convert_kernel(View<typename SD::ele
     const long long s = s_lo + i;
     for (int c = 0; c < 12; ++c) {
         double2 v = src.p[k * src.bs + c * src.cs + s - src.off];
-        SD::st(dst.p, k * dst.bs + c * dst.cs + s - dst.off,
+        SD::st(dst.p + k * dst.bs, c, dst.cs, s - dst.off,
                mk<typename SD::R>((typename SD::R)(sc * v.x), (typename SD::R)(sc * v.y)));
     }
 }
@@ -578,7 +714,7 @@ __global__ void __launch_bounds__(NT) accumulate_kernel(View<double2> x, View<ty
     const double sc = sqrt(nrm2[k]);
     const long long s = s_lo + i;
     for (int c = 0; c < 12; ++c) {
-        cpx<typename SE::R> ev = SE::ld(e.p, k * e.bs + c * e.cs + s - e.off);
+        cpx<typename SE::R> ev = SE::ld(e.p + k * e.bs, c, e.cs, s - e.off);
         double2 &xv = x.p[k * x.bs + c * x.cs + s - x.off];
         xv.x += sc * (double)ev.re;
         xv.y += sc * (double)ev.im;
@@ -982,6 +1118,7 @@ extern "C" psms_status psms_block_solve_noalloc(psms_ctx *ctx, int field, int op
         a.maxit = maxit;
         a.max_outer = 4;
         a.sys_active = nullptr;
+        a.block_active = nullptr;
         a.iters = iters;
         a.resid = resid;
         a.xnorm2 = nullptr;
@@ -1003,3 +1140,297 @@ extern "C" psms_status psms_block_solve_noalloc(psms_ctx *ctx, int field, int op
     }
     return PSMS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batched block solves over several lattices in one persistent launch
+// (a plan: autotuned schedule, CUDA-graph replay)
+// ---------------------------------------------------------------------------
+namespace psms {
+
+struct MultiArgs {
+    const BlockSolveArgs *probs;  // per lattice
+    const int4 *items;            // (problem, block rl, system k, -)
+    int n_items;
+    int *counter;                 // next item (reset to 0 before every launch)
+};
+
+// Persistent CTAs take items from an atomic counter until the list is empty;
+// no CTA waits for another.
+template <class SV, class SL, int NT>
+__global__ void __launch_bounds__(NT) block_solve_multi_kernel(const MultiArgs m) {
+    __shared__ double sh[NT / 32 + 1];
+    __shared__ int item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = atomicAdd(m.counter, 1);
+        __syncthreads();
+        const int it = item;
+        if (it >= m.n_items) return;
+        const int4 w = m.items[it];
+        block_solve_item<SV, SL, NT, 1>(m.probs[w.x], w.y, w.z, sh);
+    }
+}
+
+__global__ void multi_summary_kernel(const BlockSolveArgs *probs, int n_probs, const int *n_per, double *out) {
+    if (blockIdx.x || threadIdx.x) return;
+    double it = 0, worst = 0, st = 0;
+    for (int p = 0; p < n_probs; ++p)
+        for (int i = 0; i < n_per[p]; ++i) {
+            it += probs[p].iters[i];
+            worst = probs[p].resid[i] > worst ? probs[p].resid[i] : worst;
+            if (probs[p].status[i]) st = 1;
+        }
+    out[0] = it;
+    out[1] = worst;
+    out[2] = st;
+}
+
+}  // namespace psms
+
+struct psms_block_plan {
+    std::vector<psms_block_problem> probs;
+    std::vector<psms::BlockSolveArgs> h_args;
+    std::vector<int> n_per;
+    std::vector<void *> allocs;
+    psms::BlockSolveArgs *d_args = nullptr;
+    int *d_nper = nullptr;
+    int4 *d_items = nullptr;
+    int *d_counter = nullptr;
+    double *d_summary = nullptr;
+    int n_items = 0;
+    int inner = 0;
+    int ctas = 0, order = 0;
+    double tuned_ms = 0;
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::string err;
+};
+
+namespace psms {
+
+static void plan_alloc(psms_block_plan *pl, void **p, size_t bytes) {
+    cuda_check(cudaMalloc(p, bytes), "plan alloc");
+    pl->allocs.push_back(*p);
+}
+
+// work orders: 0 lattice-major (block fastest), 1 system-major across
+// lattices, 2 round-robin over lattices
+static std::vector<int4> make_items(const psms_block_plan *pl, int order) {
+    std::vector<int4> it;
+    const int np = (int)pl->probs.size();
+    if (order == 0) {
+        for (int p = 0; p < np; ++p)
+            for (int k = 0; k < pl->probs[p].n_rhs; ++k)
+                for (int r = 0; r < pl->h_args[p].n_ranks; ++r) it.push_back(make_int4(p, r, k, 0));
+    } else if (order == 1) {
+        int kmax = 0;
+        for (auto &q : pl->probs) kmax = std::max(kmax, q.n_rhs);
+        for (int k = 0; k < kmax; ++k)
+            for (int p = 0; p < np; ++p)
+                if (k < pl->probs[p].n_rhs)
+                    for (int r = 0; r < pl->h_args[p].n_ranks; ++r) it.push_back(make_int4(p, r, k, 0));
+    } else {
+        std::vector<std::vector<int4>> per(np);
+        for (int p = 0; p < np; ++p)
+            for (int k = 0; k < pl->probs[p].n_rhs; ++k)
+                for (int r = 0; r < pl->h_args[p].n_ranks; ++r) per[p].push_back(make_int4(p, r, k, 0));
+        size_t mx = 0;
+        for (auto &v : per) mx = std::max(mx, v.size());
+        for (size_t i = 0; i < mx; ++i)
+            for (int p = 0; p < np; ++p)
+                if (i < per[p].size()) it.push_back(per[p][i]);
+    }
+    return it;
+}
+
+static void plan_launch(psms_block_plan *pl, cudaStream_t s, int ctas) {
+    MultiArgs m{pl->d_args, pl->d_items, pl->n_items, pl->d_counter};
+    cuda_check(cudaMemsetAsync(pl->d_counter, 0, sizeof(int), s), "plan counter");
+    const int NT = 128;
+    if (pl->inner == P64)
+        block_solve_multi_kernel<Store<double>, Store<double>, NT><<<ctas, NT, 0, s>>>(m);
+    else
+        block_solve_multi_kernel<Store<float>, Store<float>, NT><<<ctas, NT, 0, s>>>(m);
+    PSMS_LAUNCH_CHECK("block_solve_multi_kernel");
+    multi_summary_kernel<<<1, 1, 0, s>>>(pl->d_args, (int)pl->probs.size(), pl->d_nper, pl->d_summary);
+    PSMS_LAUNCH_CHECK("multi_summary_kernel");
+}
+
+static void plan_destroy(psms_block_plan *pl) {
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->stream) cudaStreamDestroy(pl->stream);
+    for (void *p : pl->allocs) cudaFree(p);
+    delete pl;
+}
+
+}  // namespace psms
+
+extern "C" {
+
+psms_status psms_block_plan_create(const psms_block_problem *probs, int n_probs, double tol, int maxit,
+                                   int inner_prec, psms_block_plan **out) {
+    using namespace psms;
+    if (!probs || n_probs < 1 || !out) return PSMS_EINVAL;
+    *out = nullptr;
+    psms_block_plan *pl = new psms_block_plan();
+    try {
+        if (!(tol > 0) || maxit < 1) fail(PSMS_EINVAL, "tol > 0 and maxit >= 1");
+        if (inner_prec != P64 && inner_prec != P32) fail(PSMS_EINVAL, "inner precision FP64 or FP32");
+        pl->inner = inner_prec;
+        pl->probs.assign(probs, probs + n_probs);
+        cuda_check(cudaStreamCreateWithFlags(&pl->stream, cudaStreamNonBlocking), "plan stream");
+        for (int p = 0; p < n_probs; ++p) {
+            const psms_block_problem &q = probs[p];
+            psms_ctx *c = q.ctx;
+            if (!c || !q.b_dev || !q.x_dev || q.n_rhs < 1) fail(PSMS_EINVAL, "bad problem description");
+            check_field(c, q.field);
+            cuda_check(cudaStreamSynchronize(c->stream), "plan sync");
+            const Geom &g = c->g;
+            const long long V = g.V;
+            BlockSolveArgs a;
+            a.g = g;
+            a.binfo = c->d_binfo;
+            a.A = c->A;
+            a.rank_lo = 0;
+            a.n_ranks = g.nblocks;
+            a.b = View<double2>{(double2 *)q.b_dev, V, 0, 12 * V};
+            a.x = View<double2>{(double2 *)q.x_dev, V, 0, 12 * V};
+            void *r64 = nullptr;
+            plan_alloc(pl, &r64, sizeof(double2) * 12 * (size_t)V * q.n_rhs);
+            a.r64 = View<double2>{(double2 *)r64, V, 0, 12 * V};
+            a.U64 = c->U64[q.field];
+            a.U64_bs = 0;
+            const bool in64 = inner_prec == P64;
+            a.Uin = in64 ? (const void *)c->U64[q.field] : (const void *)links32(c, q.field);
+            cuda_check(cudaStreamSynchronize(c->stream), "plan sync");
+            a.Uin_bs = 0;
+            const long long per_sys = 24 * V + 7 * 12 * (long long)g.Vh;
+            void *vin = nullptr;
+            plan_alloc(pl, &vin, (in64 ? sizeof(double2) : sizeof(float2)) * (size_t)per_sys * q.n_rhs);
+            a.vin = vin;
+            a.vin_bs = per_sys;
+            a.tol = tol;
+            a.delta = in64 ? std::max(0.1 * tol, 1e-15) : 1e-6;
+            a.maxit = maxit;
+            a.max_outer = in64 ? 4 : 12;
+            a.sys_active = nullptr;
+            a.block_active = nullptr;
+            const int n_out = g.nblocks * q.n_rhs;
+            void *it = nullptr, *rs = nullptr, *st = nullptr;
+            plan_alloc(pl, &it, sizeof(int) * n_out);
+            plan_alloc(pl, &rs, sizeof(double) * n_out);
+            plan_alloc(pl, &st, sizeof(int) * n_out);
+            a.iters = (int *)it;
+            a.resid = (double *)rs;
+            a.status = (int *)st;
+            a.xnorm2 = nullptr;
+            pl->h_args.push_back(a);
+            pl->n_per.push_back(n_out);
+            pl->n_items += n_out;
+        }
+        plan_alloc(pl, (void **)&pl->d_args, sizeof(BlockSolveArgs) * n_probs);
+        plan_alloc(pl, (void **)&pl->d_nper, sizeof(int) * n_probs);
+        plan_alloc(pl, (void **)&pl->d_items, sizeof(int4) * pl->n_items);
+        plan_alloc(pl, (void **)&pl->d_counter, sizeof(int));
+        plan_alloc(pl, (void **)&pl->d_summary, sizeof(double) * 3);
+        cuda_check(cudaMemcpy(pl->d_args, pl->h_args.data(), sizeof(BlockSolveArgs) * n_probs, cudaMemcpyHostToDevice),
+                   "plan args");
+        cuda_check(cudaMemcpy(pl->d_nper, pl->n_per.data(), sizeof(int) * n_probs, cudaMemcpyHostToDevice), "plan n");
+        // autotune: persistent grid size x work order, each candidate timed once
+        // (the results do not depend on the schedule)
+        int dev = 0, nsm = 0;
+        cuda_check(cudaGetDevice(&dev), "device");
+        cuda_check(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "sm count");
+        cudaEvent_t e0, e1;
+        cuda_check(cudaEventCreate(&e0), "event");
+        cuda_check(cudaEventCreate(&e1), "event");
+        float best = 1e30f;
+        for (int order = 0; order < 3; ++order) {
+            std::vector<int4> items = make_items(pl, order);
+            cuda_check(cudaMemcpy(pl->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice),
+                       "plan items");
+            for (int per_sm : {1, 2, 3, 4}) {
+                const int ctas = std::min(pl->n_items, per_sm * nsm);
+                cuda_check(cudaEventRecord(e0, pl->stream), "event");
+                plan_launch(pl, pl->stream, ctas);
+                cuda_check(cudaEventRecord(e1, pl->stream), "event");
+                cuda_check(cudaEventSynchronize(e1), "event");
+                float ms = 0;
+                cuda_check(cudaEventElapsedTime(&ms, e0, e1), "event");
+                if (ms < best) {
+                    best = ms;
+                    pl->ctas = ctas;
+                    pl->order = order;
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        pl->tuned_ms = best;
+        std::vector<int4> items = make_items(pl, pl->order);
+        cuda_check(cudaMemcpy(pl->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice),
+                   "plan items");
+        // capture the tuned launch sequence once; runs replay the graph
+        cuda_check(cudaStreamBeginCapture(pl->stream, cudaStreamCaptureModeThreadLocal), "capture begin");
+        plan_launch(pl, pl->stream, pl->ctas);
+        cuda_check(cudaStreamEndCapture(pl->stream, &pl->graph), "capture end");
+        cuda_check(cudaGraphInstantiate(&pl->exec, pl->graph, 0), "graph instantiate");
+    } catch (const Error &e) {
+        psms_status st = e.st;
+        if (n_probs >= 1 && probs[0].ctx) probs[0].ctx->err = e.msg;
+        plan_destroy(pl);
+        return st;
+    }
+    *out = pl;
+    return PSMS_OK;
+}
+
+psms_status psms_block_plan_run(psms_block_plan *pl, void *stream, psms_solve_info *info) {
+    using namespace psms;
+    if (!pl) return PSMS_EINVAL;
+    try {
+        cudaStream_t s = (cudaStream_t)stream;
+        // FP32 link copies must follow changes of the gauge fields
+        for (size_t p = 0; p < pl->probs.size(); ++p) {
+            psms_ctx *c = pl->probs[p].ctx;
+            if (pl->inner == P32 && !c->u32_ok[pl->probs[p].field]) {
+                links32(c, pl->probs[p].field);
+                cuda_check(cudaStreamSynchronize(c->stream), "links sync");
+            }
+        }
+        cuda_check(cudaGraphLaunch(pl->exec, s), "graph launch");
+        double h[3];
+        cuda_check(cudaMemcpyAsync(h, pl->d_summary, sizeof(h), cudaMemcpyDeviceToHost, s), "plan summary");
+        cuda_check(cudaStreamSynchronize(s), "plan sync");
+        if (info) {
+            info->outer_iters = 0;
+            info->inner_iters = (long long)h[0];
+            info->true_residual = h[1];
+            info->n_systems = pl->n_items;
+        }
+        if (h[2] != 0.0) fail(PSMS_ENOCONV, "a block solve missed its tolerance");
+    } catch (const Error &e) {
+        pl->err = e.msg;
+        return e.st;
+    }
+    return PSMS_OK;
+}
+
+psms_status psms_block_plan_schedule(const psms_block_plan *pl, int *ctas, int *order, double *tuned_ms) {
+    if (!pl) return PSMS_EINVAL;
+    if (ctas) *ctas = pl->ctas;
+    if (order) *order = pl->order;
+    if (tuned_ms) *tuned_ms = pl->tuned_ms;
+    return PSMS_OK;
+}
+
+psms_status psms_block_plan_destroy(psms_block_plan *pl) {
+    if (!pl) return PSMS_EINVAL;
+    if (pl->stream) cudaStreamSynchronize(pl->stream);
+    psms::plan_destroy(pl);
+    return PSMS_OK;
+}
+
+}  // extern "C"

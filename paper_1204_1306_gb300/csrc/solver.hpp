@@ -19,6 +19,7 @@ struct BlockSolveReq {
     int maxit = 100000;
     int inner_prec = P64;
     const int *sys_active = nullptr;
+    const int *block_active = nullptr;  // per lexicographic block (nullable)
     int *iters = nullptr;
     double *resid = nullptr;
     double *xnorm2 = nullptr;

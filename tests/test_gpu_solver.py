@@ -89,3 +89,25 @@ def test_solver_reports_non_convergence():
     with pytest.raises(ps.PsmsError) as e:
         ps.psms_solve(ctx, 0, ps.OP_BLOCKS, native(ctx, b), x, 1e-13, 2, ps.PREC_F64)
     assert e.value.status == 4
+
+
+@pytest.mark.parametrize("variant", range(8))
+def test_block_solver_cluster_variants(variant):
+    """Every (cluster size, register cap) variant of the block solver gives the
+    oracle's solution (8^4 blocks: one block is shared by up to 8 CTAs of a
+    thread-block cluster)."""
+    dims, block, kappa = (8, 8, 8, 16), (8, 8, 8, 8), 0.156
+    geom = lattice.Geometry(dims, block)
+    ctx = ps.psms_create(dims, block, kappa, 1)
+    ps.psms_gauge_init(ctx, 0, 0.5, 15)
+    ps.psms_autotune(ctx, False, variant)
+    U = gauge.generate_links(dims, 0.5, 15)
+    b = seeded.spinor(dims, 16)
+    for inner in (ps.PREC_F32, ps.PREC_F64):
+        x = torch.zeros_like(native(ctx, b))
+        ps.psms_solve(ctx, 0, ps.OP_BLOCKS, native(ctx, b), x, 1e-13, 20000, inner)
+        got = canonical(ctx, x)
+        r = b - dirac.apply_D(U, got, kappa, geom, mode="block")
+        assert np.sqrt(linalg.norm2(r) / linalg.norm2(b)) <= 1e-13
+        ref = estimator.solve_blocks(U, b, geom, kappa, [1], 1e-14)
+        assert rel_err(dirac.extract_block(got, geom, 1), dirac.extract_block(ref, geom, 1)) < 1e-11

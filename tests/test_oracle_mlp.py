@@ -113,3 +113,20 @@ def test_bf16_rounding_model():
     z = np.random.default_rng(3).standard_normal((20, 64))
     a, b = mlp.antisym(p, z), mlp.antisym_rounded(p, z)
     assert np.linalg.norm(a - b) <= 0.25 * np.linalg.norm(a)
+
+
+def test_pair_features_distance():
+    """Slot 18 (both halves) is the block distance of Eq. (sprodgf): zero for
+    identical fields, (3 - ReTr R)/12 per link for U' = U R with R fixed, and
+    symmetric in (U, U')."""
+    geom = lattice.Geometry((8, 4, 4, 4), (4, 4, 4, 4))
+    U = gauge.generate_links(geom.dims, 0.5, 9)
+    z0 = mlp.pair_features(U, U, geom)
+    assert np.allclose(z0[:, 18], 0.0) and np.allclose(z0[:, 50], 0.0)
+    R = gauge.expm_i_hermitian(gauge.hermitian_generators(np.arange(8) * 0.1), 0.7)
+    Up = U @ R
+    z = mlp.pair_features(U, Up, geom)
+    assert np.allclose(z[:, 18], (3.0 - np.real(np.trace(R))) / 12.0)
+    zr = mlp.pair_features(Up, U, geom)
+    assert np.allclose(zr[:, 18], z[:, 18])
+    assert np.allclose(zr[:, :18], z[:, 32:50]) and np.allclose(zr[:, 32:50], z[:, :18])
