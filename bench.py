@@ -186,7 +186,7 @@ def compare_16(ps, torch, steps=6, warmup=2):
         blocks = sum(r["n_accept_blocks"] for r in recs if r["accept_global"])
         out[name] = {"s_per_step": wall / steps, "accepted_updates_per_s": acc / wall,
                      "accepted_blocks_per_s": blocks / wall, "global_acceptance": acc / steps,
-                     "learned_pass": (sum(r["n_accept_learned"] for r in recs) / (steps * r["n_blocks"])
+                     "learned_pass": (sum(r["n_accept_learned"] for r in recs) / (steps * recs[0]["n_blocks"])
                                       if learned else None), "train_s": train_s}
         if name == "plain_fp64":
             ref = recs

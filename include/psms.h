@@ -99,6 +99,28 @@ typedef struct {
     int n_systems;
 } psms_solve_info;
 
+/* Relative gauge fixing (Sec. 4.2 and App. B): steepest descent of the
+ * distance of Eq. (sprodgf) between U^{g_1} and U'^{g_2}, the
+ * transformations living on the block interiors (sites whose eight
+ * neighbours lie in the same block).  Per step and interior point:
+ * Delta = sum_mu [U'(x,mu) U(x,mu)^dag + U'(x-mu,mu)^dag U(x-mu,mu)] on the
+ * current pair, Y = Delta - Delta^dag - Tr(Delta - Delta^dag)/3,
+ * theta = sum |Y_ij|^2, and the pair takes U -> U^h, U' -> U'^{h^{-1}} with
+ * h = exp(alpha/4 Y) (relative rotation exp(alpha/2 Y), Eq. (ming)).  A block
+ * stops when the mean theta over its interior drops below theta_tol; after
+ * max_iter steps without that it restarts with alpha - dalpha, down to
+ * alpha_min, and keeps its last state after that.  Each block iterates on
+ * its pair in a canonical order, so exchanging U and U' exchanges the
+ * results exactly (the symmetry detailed balance needs). */
+typedef struct {
+    double alpha0;     /* first step size (App. B: 0.15)                     */
+    double alpha_min;  /* smallest step size (0.10)                          */
+    double dalpha;     /* step-size decrement (0.01)                         */
+    double theta_tol;  /* convergence threshold on the block mean of theta   */
+    int max_iter;      /* steps per step size, 0 .. 10^6                     */
+    int prec;          /* PSMS_PREC_F64 or PSMS_PREC_F32 iteration arithmetic */
+} psms_relgf_params;
+
 typedef struct {
     /* level 0: proposal (Sec. 6): n_iter x (HB + n_or OR + n_or OR + HB)    */
     double beta0;
@@ -116,6 +138,9 @@ typedef struct {
     uint64_t seed;
     uint64_t step;         /* filter step counter (RNG counter base)           */
     int learned;           /* 1: insert the learned level before level 1       */
+    int gauge_fix;         /* 1: interpolate between relatively gauge-fixed
+                              endpoints (Sec. 4.2) at levels 1 and 2          */
+    psms_relgf_params relgf;
 } psms_filter_params;
 
 typedef struct {
@@ -128,6 +153,7 @@ typedef struct {
     long long solver_iters;
     int hb_failed;
     int n_accept_learned;  /* blocks passing the learned level (-1: no level)  */
+    long long gf_steps;    /* gauge-fixing steps summed over blocks            */
 } psms_filter_result;
 
 typedef struct {
@@ -334,6 +360,20 @@ psms_status psms_profile_read_block(psms_ctx *ctx, long long *launches, double *
  * misses tol within maxit iterations. */
 psms_status psms_block_solve_noalloc(psms_ctx *ctx, int field, int op, const void *b_dev, void *x_dev, double tol,
                                      int maxit, long long *iters_out, double *resid_out);
+
+/* ---- relative gauge fixing --------------------------------------------------
+ * Gauge-fixes the pair (field_old, field_new) (Sec. 4.2, App. B; parameters
+ * and iteration above psms_filter_params) and writes the interpolation
+ * endpoints U^{g_1} to slot out_old and U'^{g_2} to slot out_new (FP64).
+ * out_old may equal field_old and out_new field_new; out_old != field_new,
+ * out_new != field_old, out_old != out_new (else PSMS_EINVAL).  Host arrays
+ * of n_blocks entries in lexicographic block order, each may be NULL: steps
+ * taken at the final step size, that step size, the final block mean theta,
+ * and whether the block iterated on (U', U).  g_dev (device, may be NULL):
+ * g_1 then g_2 in the canonical layout [2][V][3][3] complex<double>. */
+psms_status psms_relative_gauge_fix(psms_ctx *ctx, int field_old, int field_new, int out_old, int out_new,
+                                    const psms_relgf_params *prm, int *steps, double *alpha, double *theta,
+                                    int *swapped, void *g_dev);
 
 /* ---- checkpoint / resume ----------------------------------------------------
  * The chain state: the FP64 gauge field of slot `field` (canonical layout),

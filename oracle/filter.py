@@ -48,6 +48,7 @@ class FilterParams:
     tol: float = 1e-13
     global_level: bool = True
     learned: object = None   # MLP parameter dict (oracle.mlp) or None
+    gauge_fix: object = None  # relative gauge fixing (Sec. 4.2): dict of oracle.gaugefix parameters, or None
 
 
 def gaussian_acceptance(sigma2):
@@ -102,14 +103,29 @@ def per_block_action_change(U, Up, geom):
     return out
 
 
-def filter_step(U, geom, prm, seed, step, h_override=None):
+def _merge(U, V, acc_b, geom, active):
+    """U with the active links of accepted blocks taken from V."""
+    out = U.copy()
+    sel = acc_b[geom.block_index][..., None] & active
+    out[sel] = V[sel]
+    return out
+
+
+def filter_step(U, geom, prm, seed, step, h_override=None, gf_override=None):
     """Returns (new field, record dict).
 
     With prm.learned (per-block decisions only) a learned level precedes
     level 1: h_b from the surrogate (or h_override, the values a device
     computed, so that both sides decide on the same numbers), accepted with
     min{1, exp(-h_b)} (counter (step, 3, b)); level 1 runs on the blocks that
-    passed, with Delta_b - h_b."""
+    passed, with Delta_b - h_b.
+
+    With prm.gauge_fix the interpolations of levels 1 and 2 (Eq. (gfparam))
+    run between U^{g_1} and U'^{g_2} (Sec. 4.2): level 1 between the fixed
+    pair of (U, U'), level 2 between U and the field after level 1, whose
+    fixed pair equals the level-1 one on accepted blocks and (U, U) on the
+    others (the blocks decouple).  gf_override = (g_1, g_2) replaces the
+    oracle's own transformations with a device's."""
     active = geom.active_links()
     Unew, _, failed = domain_sweep(U, geom, prm.beta0, prm.n_iter, prm.n_or, seed, step * SWEEP_STRIDE)
     per_block = min(geom.block) >= 3
@@ -124,10 +140,20 @@ def filter_step(U, geom, prm, seed, step, h_override=None):
         passed = np.array([accept(h[b], philox.accept_uniform(seed, step, 3, b)) for b in range(geom.n_blocks)])
         rec_h = h
 
+    E0, EN = U, Unew
+    rec_gf = None
+    if prm.gauge_fix is not None or gf_override is not None:
+        from .gaugefix import relative_gauge_fix, transform
+        if gf_override is None:
+            g1, g2, rec_gf = relative_gauge_fix(U, Unew, geom, **prm.gauge_fix)
+        else:
+            g1, g2 = gf_override
+        E0, EN = transform(U, g1), transform(Unew, g2)
+
     blocks = [b for b in range(geom.n_blocks) if passed[b]]
     d_blk = np.zeros(geom.n_blocks)
     if blocks:
-        d_all = block_level(U, Unew, geom, prm.kappa, prm.n_block, seed, step, tol=prm.tol, blocks=blocks)
+        d_all = block_level(E0, EN, geom, prm.kappa, prm.n_block, seed, step, tol=prm.tol, blocks=blocks)
         d_blk[blocks] = d_all[blocks].sum(axis=1)
     if prm.beta_block != 0.0:
         d_blk = d_blk + prm.beta_block * per_block_action_change(U, Unew, geom)
@@ -139,15 +165,16 @@ def filter_step(U, geom, prm, seed, step, h_override=None):
         a = accept(d_blk.sum(), philox.accept_uniform(seed, step, 1, 0))
         acc_b = np.full(geom.n_blocks, a)
 
-    Umid = U.copy()
-    link_block_acc = acc_b[geom.block_index][..., None] & active
-    Umid[link_block_acc] = Unew[link_block_acc]
+    Umid = _merge(U, Unew, acc_b, geom, active)
 
     rec = {"delta_block": d_blk, "accept_block": acc_b, "hb_failed": failed, "h": rec_h,
-           "passed_learned": passed}
+           "passed_learned": passed, "gauge_fix": rec_gf}
     Ufin = Umid
     if prm.global_level:
-        dg = global_level(U, Umid, geom, prm.kappa, prm.n_global, seed, step, tol=prm.tol)
+        G0, GN = U, Umid
+        if E0 is not U:
+            G0, GN = _merge(U, E0, acc_b, geom, active), _merge(U, EN, acc_b, geom, active)
+        dg = global_level(G0, GN, geom, prm.kappa, prm.n_global, seed, step, tol=prm.tol)
         d = float(dg.sum())
         if prm.beta_global != 0.0:
             d += prm.beta_global * (wilson_action(Umid) - wilson_action(U))

@@ -22,6 +22,7 @@ __all__ = [
     "psms_mlp_train", "psms_block_plan_create", "psms_block_plan_run", "psms_block_plan_schedule",
     "psms_block_plan_destroy", "BlockPlan", "psms_autotune", "psms_profile_read_block",
     "psms_domain_features_pair", "psms_checkpoint_save", "psms_checkpoint_load",
+    "psms_relative_gauge_fix",
     "PREC_F64", "PREC_F32", "PREC_BF16", "OP_FULL", "OP_BLOCKS", "ACTIVE_BLOCKS", "ACTIVE_ALL",
     "LEVEL_BLOCK", "LEVEL_GLOBAL", "EST_INTERP", "EST_INDEPENDENT",
 ]
@@ -54,19 +55,29 @@ class SolveInfo(ctypes.Structure):
                 ("true_residual", ctypes.c_double), ("n_systems", ctypes.c_int)]
 
 
+class RelGFParams(ctypes.Structure):
+    _fields_ = [("alpha0", ctypes.c_double), ("alpha_min", ctypes.c_double), ("dalpha", ctypes.c_double),
+                ("theta_tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("prec", ctypes.c_int)]
+
+
+def _relgf(alpha0=0.15, alpha_min=0.10, dalpha=0.01, theta_tol=1e-3, max_iter=1000, prec=None):
+    return RelGFParams(float(alpha0), float(alpha_min), float(dalpha), float(theta_tol), int(max_iter),
+                       int(PREC_F32 if prec is None else prec))
+
+
 class FilterParams(ctypes.Structure):
     _fields_ = [("beta0", ctypes.c_double), ("n_iter", ctypes.c_int), ("n_or", ctypes.c_int),
                 ("n_block", ctypes.c_int), ("beta_block", ctypes.c_double), ("n_global", ctypes.c_int),
                 ("beta_global", ctypes.c_double), ("global_level", ctypes.c_int), ("tol", ctypes.c_double),
                 ("inner_prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("step", ctypes.c_uint64),
-                ("learned", ctypes.c_int)]
+                ("learned", ctypes.c_int), ("gauge_fix", ctypes.c_int), ("relgf", RelGFParams)]
 
 
 class FilterResult(ctypes.Structure):
     _fields_ = [("n_blocks", ctypes.c_int), ("n_accept_blocks", ctypes.c_int), ("accept_global", ctypes.c_int),
                 ("shift", ctypes.c_int * 4), ("delta_global", ctypes.c_double),
                 ("delta_block_sum", ctypes.c_double), ("solver_iters", ctypes.c_longlong),
-                ("hb_failed", ctypes.c_int), ("n_accept_learned", ctypes.c_int)]
+                ("hb_failed", ctypes.c_int), ("n_accept_learned", ctypes.c_int), ("gf_steps", ctypes.c_longlong)]
 
 
 class BlockProblem(ctypes.Structure):
@@ -119,6 +130,7 @@ _SIGS = {
     "psms_mlp_train": [_P, _P, _P, _I, ctypes.POINTER(TrainParams), ctypes.POINTER(_D)],
     "psms_autotune": [_P, _I, _I],
     "psms_checkpoint_save": [_P, _I, ctypes.c_char_p, _U64, _U64],
+    "psms_relative_gauge_fix": [_P, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P],
     "psms_checkpoint_load": [_P, _I, ctypes.c_char_p, ctypes.POINTER(_U64), ctypes.POINTER(_U64)],
     "psms_profile_read_block": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), ctypes.POINTER(_D)],
     "psms_profile_enable": [_P, _I],
@@ -286,10 +298,12 @@ def psms_logdet_ratio(ctx, level, field_old, field_new, n, mode, seed, counter, 
 
 def psms_filter_step(ctx, field, *, beta0, n_iter=1, n_or=0, n_block=4, n_global=4, beta_block=0.0,
                      beta_global=0.0, global_level=True, tol=1e-10, inner_prec=PREC_F64, seed=0, step=0,
-                     learned=False):
+                     learned=False, gauge_fix=None):
+    """gauge_fix: None (off) or a dict of relative gauge-fixing parameters
+    (alpha0, alpha_min, dalpha, theta_tol, max_iter, prec; {} = defaults)."""
     p = FilterParams(float(beta0), int(n_iter), int(n_or), int(n_block), float(beta_block), int(n_global),
                      float(beta_global), int(bool(global_level)), float(tol), int(inner_prec), int(seed), int(step),
-                     int(bool(learned)))
+                     int(bool(learned)), int(gauge_fix is not None), _relgf(**(gauge_fix or {})))
     r = FilterResult()
     nb = int(np.prod([d // b for d, b in zip(ctx.dims, ctx.block)]))
     db = (_D * nb)()
@@ -298,6 +312,7 @@ def psms_filter_step(ctx, field, *, beta0, n_iter=1, n_or=0, n_block=4, n_global
     return {"n_blocks": r.n_blocks, "n_accept_blocks": r.n_accept_blocks, "accept_global": bool(r.accept_global),
             "shift": tuple(r.shift), "delta_global": r.delta_global, "delta_block_sum": r.delta_block_sum,
             "solver_iters": r.solver_iters, "hb_failed": r.hb_failed, "n_accept_learned": r.n_accept_learned,
+            "gf_steps": r.gf_steps,
             "delta_block": np.frombuffer(db, dtype=np.float64).copy(),
             "accept_block": np.frombuffer(ab, dtype=np.int32).astype(bool)}
 
@@ -421,6 +436,19 @@ def psms_profile_read_block(ctx):
     n, ms, by = ctypes.c_longlong(), _D(), _D()
     ctx.check(ctx.lib.psms_profile_read_block(ctx.handle, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
     return n.value, ms.value, by.value
+
+
+def psms_relative_gauge_fix(ctx, field_old, field_new, out_old, out_new, g_dev=None, **kw):
+    """Relative gauge fixing of (field_old, field_new) into (out_old, out_new);
+    returns per-block steps, alpha, theta, swapped (lexicographic order)."""
+    nb = int(np.prod([d // b for d, b in zip(ctx.dims, ctx.block)]))
+    st, al, th, sw = (_I * nb)(), (_D * nb)(), (_D * nb)(), (_I * nb)()
+    p = _relgf(**kw)
+    ctx.check(ctx.lib.psms_relative_gauge_fix(ctx.handle, field_old, field_new, out_old, out_new, ctypes.byref(p),
+                                              st, al, th, sw, None if g_dev is None else _ptr(g_dev)))
+    return {"steps": np.frombuffer(st, dtype=np.int32).copy(), "alpha": np.frombuffer(al, dtype=np.float64).copy(),
+            "theta": np.frombuffer(th, dtype=np.float64).copy(),
+            "swapped": np.frombuffer(sw, dtype=np.int32).astype(bool)}
 
 
 def psms_checkpoint_save(ctx, field, path, step, seed):

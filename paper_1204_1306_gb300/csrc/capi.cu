@@ -10,6 +10,7 @@
 
 #include "estimator.hpp"
 #include "gauge.hpp"
+#include "gaugefix.hpp"
 #include "mlp.hpp"
 #include "solver.hpp"
 
@@ -573,6 +574,53 @@ psms_status psms_logdet_ratio(psms_ctx *ctx, int level, int field_old, int field
     PSMS_CATCH(ctx)
 }
 
+static GaugeFixParams gf_params(const psms_relgf_params &p) {
+    if (!(p.alpha0 > 0) || !(p.alpha_min > 0) || p.alpha_min > p.alpha0 || !(p.dalpha > 0) || !(p.theta_tol >= 0) ||
+        p.max_iter < 0 || p.max_iter > 1000000 || (p.prec != P64 && p.prec != P32))
+        fail(PSMS_EINVAL, "gauge fixing: need alpha0 >= alpha_min > 0, dalpha > 0, theta_tol >= 0, "
+                          "0 <= max_iter <= 1e6, prec FP64 or FP32");
+    GaugeFixParams q;
+    q.alpha0 = p.alpha0;
+    q.alpha_min = p.alpha_min;
+    q.dalpha = p.dalpha;
+    q.theta_tol = p.theta_tol;
+    q.max_iter = p.max_iter;
+    q.prec = p.prec;
+    return q;
+}
+
+psms_status psms_relative_gauge_fix(psms_ctx *ctx, int field_old, int field_new, int out_old, int out_new,
+                                    const psms_relgf_params *prm, int *steps, double *alpha, double *theta,
+                                    int *swapped, void *g_dev) {
+    PSMS_TRY(ctx)
+    check_field(ctx, field_old);
+    check_field(ctx, field_new);
+    check_field(ctx, out_old);
+    check_field(ctx, out_new);
+    if (!prm) fail(PSMS_EINVAL, "null parameters");
+    if (out_old == field_new || out_new == field_old || out_old == out_new)
+        fail(PSMS_EINVAL, "output slots overlap the other input");
+    const GaugeFixParams q = gf_params(*prm);
+    GaugeFixInfo gi;
+    gauge_fix_pair(ctx, ctx->U64[field_old], ctx->U64[field_new], ctx->U64[out_old], ctx->U64[out_new], q, &gi);
+    touch_field(ctx, out_old);
+    touch_field(ctx, out_new);
+    if (g_dev) {
+        gauge_fix_export(ctx, gi.G1, (double2 *)g_dev);
+        gauge_fix_export(ctx, gi.G2, (double2 *)g_dev + 9 * ctx->g.V);
+    }
+    const int nb = ctx->g.nblocks;
+    if (steps) cuda_check(cudaMemcpyAsync(steps, gi.d_steps, sizeof(int) * nb, cudaMemcpyDeviceToHost, ctx->stream), "gf");
+    if (alpha)
+        cuda_check(cudaMemcpyAsync(alpha, gi.d_alpha, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream), "gf");
+    if (theta)
+        cuda_check(cudaMemcpyAsync(theta, gi.d_theta, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream), "gf");
+    if (swapped)
+        cuda_check(cudaMemcpyAsync(swapped, gi.d_swap, sizeof(int) * nb, cudaMemcpyDeviceToHost, ctx->stream), "gf");
+    cuda_check(cudaStreamSynchronize(ctx->stream), "gf");
+    PSMS_CATCH(ctx)
+}
+
 psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params *prm, psms_filter_result *res,
                              double *delta_block_out, int *accept_block_out) {
     PSMS_TRY(ctx)
@@ -620,11 +668,27 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         for (int v : h3) n_learned += v;
         d_mask = d_acc3;
     }
+    // relative gauge fixing: the estimators interpolate between U^{g_1} and
+    // U'^{g_2} (Sec. 4.2); blocks decouple, so the level-2 endpoints are the
+    // level-1 ones on accepted blocks and U elsewhere
+    double2 *e0 = old, *eN = prop;
+    long long gf_steps = 0;
+    if (prm->gauge_fix) {
+        const GaugeFixParams q = gf_params(prm->relgf);
+        e0 = (double2 *)scratch(ctx, "fs_e0", fb);
+        eN = (double2 *)scratch(ctx, "fs_en", fb);
+        GaugeFixInfo gi;
+        gauge_fix_pair(ctx, old, prop, e0, eN, q, &gi);
+        std::vector<int> hs(nb);
+        cuda_check(cudaMemcpyAsync(hs.data(), gi.d_steps, sizeof(int) * nb, cudaMemcpyDeviceToHost, ctx->stream), "gf");
+        cuda_check(cudaStreamSynchronize(ctx->stream), "gf");
+        for (int v : hs) gf_steps += v;
+    }
     // level 1: block det ratios (blocks that passed the learned level)
     double *d_db = (double *)scratch(ctx, "fs_dblk", sizeof(double) * nb * N1);
     long long iters = 0;
     if (n_learned != 0)
-        iters = block_level(ctx, old, prop, N1, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol, prm->inner_prec,
+        iters = block_level(ctx, e0, eN, N1, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol, prm->inner_prec,
                             d_db, d_mask);
     else
         cuda_check(cudaMemsetAsync(d_db, 0, sizeof(double) * nb * N1, ctx->stream), "dblk");
@@ -652,8 +716,12 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
     if (prm->global_level && nacc > 0) {
         const int N2 = prm->n_global;
         double *d_dg = (double *)scratch(ctx, "fs_dg", sizeof(double) * N2);
-        iters += global_level(ctx, old, mid, N2, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol, prm->inner_prec,
-                              d_dg);
+        if (prm->gauge_fix) {
+            merge_blocks(ctx, old, e0, e0, d_acc);
+            merge_blocks(ctx, old, eN, eN, d_acc);
+        }
+        iters += global_level(ctx, e0, prm->gauge_fix ? eN : mid, N2, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol,
+                              prm->inner_prec, d_dg);
         std::vector<double> hg(N2);
         cuda_check(cudaMemcpyAsync(hg.data(), d_dg, sizeof(double) * N2, cudaMemcpyDeviceToHost, ctx->stream), "dg");
         cuda_check(cudaStreamSynchronize(ctx->stream), "dg");
@@ -694,6 +762,7 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         res->solver_iters = iters;
         res->hb_failed = failed;
         res->n_accept_learned = n_learned;
+        res->gf_steps = gf_steps;
     }
     if (delta_block_out)
         for (int b = 0; b < nb; ++b) delta_block_out[b] = hd[b];

@@ -1,0 +1,131 @@
+"""Pins of the oracle's relative gauge fixing (Sec. 4.2, App. B) against what
+the mathematics fixes: recovery of a pure gauge transformation, the brute
+force maximum of the single-site problem, monotone descent of Eq. (sprodgf),
+exact swap symmetry, gauge covariance of the endpoints, and the trivial
+cases."""
+import numpy as np
+import pytest
+from scipy import optimize
+
+from oracle import dirac, gauge, gaugefix, lattice
+from tests import seeded
+
+
+def _interior_transform(geom, eps, seed):
+    """Random SU(3) on the block interiors, identity elsewhere."""
+    g = np.random.default_rng(seed)
+    om = g.standard_normal(geom.dims + (8,))
+    k = gauge.expm_i_hermitian(gauge.hermitian_generators(om), eps)
+    inside = gaugefix.interior_mask(geom)
+    return np.where(inside[..., None, None], k, np.eye(3))
+
+
+def _perturb_interior_links(U, geom, eps, seed):
+    """U' = U exp(i eps H) on every link that touches an interior point."""
+    g = np.random.default_rng(seed)
+    om = g.standard_normal(U.shape[:5] + (8,))
+    R = gauge.expm_i_hermitian(gauge.hermitian_generators(om), eps)
+    inside = gaugefix.interior_mask(geom)
+    touch = np.stack([inside | lattice.gauge_shift(inside, mu, +1) for mu in range(4)], axis=-1)
+    return np.where(touch[..., None, None], U @ R, U)
+
+
+def test_interior_mask_counts():
+    geom = lattice.Geometry((8, 8, 8, 8), (4, 4, 4, 4))
+    assert gaugefix.interior_mask(geom).sum() == geom.n_blocks * 2 ** 4
+    geom = lattice.Geometry((4, 4, 4, 4), (2, 2, 2, 2))
+    assert gaugefix.interior_mask(geom).sum() == 0
+
+
+def test_recovers_a_pure_gauge_transformation():
+    """U' = U^k with k on the block interiors: the fixed pair coincides
+    (Eq. (sprodgf) -> 0), which a wrong sign, a dropped backward term or a
+    wrong neighbour in Delta all prevent."""
+    geom = lattice.Geometry((4, 4, 8, 8), (4, 4, 4, 4))
+    U = seeded.gauge_field(geom.dims, 21)
+    Up = gaugefix.transform(U, _interior_transform(geom, 0.6, 5))
+    assert gaugefix.sprod(U, Up) > 1e-2
+    A, B, info = gaugefix.fixed_pair(U, Up, geom, theta_tol=1e-20, max_iter=3000, alpha0=0.1, alpha_min=0.1)
+    assert gaugefix.sprod(A, B) < 1e-12
+    assert np.all(info["theta"] < 1e-20)
+
+
+def test_single_site_reaches_the_brute_force_maximum():
+    """Blocks 3^4 have one interior point x: the functional depends on g only
+    through X in SU(3) as Re Tr(X Delta_0), and the fixed pair must reach the
+    maximum found by direct optimisation over the eight group parameters."""
+    geom = lattice.Geometry((6, 6, 6, 6), (3, 3, 3, 3))
+    U = seeded.gauge_field(geom.dims, 22)
+    Up = _perturb_interior_links(U, geom, 0.5, 23)
+    A, B, _ = gaugefix.fixed_pair(U, Up, geom, theta_tol=1e-24, max_iter=5000, alpha0=0.1, alpha_min=0.1)
+    inside = gaugefix.interior_mask(geom)
+    D0 = gaugefix.delta(U, Up)[inside]
+    D1 = gaugefix.delta(A, B)[inside]
+    lam = gauge.GELL_MANN
+    for blk in range(3):
+        def neg(c, D=D0[blk]):
+            X = gauge.expm_i_hermitian(np.einsum("a,aij->ij", c, lam) / 2, 1.0)
+            return -np.real(np.trace(X @ D))
+        best = max(-optimize.minimize(neg, x0, method="BFGS", options={"gtol": 1e-10}).fun
+                   for x0 in np.random.default_rng(blk).standard_normal((6, 8)))
+        got = np.real(np.trace(D1[blk]))
+        assert abs(got - best) < 1e-7 * abs(best), (got, best)
+
+
+def test_functional_decreases_step_by_step():
+    geom = lattice.Geometry((4, 4, 8, 8), (4, 4, 4, 4))
+    U = seeded.gauge_field(geom.dims, 24)
+    Up = _perturb_interior_links(U, geom, 0.8, 25)
+    vals = []
+    for k in range(6):
+        A, B, info = gaugefix.fixed_pair(U, Up, geom, theta_tol=0.0, max_iter=k, alpha0=0.1, alpha_min=0.1)
+        vals.append(gaugefix.sprod(A, B))
+        assert np.all(info["steps"] == k)
+    assert all(b < a for a, b in zip(vals, vals[1:])), vals
+
+
+def test_swap_symmetry_is_exact():
+    """The reverse move (U', U) gets exactly the swapped transformations."""
+    geom = lattice.Geometry((4, 4, 8, 8), (4, 4, 4, 4))
+    U = seeded.gauge_field(geom.dims, 26)
+    Up = _perturb_interior_links(U, geom, 0.7, 27)
+    g1, g2, i1 = gaugefix.relative_gauge_fix(U, Up, geom)
+    h1, h2, i2 = gaugefix.relative_gauge_fix(Up, U, geom)
+    assert np.array_equal(g1, h2) and np.array_equal(g2, h1)
+    assert np.array_equal(i1["swapped"], ~i2["swapped"])
+    assert np.all(i1["theta"] < 1e-3)
+
+
+def test_endpoints_are_gauge_transforms():
+    """g_1, g_2 are SU(3), unity off the interiors, and D(U^g) = g D(U) g^{-1}."""
+    geom = lattice.Geometry((4, 4, 4, 8), (4, 4, 4, 4))
+    U = seeded.gauge_field(geom.dims, 28)
+    Up = _perturb_interior_links(U, geom, 3.0, 29)
+    g1, g2, _ = gaugefix.relative_gauge_fix(U, Up, geom)
+    inside = gaugefix.interior_mask(geom)
+    for g in (g1, g2):
+        assert np.abs(g @ gauge.dag(g) - np.eye(3)).max() < 1e-14
+        assert np.abs(np.linalg.det(g) - 1).max() < 1e-14
+        assert np.array_equal(g[~inside], np.broadcast_to(np.eye(3), g[~inside].shape))
+    psi = seeded.spinor(geom.dims, 30)
+    kappa = 0.156
+    gpsi = np.einsum("...ij,...sj->...si", g1, psi)
+    lhs = dirac.apply_D(gaugefix.transform(U, g1), gpsi, kappa, geom, mode="block")
+    rhs = np.einsum("...ij,...sj->...si", g1, dirac.apply_D(U, psi, kappa, geom, mode="block"))
+    assert np.abs(lhs - rhs).max() < 1e-13
+    # the fixed pair is clearly closer than the unfixed one
+    assert gaugefix.sprod(gaugefix.transform(U, g1), gaugefix.transform(Up, g2)) < 0.8 * gaugefix.sprod(U, Up)
+
+
+def test_unchanged_blocks_stay_unfixed():
+    geom = lattice.Geometry((4, 4, 8, 8), (4, 4, 4, 4))
+    U = seeded.gauge_field(geom.dims, 31)
+    g1, g2, info = gaugefix.relative_gauge_fix(U, U.copy(), geom)
+    assert np.all(info["steps"] == 0)
+    assert np.array_equal(g1, np.broadcast_to(np.eye(3), g1.shape))
+    Up = _perturb_interior_links(U, geom, 0.7, 32)
+    keep = geom.block_index == 3
+    Up[keep] = U[keep]
+    g1, g2, info = gaugefix.relative_gauge_fix(U, Up, geom)
+    assert info["steps"][3] == 0 and np.all(np.delete(info["steps"], 3) > 0)
+    assert np.array_equal(g1[keep], np.broadcast_to(np.eye(3), g1[keep].shape))
