@@ -1,12 +1,17 @@
 """Benchmark of the PSMS hot path on GB300.
 
-A step is one 3-level hierarchical filter update (domain sweep -> per-block
-stochastic det ratios -> global Schur det ratio -> random translation) on the
-synthetic 32^3 x 64 workload: kappa 0.157, beta 5.3, 8^4 domains, 24
-interpolation steps (noise vectors) at the global level, FP32 inner Krylov
-iterations inside FP64 defect correction, tolerance 1e-10.  The gauge field
-U = exp(i eps H) (eps 0.5) is thermalised by pure-gauge sweeps at beta 5.3
-before timing.  Inputs (1.2 GB of links) are larger than the 129 MB L2.
+A step is one 3-level hierarchical filter update of the synthetic 16^4
+workload (kappa 0.156, beta 5.3, 4^4 domains): domain sweep -> relative gauge
+fixing of the proposal -> learned level -> per-block stochastic det ratios
+(48 interpolation steps, all blocks and steps batched) -> global Schur det
+ratio (12 steps) -> random translation, FP32 inner Krylov iterations inside
+FP64 defect correction to a true residual of 1e-13 (estimates within 1e-8 of
+the FP64 ones).  The gauge field U = exp(i eps H) (eps 0.5) is thermalised
+by pure-gauge sweeps at beta 5.3 before timing; the learned level is trained
+on the GPU before timing.  The same line carries the plain FP64 and the
+mixed-precision arms on identical proposals and noise, and the 32^3 x 64
+measurements (D_w GB/s per precision, the domain heatbath, filter steps with
+8^4 domains).
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 instead (bounded sample, extrapolated, see `reference_arm`).
@@ -33,11 +38,11 @@ SEED = 0x50534D53
 WORKLOADS = {
     # name: dims (L0..L3), block, kappa, eps, beta, n_block, n_global, therm iterations
     "32^3x64": dict(dims=(64, 32, 32, 32), block=(8, 8, 8, 8), kappa=0.157, eps=0.5, beta=5.3, n_block=4,
-                    n_global=24, therm=4, n_iter=1, n_or=2, tol=1e-10),
-    "16^4": dict(dims=(16, 16, 16, 16), block=(4, 4, 4, 4), kappa=0.156, eps=0.5, beta=5.3, n_block=12,
-                 n_global=12, therm=4, n_iter=1, n_or=1, tol=1e-10),
+                    n_global=24, therm=4, n_iter=1, n_or=2, tol=1e-10, train_props=8),
+    "16^4": dict(dims=(16, 16, 16, 16), block=(4, 4, 4, 4), kappa=0.156, eps=0.5, beta=5.3, n_block=48,
+                 n_global=12, therm=4, n_iter=1, n_or=1, tol=1e-13, train_props=48),
     "4^4": dict(dims=(4, 4, 4, 4), block=(2, 2, 2, 2), kappa=0.15, eps=0.3, beta=5.3, n_block=4, n_global=4,
-                therm=0, n_iter=1, n_or=0, tol=1e-10),
+                therm=0, n_iter=1, n_or=0, tol=1e-10, train_props=8),
 }
 DW_FLOP_PER_SITE = 1320.0
 DW_BYTES_PER_SITE = {"bf16": 384.0, "f32": 480.0, "f64": 960.0}
@@ -151,67 +156,23 @@ def roofline_entry(kernel, n, ms, nbytes, peak, peak_kind):
             "avg_launch_ms": round(ms / max(n, 1), 4), "total_ms": round(ms, 2)}
 
 
-def compare_16(ps, torch, steps=6, warmup=2):
-    """Config 2 scale (16^4, 4^4 domains, kappa 0.156, eps 0.5): the plain FP64
-    hierarchy against FP32-inner mixed precision and against mixed precision
-    with the learned level, on identical proposals and noise (N = 48 at the
-    block level, 12 at the global level, solves to 1e-12).  Reports accepted
-    updates/s (global accept with at least one block changed), accepted
-    blocks/s, and the largest estimate difference to the FP64 hierarchy."""
-    dims, block, kappa = (16, 16, 16, 16), (4, 4, 4, 4), 0.156
-    prm = dict(beta0=5.3, n_iter=1, n_or=1, n_block=48, n_global=12, tol=1e-12, seed=SEED + 1)
-    out = {}
-    ref = None
-    for name, inner, learned in (("plain_fp64", ps.PREC_F64, False), ("mixed", ps.PREC_F32, False),
-                                 ("learned_mixed", ps.PREC_F32, True)):
-        ctx = ps.psms_create(dims, block, kappa, 2)
-        ps.psms_set_stream(ctx, torch.cuda.current_stream())
-        ps.psms_gauge_init(ctx, 0, 0.5, SEED + 1)
-        ps.psms_gauge_sweep(ctx, 0, ps.ACTIVE_ALL, 4, 2, 5.3, SEED, 1 << 40)
-        train_s = 0.0
-        if learned:
-            t0 = time.perf_counter()
-            train_learned(ps, torch, ctx, 24)
-            train_s = time.perf_counter() - t0
-        recs = []
-        for i in range(warmup):
-            ps.psms_filter_step(ctx, 0, inner_prec=inner, learned=learned, step=10_000 + i, **prm)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(steps):
-            recs.append(ps.psms_filter_step(ctx, 0, inner_prec=inner, learned=learned, step=i, **prm))
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        acc = sum(1 for r in recs if r["accept_global"] and r["n_accept_blocks"] > 0)
-        blocks = sum(r["n_accept_blocks"] for r in recs if r["accept_global"])
-        out[name] = {"s_per_step": wall / steps, "accepted_updates_per_s": acc / wall,
-                     "accepted_blocks_per_s": blocks / wall, "global_acceptance": acc / steps,
-                     "learned_pass": (sum(r["n_accept_learned"] for r in recs) / (steps * recs[0]["n_blocks"])
-                                      if learned else None), "train_s": train_s}
-        if name == "plain_fp64":
-            ref = recs
-        elif not learned:
-            # same proposals, same noise: differences are solver precision
-            db = max(float(np.abs(a["delta_block"] - b["delta_block"]).max()) for a, b in zip(recs, ref))
-            dg = max(abs(a["delta_global"] - b["delta_global"]) for a, b in zip(recs, ref))
-            out[name]["max_estimate_error_vs_fp64"] = max(db, dg)
-        ctx.close()
-    out["speedup_learned_mixed_vs_fp64"] = (out["plain_fp64"]["s_per_step"] /
-                                           max(out["learned_mixed"]["s_per_step"], 1e-12))
-    out["speedup_mixed_vs_fp64"] = out["plain_fp64"]["s_per_step"] / max(out["mixed"]["s_per_step"], 1e-12)
-    return out
-
-
-def train_learned(ps, torch, ctx, n_props, n_interp=48):
+def train_learned(ps, torch, ctx, n_props, n_interp=48, gauge_fix=True):
     """Train the learned level on block log-det-ratio estimates the method
-    generates for domain-sweep proposals of the current field."""
+    generates for domain-sweep proposals of the current field (between the
+    relatively gauge-fixed endpoints when the filter uses them; slots 2, 3
+    hold those).  The labels are noise-dominated, so the learning rate is
+    small and the epochs few (larger ones fit the label noise)."""
     nb = ps.psms_geometry_info(ctx)[0]
     zs, ys = [], []
     zb = torch.zeros(nb * 64, dtype=torch.float32, device="cuda")
     for s in range(n_props):
         ps.psms_gauge_copy(ctx, 1, 0)
         ps.psms_gauge_sweep(ctx, 1, ps.ACTIVE_BLOCKS, 1, 1, 5.3, SEED, (s + 7) << 20)
-        d = ps.psms_logdet_ratio(ctx, ps.LEVEL_BLOCK, 0, 1, n_interp, ps.EST_INTERP, SEED, 50_000 + s, 1e-10,
+        f0, f1 = 0, 1
+        if gauge_fix:
+            ps.psms_relative_gauge_fix(ctx, 0, 1, 2, 3, prec=ps.PREC_F32)
+            f0, f1 = 2, 3
+        d = ps.psms_logdet_ratio(ctx, ps.LEVEL_BLOCK, f0, f1, n_interp, ps.EST_INTERP, SEED, 50_000 + s, 1e-10,
                                  ps.PREC_F32)
         ps.psms_domain_features_pair(ctx, 0, 1, zb)
         zs.append(zb.view(nb, 64).clone())
@@ -219,7 +180,7 @@ def train_learned(ps, torch, ctx, n_props, n_interp=48):
     z = torch.cat(zs).contiguous()
     y = torch.cat(ys).to("cuda").contiguous()
     ps.psms_mlp_init(ctx, 7)
-    return ps.psms_mlp_train(ctx, z, y, len(y), epochs=60, batch=256, lr=1e-3, weight_decay=1e-4, seed=3)
+    return ps.psms_mlp_train(ctx, z, y, len(y), epochs=10, batch=256, lr=1e-4, weight_decay=1e-4, seed=3)
 
 
 def measure_heatbath(ps, ctx, torch, wl, reps=3):
@@ -348,7 +309,7 @@ def solve_only(args):
 
 
 def batch_only(args):
-    """Config 3: all 4^4 Dirichlet blocks x 16 noise vectors of three uneven
+    """All 4^4 Dirichlet blocks x 16 noise vectors of three uneven
     lattices (8^4, 12^4, 16^3 x 32; kappa 0.155, eps 0.5) in one persistent
     graph-captured launch, FP32 inner / FP64 refinement to 1e-10, autotuned
     schedule.  Reports the batch time, the mean time a CTA spends per system,
@@ -389,11 +350,77 @@ def batch_only(args):
     iters = infos[0]["inner_iters"]
     gbs = iters * 128 * 4416.0 / (ms * 1e-3) / 1e9
     peak, kind = peaks()
-    print(json.dumps({"workload": "config3: 8^4 + 12^4 + 16^3x32, 4^4 blocks x 16 noises", "systems": items,
+    print(json.dumps({"workload": "8^4 + 12^4 + 16^3x32, 4^4 blocks x 16 noises", "systems": items,
                       "batch_ms": round(ms, 3), "cta_ms_per_system": round(ms * sched["ctas"] / items, 4),
                       "block_cg_iterations": iters, "algorithmic_GB/s": round(gbs, 1), "frac": round(gbs / peak, 4),
                       "peak_gbs": peak, "peak_kind": kind, "schedule": sched,
                       "true_residual": max(i["true_residual"] for i in infos)}), flush=True)
+
+
+ARMS = (
+    # name, inner Krylov precision, learned level
+    ("learned_mixed", "f32", True),
+    ("mixed", "f32", False),
+    ("plain_fp64", "f64", False),
+)
+
+
+def _filter_prm(ps, wl, seed):
+    return dict(beta0=wl["beta"], n_iter=wl["n_iter"], n_or=wl["n_or"], n_block=wl["n_block"],
+                n_global=wl["n_global"], tol=wl["tol"], seed=seed, gauge_fix={"prec": ps.PREC_F32})
+
+
+def _new_chain(ps, torch, wl, seed):
+    ctx = ps.psms_create(wl["dims"], wl["block"], wl["kappa"], 4)
+    ps.psms_set_stream(ctx, torch.cuda.current_stream())
+    ps.psms_gauge_init(ctx, 0, wl["eps"], seed)
+    if wl["therm"]:
+        ps.psms_gauge_sweep(ctx, 0, ps.ACTIVE_ALL, wl["therm"], 2, wl["beta"], seed, 1 << 40)
+    return ctx
+
+
+def _timed_steps(ps, torch, ctx, prm, inner, learned, steps, flush, step0=0):
+    """`steps` filter steps, each timed with CUDA events on the library's
+    stream; L2 is flushed (a 256 MB write) between steps, outside the events."""
+    stream = torch.cuda.current_stream()
+    recs, ms = [], 0.0
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        recs.append(ps.psms_filter_step(ctx, 0, step=step0 + i, inner_prec=inner, learned=learned, **prm))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    return recs, ms
+
+
+def _accepted(recs):
+    """Accepted updates: steps whose global level accepted a changed field."""
+    return sum(1 for r in recs if r["accept_global"] and r["n_accept_blocks"] > 0)
+
+
+def large_workload(ps, torch, steps=2):
+    """32^3 x 64, 8^4 domains, kappa 0.157, 24 interpolation steps at the
+    global level: stand-alone D_w per precision, the domain heatbath, and
+    filter steps (FP32 inner, relative gauge fixing)."""
+    wl = WORKLOADS["32^3x64"]
+    ctx = _new_chain(ps, torch, wl, SEED + 4)
+    dw = measure_dw(ps, ctx, torch)
+    hb = measure_heatbath(ps, ctx, torch, wl)
+    prm = _filter_prm(ps, wl, SEED + 4)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ps.psms_filter_step(ctx, 0, step=10_000, inner_prec=ps.PREC_F32, **prm)
+    recs, ms = _timed_steps(ps, torch, ctx, prm, ps.PREC_F32, False, steps, flush)
+    out = {"dims": list(wl["dims"]), "block": list(wl["block"]), "kappa": wl["kappa"], "n_block": wl["n_block"],
+           "n_global": wl["n_global"], "tol": wl["tol"], "ms_per_step": round(ms / steps, 2),
+           "accepted_updates_per_s": _accepted(recs) / (ms * 1e-3),
+           "block_acceptance": sum(r["n_accept_blocks"] for r in recs) / sum(r["n_blocks"] for r in recs),
+           "delta_block_mean": float(np.mean([r["delta_block"].mean() for r in recs])),
+           "gauge_fix_steps_per_step": sum(r["gf_steps"] for r in recs) / steps,
+           "dw": dw, "heatbath": hb}
+    ctx.close()
+    return out
 
 
 def our_arm(args):
@@ -406,52 +433,40 @@ def our_arm(args):
     _build.build()
     wl = WORKLOADS[args.workload]
     stream = torch.cuda.current_stream()
-    ctx = ps.psms_create(wl["dims"], wl["block"], wl["kappa"], 2)
-    ps.psms_set_stream(ctx, stream)
-    seed = SEED + 4 + 1000 * rank
-    ps.psms_gauge_init(ctx, 0, wl["eps"], seed)
-    if wl["therm"]:
-        ps.psms_gauge_sweep(ctx, 0, ps.ACTIVE_ALL, wl["therm"], 2, wl["beta"], seed, 1 << 40)
+    seed = SEED + 1 + 1000 * rank
+    prec = {"f32": ps.PREC_F32, "f64": ps.PREC_F64}
+    prm = _filter_prm(ps, wl, seed)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    # the headline arm: learned level + FP32 inner iterations + batched solves
+    ctx = _new_chain(ps, torch, wl, seed)
     plaq0, _ = ps.psms_plaquette(ctx, 0)
-    prm = dict(beta0=wl["beta"], n_iter=wl["n_iter"], n_or=wl["n_or"], n_block=wl["n_block"],
-               n_global=wl["n_global"], tol=wl["tol"], inner_prec=ps.PREC_F32, seed=seed)
-    step_id = 0
-
-    def step():
-        nonlocal step_id
-        r = ps.psms_filter_step(ctx, 0, step=step_id, **prm)
-        step_id += 1
-        return r
-
-    for _ in range(args.warmup):
-        step()
+    t0 = time.perf_counter()
+    losses = train_learned(ps, torch, ctx, wl["train_props"], n_interp=wl["n_block"])
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    for i in range(args.warmup):
+        ps.psms_filter_step(ctx, 0, step=100_000 + i, inner_prec=ps.PREC_F32, learned=True, **prm)
     torch.cuda.synchronize()
     barrier(ws)
     n_launch0 = ps.load_library().psms_kernel_launches()
     ps.psms_profile_enable(ctx, 10 + ps.PREC_F32)
-    recs = []
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e0.record(stream)
-        for _ in range(args.steps):
-            recs.append(step())
-        e1.record(stream)
+        tw = time.perf_counter()
+        torch.cuda.nvtx.range_push("timed_steps")
+        recs, ms = _timed_steps(ps, torch, ctx, prm, ps.PREC_F32, True, args.steps, flush)
         torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
+        torch.cuda.nvtx.range_pop()
+        wall = time.perf_counter() - tw
     barrier(ws)
-    ms = e0.elapsed_time(e1)
     n_launch = ps.load_library().psms_kernel_launches() - n_launch0
     hop_n, hop_ms, hop_bytes = ps.psms_profile_read(ctx)
     blk_n, blk_ms, blk_bytes = ps.psms_profile_read_block(ctx)
     ps.psms_profile_enable(ctx, 0)
     ms_max = allmax(ws, ms)
-    accepted = sum(1 for r in recs if r["accept_global"] and r["n_accept_blocks"] > 0)
-    accepted_all = allsum(ws, accepted)
-    value = accepted_all / (ms_max * 1e-3)
-    attempted = allsum(ws, len(recs)) / (ms_max * 1e-3)
+    accepted = _accepted(recs)
+    value = allsum(ws, accepted) / (ms_max * 1e-3)
 
     # end to end through the C ABI with host buffers: H2D of the gauge field,
     # one filter step, D2H of the updated field, every step
@@ -464,10 +479,10 @@ def our_arm(args):
     barrier(ws)
     t0 = time.perf_counter()
     e2e_acc = 0
-    for _ in range(args.steps):
+    for i in range(args.steps):
         dev_links.copy_(host_links, non_blocking=True)
         ps.psms_gauge_set(ctx, 0, dev_links)
-        r = step()
+        r = ps.psms_filter_step(ctx, 0, step=200_000 + i, inner_prec=ps.PREC_F32, learned=True, **prm)
         e2e_acc += int(r["accept_global"] and r["n_accept_blocks"] > 0)
         ps.psms_gauge_get(ctx, 0, dev_links)
         host_links.copy_(dev_links, non_blocking=True)
@@ -475,9 +490,8 @@ def our_arm(args):
     e2e_s = allmax(ws, time.perf_counter() - t0)
     e2e_value = allsum(ws, e2e_acc) / e2e_s
     link_bytes = V * 4 * 9 * 16
+    ctx.close()
 
-    dw = measure_dw(ps, ctx, torch)
-    hb = measure_heatbath(ps, ctx, torch, wl)
     peak, peak_kind = peaks()
     rl_hop = roofline_entry("hop_kernel<float> (Wilson hop of the FP32 inner Krylov iterations)", hop_n, hop_ms,
                             hop_bytes, peak, peak_kind)
@@ -487,7 +501,35 @@ def our_arm(args):
     rl_main, rl_other = (rl_blk, rl_hop) if blk_ms >= hop_ms else (rl_hop, rl_blk)
     if rank != 0:
         return
-    compare = None if args.no_compare else compare_16(ps, torch)
+
+    # the other arms on identical proposals and noise (same seed and steps)
+    arms = {"learned_mixed": {"s_per_step": ms / args.steps / 1e3, "accepted_updates_per_s": accepted / (ms * 1e-3),
+                              "accepted_blocks_per_s": sum(r["n_accept_blocks"] for r in recs if r["accept_global"])
+                              / (ms * 1e-3),
+                              "learned_pass": sum(r["n_accept_learned"] for r in recs) /
+                              sum(r["n_blocks"] for r in recs), "train_s": round(train_s, 2),
+                              "train_loss_first_last": [losses[0], losses[-1]]}}
+    ref = None
+    if not args.no_compare:
+        for name, inner, learned in ARMS[1:]:
+            c = _new_chain(ps, torch, wl, seed)
+            ps.psms_filter_step(c, 0, step=100_000, inner_prec=prec[inner], **prm)
+            rr, mm = _timed_steps(ps, torch, c, prm, prec[inner], False, args.compare_steps, flush)
+            arms[name] = {"s_per_step": mm / len(rr) / 1e3, "accepted_updates_per_s": _accepted(rr) / (mm * 1e-3),
+                          "accepted_blocks_per_s": sum(r["n_accept_blocks"] for r in rr if r["accept_global"])
+                          / (mm * 1e-3), "steps": len(rr)}
+            if name == "mixed":
+                ref = rr
+            else:
+                # same proposals and noise: the estimate differences are the
+                # solver precision (FP32 inner vs FP64 inner, both refined)
+                db = max(float(np.abs(a["delta_block"] - b["delta_block"]).max()) for a, b in zip(ref, rr))
+                dg = max(abs(a["delta_global"] - b["delta_global"]) for a, b in zip(ref, rr))
+                arms["mixed"]["max_estimate_diff_vs_fp64"] = max(db, dg)
+            c.close()
+        arms["speedup_learned_mixed_vs_plain_fp64_s_per_step"] = (arms["plain_fp64"]["s_per_step"] /
+                                                                  arms["learned_mixed"]["s_per_step"])
+    large = None if args.no_large else large_workload(ps, torch)
     full_iters = sum(r["solver_iters"] for r in recs) / max(len(recs), 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -497,22 +539,21 @@ def our_arm(args):
         "config": {"workload": args.workload, "dims": list(wl["dims"]), "block": list(wl["block"]),
                    "kappa": wl["kappa"], "beta": wl["beta"], "eps": wl["eps"], "n_block": wl["n_block"],
                    "n_global": wl["n_global"], "tol": wl["tol"], "inner": "fp32 in fp64 defect correction",
-                   "l2": "inputs larger than L2 (1.2 GB links)", "parallelism": f"independent chains x{ws}"},
-        "attempted_updates_per_s": attempted,
+                   "learned_level": True, "gauge_fix": "relative, block interiors, fp32 steps",
+                   "l2": "flushed between timed steps (256 MB write, outside the step events)",
+                   "parallelism": f"independent chains x{ws}"},
         "acceptance": {"global": sum(r["accept_global"] for r in recs) / len(recs),
                        "blocks": sum(r["n_accept_blocks"] for r in recs) / sum(r["n_blocks"] for r in recs)},
         "solver_iters_per_step": full_iters,
-        "delta_block_mean": float(sum(float(r["delta_block"].mean()) for r in recs) / len(recs)),
-        "delta_block_std": float(sum(float(r["delta_block"].std()) for r in recs) / len(recs)),
+        "gauge_fix_steps_per_step": sum(r["gf_steps"] for r in recs) / len(recs),
         "plaquette_start": plaq0,
-        "dw": dict(dw, peak_gbs=peak, frac_bf16=round(dw["bf16"]["GB/s"] / peak, 4)),
         "roofline": rl_main,
         "roofline_secondary": rl_other,
-        "compare_16^4": compare,
-        "heatbath": hb,
+        "arms": arms,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": link_bytes, "d2h_bytes_per_step": link_bytes},
         "gpu_launches": n_launch,
         "wall_s_timed": wall,
+        "large_workload_32^3x64": large,
     }
     line["clocks"] = clk.summary()
     if not args.no_cpu_baseline:
@@ -608,12 +649,14 @@ STEP_MODEL = {"32^3x64": (4000, 0.5), "16^4": (3000, 0.5), "4^4": (600, 0.3)}
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="32^3x64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="16^4", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-compare", action="store_true", help="skip the 16^4 plain / mixed / learned comparison")
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 and mixed arms")
+    ap.add_argument("--compare-steps", type=int, default=6, help="timed steps of each comparison arm")
+    ap.add_argument("--no-large", action="store_true", help="skip the 32^3x64 measurements")
     ap.add_argument("--dw-only", action="store_true", help="stand-alone D_w measurement only")
     ap.add_argument("--solve-only", action="store_true", help="single-system solver measurement only")
     ap.add_argument("--batch-only", action="store_true", help="config-3 multi-lattice batched block solves")

@@ -103,7 +103,7 @@ def test_global_level_parity_with_projector():
     assert np.abs(got - ref).max() < 1e-8
 
 
-def test_filter_step_parity_config1():
+def test_filter_step_parity_4x4_2x4_blocks():
     """4^4 lattice, 2^4 blocks, kappa 0.15, eps 0.3, beta 5.3, N = 4 (3 steps):
     identical decisions, estimates within 1e-8, identical links."""
     dims, block, kappa = (4, 4, 4, 4), (2, 2, 2, 2), 0.15
