@@ -334,6 +334,11 @@ psms_status psms_profile_read(psms_ctx *ctx, long long *launches, double *total_
  * summed milliseconds and algorithmic bytes (per block-CG iteration and
  * half-block site: 4416 B with FP32 inner iterations, 8832 B with FP64). */
 psms_status psms_profile_read_block(psms_ctx *ctx, long long *launches, double *total_ms, double *bytes);
+/* Per block-solver launch since profiling was enabled (the first 4096, in
+ * launch order): CUDA-event milliseconds and algorithmic bytes.  Writes
+ * min(n_max, recorded) entries to the host arrays ms, bytes (each may be
+ * NULL) and their number to *n_out. */
+psms_status psms_profile_block_launches(psms_ctx *ctx, int n_max, int *n_out, double *ms, double *bytes);
 
 /* Dirichlet block solve that allocates no memory.  The paper has no
  * counterpart: this is a deployment variant of psms_solve for op =
@@ -375,6 +380,14 @@ psms_status psms_relative_gauge_fix(psms_ctx *ctx, int field_old, int field_new,
                                     const psms_relgf_params *prm, int *steps, double *alpha, double *theta,
                                     int *swapped, void *g_dev);
 
+/* Force the Wilson-hop kernel variant (register cap and, for the whole
+ * lattice, the branch-free specialisation; 8 variants for FP32 links in the
+ * whole-lattice mode, 4 otherwise, used modulo their count) instead of the
+ * autotuned one; -1 returns to autotuning.  All variants compute the same
+ * operator.  *n_variants (may be NULL) receives 8.  PSMS_EINVAL outside
+ * -1..7. */
+psms_status psms_hop_variant(psms_ctx *ctx, int variant, int *n_variants);
+
 /* ---- checkpoint / resume ----------------------------------------------------
  * The chain state: the FP64 gauge field of slot `field` (canonical layout),
  * the caller's filter-step counter and seed, and the learned level's
@@ -390,8 +403,10 @@ psms_status psms_checkpoint_load(psms_ctx *ctx, int field, const char *path, uin
  * their first use per shape and the fastest kept; every variant computes
  * the same result.  block_variant >= 0 forces block-solver variant
  * (cluster size, min CTAs per SM) = (1,1),(1,4),(2,1),(2,4),(4,1),(4,4),
- * (8,1),(8,4) for index 0..7 (falling back to 0 when the block is too small
- * for the cluster); -1 restores the tuned choice.  Clears the tuning cache. */
+ * (8,1),(8,4) for index 0..7 and (1,1),(1,4) with one out-of-line copy of
+ * the hop for 8, 9 (falling back to 0 when the block is too small for the
+ * cluster); -1 restores the tuned choice.  Clears the tuning cache.
+ * PSMS_EINVAL outside -1..9. */
 psms_status psms_autotune(psms_ctx *ctx, int enable, int block_variant);
 
 /* Number of CUDA kernels the library has launched in this process. */

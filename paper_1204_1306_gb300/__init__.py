@@ -22,7 +22,7 @@ __all__ = [
     "psms_mlp_train", "psms_block_plan_create", "psms_block_plan_run", "psms_block_plan_schedule",
     "psms_block_plan_destroy", "BlockPlan", "psms_autotune", "psms_profile_read_block",
     "psms_domain_features_pair", "psms_checkpoint_save", "psms_checkpoint_load",
-    "psms_relative_gauge_fix",
+    "psms_relative_gauge_fix", "psms_profile_block_launches", "psms_hop_variant",
     "PREC_F64", "PREC_F32", "PREC_BF16", "OP_FULL", "OP_BLOCKS", "ACTIVE_BLOCKS", "ACTIVE_ALL",
     "LEVEL_BLOCK", "LEVEL_GLOBAL", "EST_INTERP", "EST_INDEPENDENT",
 ]
@@ -131,6 +131,8 @@ _SIGS = {
     "psms_autotune": [_P, _I, _I],
     "psms_checkpoint_save": [_P, _I, ctypes.c_char_p, _U64, _U64],
     "psms_relative_gauge_fix": [_P, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P],
+    "psms_profile_block_launches": [_P, _I, _P, _P, _P],
+    "psms_hop_variant": [_P, _I, _P],
     "psms_checkpoint_load": [_P, _I, ctypes.c_char_p, ctypes.POINTER(_U64), ctypes.POINTER(_U64)],
     "psms_profile_read_block": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), ctypes.POINTER(_D)],
     "psms_profile_enable": [_P, _I],
@@ -436,6 +438,22 @@ def psms_profile_read_block(ctx):
     n, ms, by = ctypes.c_longlong(), _D(), _D()
     ctx.check(ctx.lib.psms_profile_read_block(ctx.handle, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
     return n.value, ms.value, by.value
+
+
+def psms_hop_variant(ctx, variant):
+    """Force Wilson-hop variant `variant` (-1: autotuned); returns the count."""
+    n = _I()
+    ctx.check(ctx.lib.psms_hop_variant(ctx.handle, int(variant), ctypes.byref(n)))
+    return n.value
+
+
+def psms_profile_block_launches(ctx, n_max=4096):
+    """[(ms, algorithmic bytes)] of the block-solver launches since profiling
+    was enabled, in launch order."""
+    n = _I()
+    ms, by = (_D * n_max)(), (_D * n_max)()
+    ctx.check(ctx.lib.psms_profile_block_launches(ctx.handle, int(n_max), ctypes.byref(n), ms, by))
+    return [(ms[i], by[i]) for i in range(n.value)]
 
 
 def psms_relative_gauge_fix(ctx, field_old, field_new, out_old, out_new, g_dev=None, **kw):

@@ -146,6 +146,7 @@ static void prof_collect_block(psms_ctx *c) {
         c->prof_b_ms += ms;
         c->prof_b_bytes += pp.second;
         c->prof_b_launches += 1;
+        if (c->prof_b_list.size() < 4096) c->prof_b_list.push_back({ms, pp.second});
     }
     c->prof_b_pending.clear();
     c->last_block_slot = -1;
@@ -783,6 +784,7 @@ psms_status psms_profile_enable(psms_ctx *ctx, int enable) {
     ctx->prof_b_launches = 0;
     ctx->prof_b_ms = 0;
     ctx->prof_b_bytes = 0;
+    ctx->prof_b_list.clear();
     PSMS_CATCH(ctx)
 }
 
@@ -792,6 +794,14 @@ long long psms_kernel_launches(void) { return launch_counter(); }
 // has_mlp, then the FP64 links in the canonical layout, then (if has_mlp)
 // the MLP parameter block as float32
 static const char PSMS_MAGIC[8] = {'P', 'S', 'M', 'S', 'C', 'K', 'P', '1'};
+
+psms_status psms_hop_variant(psms_ctx *ctx, int variant, int *n_variants) {
+    PSMS_TRY(ctx)
+    if (variant < -1 || variant > 7) fail(PSMS_EINVAL, "hop variant must be -1 or 0..7");
+    ctx->forced_hop_variant = variant;
+    if (n_variants) *n_variants = 8;
+    PSMS_CATCH(ctx)
+}
 
 psms_status psms_checkpoint_save(psms_ctx *ctx, int field, const char *path, uint64_t step, uint64_t seed) {
     PSMS_TRY(ctx)
@@ -866,6 +876,19 @@ psms_status psms_checkpoint_load(psms_ctx *ctx, int field, const char *path, uin
     PSMS_CATCH(ctx)
 }
 
+psms_status psms_profile_block_launches(psms_ctx *ctx, int n_max, int *n_out, double *ms, double *bytes) {
+    PSMS_TRY(ctx)
+    if (n_max < 0 || !n_out) fail(PSMS_EINVAL, "n_max >= 0 and n_out required");
+    prof_collect_block(ctx);
+    const int n = std::min(n_max, (int)ctx->prof_b_list.size());
+    for (int i = 0; i < n; ++i) {
+        if (ms) ms[i] = ctx->prof_b_list[i].first;
+        if (bytes) bytes[i] = ctx->prof_b_list[i].second;
+    }
+    *n_out = n;
+    PSMS_CATCH(ctx)
+}
+
 psms_status psms_profile_read_block(psms_ctx *ctx, long long *launches, double *total_ms, double *bytes) {
     PSMS_TRY(ctx)
     prof_collect_block(ctx);
@@ -877,11 +900,12 @@ psms_status psms_profile_read_block(psms_ctx *ctx, long long *launches, double *
 
 psms_status psms_autotune(psms_ctx *ctx, int enable, int block_variant) {
     PSMS_TRY(ctx)
-    if (block_variant < -1 || block_variant > 7) fail(PSMS_EINVAL, "block_variant must be -1 or 0..7");
+    if (block_variant < -1 || block_variant > 9) fail(PSMS_EINVAL, "block_variant must be -1 or 0..9");
     ctx->autotune = enable != 0;
     ctx->forced_block_variant = block_variant;
     ctx->block_variant.clear();
-    for (auto &row : ctx->hop_variant) row[0] = row[1] = -1;
+    for (auto &row : ctx->hop_variant)
+        for (auto &cell : row) cell[0] = cell[1] = -1;
     PSMS_CATCH(ctx)
 }
 

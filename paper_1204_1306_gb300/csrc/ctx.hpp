@@ -60,8 +60,9 @@ struct psms_ctx {
     int prof_cap = 0;
     long long prof_launches = 0;
     // autotuned hop-kernel variant per (storage precision, both parities)
-    int hop_variant[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
+    int hop_variant[3][2][2] = {{{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}};
     bool autotune = true;
+    int forced_hop_variant = -1;  // -1: autotuned; else the variant index (mod the variant count)
     // autotuned block-solver variant per (precision, block size, batched)
     std::map<long long, int> block_variant;
     int forced_block_variant = -1;
@@ -75,6 +76,7 @@ struct psms_ctx {
     int last_block_slot = -1;
     long long prof_b_launches = 0;
     double prof_b_ms = 0, prof_b_bytes = 0;
+    std::vector<std::pair<float, double>> prof_b_list;  // per launch: (ms, algorithmic bytes), first 4096
 };
 
 namespace psms {

@@ -38,7 +38,11 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return t;  // valid in thread 0
 }
 
-template <class S, class SL, int NT, int MINB>
+// ALL = 1: specialised for HOP_ALL (every neighbour exists): the eight
+// neighbour indices are computed first and the eight hops run as one
+// branch-free sequence, so the compiler can issue later directions' loads
+// before earlier directions' arithmetic (more loads in flight per thread).
+template <class S, class SL, int NT, int MINB, int ALL>
 __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S::elem> a) {
     using R = typename SL::R;
     using E = typename S::elem;
@@ -93,6 +97,30 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
         const R sg = a.dag ? R(-1) : R(1);
         Spinor<R> acc;
         zero(acc);
+        if constexpr (ALL) {
+            long long snb[8];
+            int bsg[8];
+#pragma unroll
+            for (int d = 0; d < 8; ++d) neighbour(g, bi, r, p, y, ll, d >> 1, (d & 1) ? -1 : 1, HOP_ALL, snb[d], bsg[d]);
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                const int mu = d >> 1;
+                const bool fwd = (d & 1) == 0;
+                Spinor<R> v = load_spinor_ro<S>(in, a.in.cs, snb[d] - a.in.off);
+                const R tt = fwd ? -sg : sg;
+                Half<R> h = project(mu, tt, v);
+                if (mu == 0) {
+                    // antiperiodic time boundary: sign on the hop
+                    const R bsr = R(bsg[d]);
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) h.c[q][c] = bsr * h.c[q][c];
+                }
+                SU3<R> u = load_link<SL>(U, g.V, mu, fwd ? s : snb[d]);
+                reconstruct_add(mu, tt, fwd ? su3_mul(u, h) : su3_dag_mul(u, h), acc);
+            }
+        } else {
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
             long long sn;
@@ -123,6 +151,7 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
                 SU3<R> u = load_link<SL>(U, g.V, mu, sn);
                 reconstruct_add(mu, tb, su3_dag_mul(u, h), acc);
             }
+        }
         }
         const R cb = (R)a.b;
         Spinor<R> o;
@@ -220,13 +249,27 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
     // y2, U only), so the extra tuning launches leave the result unchanged.
     using KFn = void (*)(const HopArgs<E>);
     constexpr bool f32 = sizeof(typename SL::R) == 4;
-    static const KFn variants32[] = {hop_kernel<S, SL, HOP_NT, 2>, hop_kernel<S, SL, HOP_NT, 6>,
-                                     hop_kernel<S, SL, HOP_NT, 7>, hop_kernel<S, SL, HOP_NT, 8>};
-    static const KFn variants64[] = {hop_kernel<S, SL, HOP_NT, 2>};
-    const KFn *vars = f32 ? variants32 : variants64;
-    const int nvar = f32 ? 4 : 1;
-    int &choice = c->hop_variant[h.prec][h.p < 0 ? 1 : 0];
-    if (choice < 0 && c->autotune && nvar > 1 && slot < 0) {
+    // FP32 links: register caps 2, 6, 7, 8 CTAs/SM; for the whole lattice
+    // (HOP_ALL) the branch-free specialisation with caps 4, 5, 6, 7 besides
+    const bool all = h.mode == HOP_ALL;
+    const KFn *vars;
+    int nvar;
+    if constexpr (f32) {
+        static const KFn v32[] = {hop_kernel<S, SL, HOP_NT, 2, 0>, hop_kernel<S, SL, HOP_NT, 6, 0>,
+                                  hop_kernel<S, SL, HOP_NT, 7, 0>, hop_kernel<S, SL, HOP_NT, 8, 0>};
+        static const KFn v32all[] = {hop_kernel<S, SL, HOP_NT, 2, 0>, hop_kernel<S, SL, HOP_NT, 6, 0>,
+                                     hop_kernel<S, SL, HOP_NT, 7, 0>, hop_kernel<S, SL, HOP_NT, 8, 0>,
+                                     hop_kernel<S, SL, HOP_NT, 4, 1>, hop_kernel<S, SL, HOP_NT, 5, 1>,
+                                     hop_kernel<S, SL, HOP_NT, 6, 1>, hop_kernel<S, SL, HOP_NT, 7, 1>};
+        vars = all ? v32all : v32;
+        nvar = all ? 8 : 4;
+    } else {
+        static const KFn v64[] = {hop_kernel<S, SL, HOP_NT, 2, 0>};
+        vars = v64;
+        nvar = 1;
+    }
+    int &choice = c->hop_variant[h.prec][h.p < 0 ? 1 : 0][all ? 1 : 0];
+    if (choice < 0 && c->autotune && nvar > 1 && slot < 0 && c->forced_hop_variant < 0) {
         cudaEvent_t e0, e1;
         cuda_check(cudaEventCreate(&e0), "tune event");
         cuda_check(cudaEventCreate(&e1), "tune event");
@@ -250,7 +293,8 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
         cudaEventDestroy(e1);
         PSMS_LAUNCH_CHECK("hop_kernel (autotune)");
     }
-    const int v = (choice >= 0 && choice < nvar) ? choice : (f32 ? 1 : 0);
+    int v = (choice >= 0 && choice < nvar) ? choice : (f32 ? 1 : 0);
+    if (c->forced_hop_variant >= 0) v = c->forced_hop_variant % nvar;
     vars[v]<<<grid, HOP_NT, 0, c->stream>>>(a);
     PSMS_LAUNCH_CHECK("hop_kernel");
     if (slot >= 0) prof_end(c, slot, bytes);

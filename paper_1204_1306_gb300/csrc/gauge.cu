@@ -409,39 +409,74 @@ void translate(psms_ctx *c, const double2 *src, double2 *dst, const int sh[4]) {
 
 // out_i = ((N - i)/N) U + (i/N) U', i = i0 .. i0 + n - 1, FP64 and optional FP32
 // FP32 link element index of the FP64 element t = (mu * 9 + e) * V + s
-__device__ __forceinline__ long long f32_link_index(long long t, long long V) {
-    const long long s = t % V;
-    const long long me = t / V;
-    return link_idx<Store<float>>(V, (int)(me / 9), (int)(me % 9), s);
-}
-
-__global__ void interp_kernel(const double2 *U, const double2 *Up, double2 *out64, float2 *out32, long long n_el, int N,
-                              int i0, long long V) {
+// U_i = ((N - i)/N) U + (i/N) U' for i = i0 .. i0 + n - 1, one thread per
+// link: the link of both endpoints is read once, every system's FP64 copy
+// ([mu][e][s]) and FP32 copy (four 16-byte units of element pairs, then
+// element 8) are written with full coalesced stores
+__global__ void interp_kernel(const double2 *U, const double2 *Up, double2 *out64, float2 *out32, int N, int i0,
+                              int n, long long V) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_el) return;
-    const int i = i0 + blockIdx.y;
-    const double a = (double)(N - i) / N, b = (double)i / N;
-    const double2 u = U[t], v = Up[t];
-    const double2 w = make_double2(a * u.x + b * v.x, a * u.y + b * v.y);
-    if (out64) out64[(long long)blockIdx.y * n_el + t] = w;
-    if (out32) out32[(long long)blockIdx.y * n_el + f32_link_index(t, V)] = make_float2((float)w.x, (float)w.y);
+    if (t >= 4 * V) return;
+    const int mu = (int)(t / V);
+    const long long s = t - (long long)mu * V;
+    double2 u[9], v[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        u[e] = U[((long long)mu * 9 + e) * V + s];
+        v[e] = Up[((long long)mu * 9 + e) * V + s];
+    }
+    const long long n_el = 36 * V;
+    for (int k = 0; k < n; ++k) {
+        const int i = i0 + k;
+        const double a = (double)(N - i) / N, b = (double)i / N;
+        double2 w[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) w[e] = make_double2(a * u[e].x + b * v[e].x, a * u[e].y + b * v[e].y);
+        if (out64) {
+#pragma unroll
+            for (int e = 0; e < 9; ++e) out64[(long long)k * n_el + ((long long)mu * 9 + e) * V + s] = w[e];
+        }
+        if (out32) {
+            float2 *o = out32 + (long long)k * n_el + (long long)mu * 9 * V;
+            float4 *o4 = reinterpret_cast<float4 *>(o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                o4[(long long)q * V + s] = make_float4((float)w[2 * q].x, (float)w[2 * q].y, (float)w[2 * q + 1].x,
+                                                       (float)w[2 * q + 1].y);
+            o[8 * V + s] = make_float2((float)w[8].x, (float)w[8].y);
+        }
+    }
 }
 
 void interpolate(psms_ctx *c, const double2 *U, const double2 *Up, double2 *out64, float2 *out32, int N, int i0,
                  int n) {
-    const long long n_el = 36 * c->g.V;
-    dim3 grid((unsigned)((n_el + 255) / 256), n);
-    interp_kernel<<<grid, 256, 0, c->stream>>>(U, Up, out64, out32, n_el, N, i0, c->g.V);
+    const long long nl = 4 * c->g.V;
+    interp_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, c->stream>>>(U, Up, out64, out32, N, i0, n, c->g.V);
     PSMS_LAUNCH_CHECK("interpolate");
 }
 
-__global__ void to_f32_kernel(const double2 *a, float2 *b, long long n, long long V) {
+// FP32 copy of an FP64 link field (n_el = 36 V elements), one thread per
+// link, full 16-byte stores of the element pairs
+__global__ void to_f32_kernel(const double2 *a, float2 *b, long long V) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) b[f32_link_index(t, V)] = make_float2((float)a[t].x, (float)a[t].y);
+    if (t >= 4 * V) return;
+    const int mu = (int)(t / V);
+    const long long s = t - (long long)mu * V;
+    const double2 *q = a + (long long)mu * 9 * V + s;
+    float2 *o = b + (long long)mu * 9 * V;
+    float4 *o4 = reinterpret_cast<float4 *>(o);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const double2 x = q[(2 * p) * V], y = q[(2 * p + 1) * V];
+        o4[(long long)p * V + s] = make_float4((float)x.x, (float)x.y, (float)y.x, (float)y.y);
+    }
+    const double2 z = q[8 * V];
+    o[8 * V + s] = make_float2((float)z.x, (float)z.y);
 }
 
 void links_to_f32(psms_ctx *c, const double2 *a, float2 *b, long long n_el) {
-    to_f32_kernel<<<(unsigned)((n_el + 255) / 256), 256, 0, c->stream>>>(a, b, n_el, c->g.V);
+    const long long V = n_el / 36;
+    to_f32_kernel<<<(unsigned)((4 * V + 255) / 256), 256, 0, c->stream>>>(a, b, V);
     PSMS_LAUNCH_CHECK("links_to_f32");
 }
 

@@ -137,6 +137,33 @@ __device__ __forceinline__ double block_hop(const Geom &g, const BlockInfo &bi, 
     return nrm;
 }
 
+// The same hop as an out-of-line function: one copy of its code serves every
+// call site of the block CG (instruction-cache footprint), at the price of a
+// call and of no specialisation on constant arguments.
+template <class S, class SL, class SY>
+__device__ __noinline__ double block_hop_ool(const Geom &g, const BlockInfo &bi, int r, int p, int dag,
+                                             const typename S::elem *in, long long in_cs, long long in_off,
+                                             typename S::elem *out, long long out_cs, long long out_off,
+                                             const typename SY::elem *y, long long y_cs, long long y_off, double a,
+                                             double b, const typename SL::elem *U, int jlo, int jhi) {
+    return block_hop<S, SL, SY>(g, bi, r, p, dag, in, in_cs, in_off, out, out_cs, out_off, y, y_cs, y_off, a, b, U,
+                                jlo, jhi);
+}
+
+template <int OUTL, class S, class SL, class SY>
+__device__ __forceinline__ double hop_call(const Geom &g, const BlockInfo &bi, int r, int p, int dag,
+                                           const typename S::elem *in, long long in_cs, long long in_off,
+                                           typename S::elem *out, long long out_cs, long long out_off,
+                                           const typename SY::elem *y, long long y_cs, long long y_off, double a,
+                                           double b, const typename SL::elem *U, int jlo, int jhi) {
+    if constexpr (OUTL)
+        return block_hop_ool<S, SL, SY>(g, bi, r, p, dag, in, in_cs, in_off, out, out_cs, out_off, y, y_cs, y_off, a,
+                                        b, U, jlo, jhi);
+    else
+        return block_hop<S, SL, SY>(g, bi, r, p, dag, in, in_cs, in_off, out, out_cs, out_off, y, y_cs, y_off, a, b,
+                                    U, jlo, jhi);
+}
+
 template <class E>
 struct BlockVecs {
     // inner-precision vectors of one system (views with the system offset applied)
@@ -171,7 +198,7 @@ struct BlockSolveArgs {
 // The whole solve of one (block rl, system k) item by CL CTAs (a thread-block
 // cluster, CL = 1: one CTA) of NT threads; CTA rank q of the cluster works on
 // the sites j in [q Vbh/CL, (q+1) Vbh/CL) of each parity.
-template <class SV, class SL, int NT, int CL>
+template <class SV, class SL, int NT, int CL, int OUTL = 0>
 __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const int k, double *sh) {
     using E = typename SV::elem;
     using R = typename SL::R;
@@ -243,7 +270,7 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
         double rn = 0;
         bar<CL>();
         for (int p = 0; p < 2; ++p) {
-            block_hop<S64, S64, S64>(g, bi, r, p, 0, x, a.x.cs, a.x.off, r64, a.r64.cs, a.r64.off, b, a.b.cs,
+            hop_call<OUTL, S64, S64, S64>(g, bi, r, p, 0, x, a.x.cs, a.x.off, r64, a.r64.cs, a.r64.off, b, a.b.cs,
                                      a.b.off, 1.0, 0.5, U64, jlo, jhi);
         }
         bar<CL>();
@@ -277,7 +304,7 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
             }
         bar<CL>();
         // bhat_o = rhs_o + H_o(rhs_e)/(2A)
-        double bb = block_hop<SV, SL, SV>(g, bi, r, 1, 0, v.rhs, V, 0, v.bhat, Vh, Vh, v.rhs, V, 0, 1.0,
+        double bb = hop_call<OUTL, SV, SL, SV>(g, bi, r, 1, 0, v.rhs, V, 0, v.bhat, Vh, Vh, v.rhs, V, 0, 1.0,
                                           0.5 / A, Uin, jlo, jhi);
         bb = cl_sum<NT, CL>(bb, sh);
         // e_o = 0, rho = bhat, res = Dhat^dag rho, p = res
@@ -289,9 +316,9 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
             }
         }
         bar<CL>();
-        block_hop<SV, SL, SV>(g, bi, r, 0, 1, v.rho, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin, jlo, jhi);
+        hop_call<OUTL, SV, SL, SV>(g, bi, r, 0, 1, v.rho, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin, jlo, jhi);
         bar<CL>();
-        double rr = block_hop<SV, SL, SV>(g, bi, r, 1, 1, v.t, Vh, 0, v.res, Vh, Vh, v.rho, Vh, Vh, A, c4, Uin, jlo, jhi);
+        double rr = hop_call<OUTL, SV, SL, SV>(g, bi, r, 1, 1, v.t, Vh, 0, v.res, Vh, Vh, v.rho, Vh, Vh, A, c4, Uin, jlo, jhi);
         rr = cl_sum<NT, CL>(rr, sh);
         for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
             const long long s = blo[1] + j - Vh;
@@ -302,9 +329,9 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
         int it = 0;
         while (total_it + it < a.maxit) {
             // q = Dhat p
-            block_hop<SV, SL, SV>(g, bi, r, 0, 0, v.pp, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin, jlo, jhi);
+            hop_call<OUTL, SV, SL, SV>(g, bi, r, 0, 0, v.pp, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin, jlo, jhi);
             bar<CL>();
-            double qq = block_hop<SV, SL, SV>(g, bi, r, 1, 0, v.t, Vh, 0, v.q, Vh, Vh, v.pp, Vh, Vh, A, c4, Uin, jlo, jhi);
+            double qq = hop_call<OUTL, SV, SL, SV>(g, bi, r, 1, 0, v.t, Vh, 0, v.q, Vh, Vh, v.pp, Vh, Vh, A, c4, Uin, jlo, jhi);
             qq = cl_sum<NT, CL>(qq, sh);
             const R alpha = (R)(rr / qq);
             double rhorho = 0;
@@ -327,9 +354,9 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
             ++it;
             if (rhorho <= target) break;
             // sv = Dhat^dag q
-            block_hop<SV, SL, SV>(g, bi, r, 0, 1, v.q, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin, jlo, jhi);
+            hop_call<OUTL, SV, SL, SV>(g, bi, r, 0, 1, v.q, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin, jlo, jhi);
             bar<CL>();
-            block_hop<SV, SL, SV>(g, bi, r, 1, 1, v.t, Vh, 0, v.sv, Vh, Vh, v.q, Vh, Vh, A, c4, Uin, jlo, jhi);
+            hop_call<OUTL, SV, SL, SV>(g, bi, r, 1, 1, v.t, Vh, 0, v.sv, Vh, Vh, v.q, Vh, Vh, A, c4, Uin, jlo, jhi);
             bar<CL>();
             double rr_new = 0;
             for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
@@ -355,7 +382,7 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
         }
         total_it += it;
         // e_e = (rhs_e + H_e(e_o)/2) / A
-        block_hop<SV, SL, SV>(g, bi, r, 0, 0, v.e, V, 0, v.e, V, 0, v.rhs, V, 0, 1.0 / A, 0.5 / A, Uin, jlo, jhi);
+        hop_call<OUTL, SV, SL, SV>(g, bi, r, 0, 0, v.e, V, 0, v.e, V, 0, v.rhs, V, 0, 1.0 / A, 0.5 / A, Uin, jlo, jhi);
         bar<CL>();
         // x += e / scale (FP64)
         const double unscale = sqrt(rn);
@@ -397,17 +424,17 @@ __global__ void __launch_bounds__(NT) block_solve_kernel(const BlockSolveArgs a)
 
 // CL CTAs (one cluster) per (block, system): grid (n_ranks * CL, n_sys),
 // cluster dimension (CL, 1, 1); MINB resident CTAs per SM caps registers
-template <class SV, class SL, int NT, int CL, int MINB>
+template <class SV, class SL, int NT, int CL, int MINB, int OUTL>
 __global__ void __launch_bounds__(NT, MINB) block_solve_cluster_kernel(const BlockSolveArgs a) {
     __shared__ double sh[NT / 32 + 1];
-    block_solve_item<SV, SL, NT, CL>(a, blockIdx.x / CL, blockIdx.y, sh);
+    block_solve_item<SV, SL, NT, CL, OUTL>(a, blockIdx.x / CL, blockIdx.y, sh);
 }
 
-template <class SV, class SL, int CL, int MINB>
+template <class SV, class SL, int CL, int MINB, int OUTL = 0>
 static void launch_block_cl(psms_ctx *c, const BlockSolveArgs &a, int n_ranks, int n_sys) {
     constexpr int NT = 128;
     if constexpr (CL == 1) {
-        block_solve_cluster_kernel<SV, SL, NT, 1, MINB><<<dim3(n_ranks, n_sys), NT, 0, c->stream>>>(a);
+        block_solve_cluster_kernel<SV, SL, NT, 1, MINB, OUTL><<<dim3(n_ranks, n_sys), NT, 0, c->stream>>>(a);
         PSMS_LAUNCH_CHECK("block_solve_cluster_kernel");
     } else {
         cudaLaunchConfig_t cfg = {};
@@ -422,14 +449,18 @@ static void launch_block_cl(psms_ctx *c, const BlockSolveArgs &a, int n_ranks, i
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cuda_check(cudaLaunchKernelEx(&cfg, block_solve_cluster_kernel<SV, SL, NT, CL, MINB>, a), "cluster launch");
+        cuda_check(cudaLaunchKernelEx(&cfg, block_solve_cluster_kernel<SV, SL, NT, CL, MINB, OUTL>, a),
+                   "cluster launch");
         PSMS_LAUNCH_CHECK("block_solve_cluster_kernel");
     }
 }
 
 template <class SV, class SL>
-static void launch_block_variant(psms_ctx *c, const BlockSolveArgs &a, int n_ranks, int n_sys, int cl, int minb) {
-    switch (cl * 10 + minb) {
+static void launch_block_variant(psms_ctx *c, const BlockSolveArgs &a, int n_ranks, int n_sys, int cl, int minb,
+                                 int outl) {
+    switch (outl * 100 + cl * 10 + minb) {
+        case 111: launch_block_cl<SV, SL, 1, 1, 1>(c, a, n_ranks, n_sys); break;
+        case 114: launch_block_cl<SV, SL, 1, 4, 1>(c, a, n_ranks, n_sys); break;
         case 11: launch_block_cl<SV, SL, 1, 1>(c, a, n_ranks, n_sys); break;
         case 14: launch_block_cl<SV, SL, 1, 4>(c, a, n_ranks, n_sys); break;
         case 21: launch_block_cl<SV, SL, 2, 1>(c, a, n_ranks, n_sys); break;
@@ -473,22 +504,26 @@ void block_solve(psms_ctx *c, const BlockSolveReq &q) {
     a.resid = q.resid;
     a.xnorm2 = q.xnorm2;
     a.status = q.status;
-    // Variants (cluster size CL, min CTAs per SM): one block solved by CL
-    // CTAs of a thread-block cluster.  The autotuner times every admissible
+    // Variants (cluster size CL, min CTAs per SM, out-of-line hop): one block
+    // solved by CL CTAs of a thread-block cluster; the last two call one
+    // out-of-line copy of the hop instead of inlining it at every call site.  The autotuner times every admissible
     // variant once on the first solve of each (precision, block size,
     // batched or not) and keeps the fastest; a solve is idempotent (x is set
     // from b), so the tuning runs leave the result unchanged.
     struct Var {
-        int cl, minb;
+        int cl, minb, outl;
     };
-    static const Var vars[] = {{1, 1}, {1, 4}, {2, 1}, {2, 4}, {4, 1}, {4, 4}, {8, 1}, {8, 4}};
-    const int nvar = 8;
+    static const Var vars[] = {{1, 1, 0}, {1, 4, 0}, {2, 1, 0}, {2, 4, 0}, {4, 1, 0},
+                               {4, 4, 0}, {8, 1, 0}, {8, 4, 0}, {1, 1, 1}, {1, 4, 1}};
+    const int nvar = 10;
     auto admissible = [&](int v) { return vars[v].cl == 1 || g.Vbh / vars[v].cl >= 128; };
     auto launch = [&](int v) {
         if (in64)
-            launch_block_variant<Store<double>, Store<double>>(c, a, q.n_ranks, q.n_sys, vars[v].cl, vars[v].minb);
+            launch_block_variant<Store<double>, Store<double>>(c, a, q.n_ranks, q.n_sys, vars[v].cl, vars[v].minb,
+                                                               vars[v].outl);
         else
-            launch_block_variant<Store<float>, Store<float>>(c, a, q.n_ranks, q.n_sys, vars[v].cl, vars[v].minb);
+            launch_block_variant<Store<float>, Store<float>>(c, a, q.n_ranks, q.n_sys, vars[v].cl, vars[v].minb,
+                                                             vars[v].outl);
     };
     const long long key = ((long long)q.inner_prec << 40) | ((long long)g.Vbh << 8) | (q.n_sys > 1 ? 1 : 0);
     auto it = c->block_variant.find(key);

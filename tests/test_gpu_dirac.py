@@ -5,7 +5,7 @@ import pytest
 import torch
 
 import paper_1204_1306_gb300 as ps
-from oracle import dirac, gauge
+from oracle import dirac, gauge, lattice
 from tests import seeded
 from tests.gpu_util import canonical, get_links, native, rel_err, set_links
 
@@ -97,6 +97,35 @@ def test_dw_low_precision(prec, tol):
     out = torch.zeros_like(nat)
     ps.psms_dw_apply(ctx, 0, ps.OP_FULL, nat, out, prec)
     assert rel_err(canonical(ctx, out, prec), dirac.apply_D(U, psi, kappa)) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [(ps.PREC_F32, 2e-6), (ps.PREC_BF16, 2e-2)])
+def test_dw_every_hop_variant(prec, tol):
+    """Every autotuned Wilson-hop variant (register caps, branch-free
+    whole-lattice specialisation), forced one by one: whole-lattice D_w with
+    the antiperiodic time boundary, and the Dirichlet block operator."""
+    dims, block = (8, 8, 4, 8), (4, 4, 4, 4)
+    geom = lattice.Geometry(dims, block)
+    kappa = 0.157
+    ctx = ps.psms_create(dims, block, kappa, 1)
+    ps.psms_gauge_init(ctx, 0, 0.5, 23)
+    U = gauge.generate_links(dims, 0.5, 23)
+    psi = seeded.spinor(dims, 24)
+    nat = native(ctx, psi, prec)
+    ref_full = dirac.apply_D(U, psi, kappa)
+    ref_blk = dirac.apply_D(U, psi, kappa, geom, mode="block")
+    n = ps.psms_hop_variant(ctx, 0)
+    for v in range(n):
+        ps.psms_hop_variant(ctx, v)
+        out = torch.zeros_like(nat)
+        ps.psms_dw_apply(ctx, 0, ps.OP_FULL, nat, out, prec)
+        assert rel_err(canonical(ctx, out, prec), ref_full) < tol, v
+        out = torch.zeros_like(nat)
+        ps.psms_dw_apply(ctx, 0, ps.OP_BLOCKS, nat, out, prec)
+        assert rel_err(canonical(ctx, out, prec), ref_blk) < tol, v
+    ps.psms_hop_variant(ctx, -1)
+    with pytest.raises(ps.PsmsError):
+        ps.psms_hop_variant(ctx, 8)
 
 
 def test_plaquette_and_translation():
