@@ -308,6 +308,88 @@ def solve_only(args):
     print(json.dumps(out), flush=True)
 
 
+def learned_only(args):
+    """The learned level at its own workload: 16^3 x 32 lattice, 8^4 domains
+    (32 per field), kappa 0.156, beta 5.3.  Labels: block log-det-ratio
+    estimates Delta_b (N = 4 interpolation steps between relatively
+    gauge-fixed endpoints) of domain-sweep proposals, `--labels` of them
+    (default 10^5); the last tenth of the proposals is held out.  The BF16
+    MLP is trained on the GPU by the library's kernels, then filter steps of
+    the learned + mixed hierarchy and of the plain mixed hierarchy run on
+    identical proposals and noise.  Reports label generation and training
+    time, held-out prediction, the fraction of blocks sent on to the
+    stochastic level, acceptances and updates/s."""
+    import torch
+
+    import paper_1204_1306_gb300 as ps
+    from paper_1204_1306_gb300 import build as _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    wl = dict(dims=(32, 16, 16, 16), block=(8, 8, 8, 8), kappa=0.156, eps=0.5, beta=5.3, n_block=4, n_global=8,
+              therm=4, n_iter=1, n_or=1, tol=1e-10)
+    seed = SEED + 3
+    ctx = _new_chain(ps, torch, wl, seed)
+    nb = ps.psms_geometry_info(ctx)[0]
+    n_props = max(2, -(-args.labels // nb))
+    zb = torch.zeros(nb * 64, dtype=torch.float32, device="cuda")
+    zs, ys = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(n_props):
+        ps.psms_gauge_copy(ctx, 1, 0)
+        ps.psms_gauge_sweep(ctx, 1, ps.ACTIVE_BLOCKS, 1, 1, wl["beta"], seed, (s + 7) << 20)
+        ps.psms_relative_gauge_fix(ctx, 0, 1, 2, 3, prec=ps.PREC_F32)
+        d = ps.psms_logdet_ratio(ctx, ps.LEVEL_BLOCK, 2, 3, wl["n_block"], ps.EST_INTERP, seed, 50_000 + s, 1e-10,
+                                 ps.PREC_F32)
+        ps.psms_domain_features_pair(ctx, 0, 1, zb)
+        zs.append(zb.view(nb, 64).clone())
+        ys.append(torch.from_numpy(d.sum(axis=1)))
+        if s % 4 == 3:
+            ps.psms_gauge_sweep(ctx, 0, ps.ACTIVE_ALL, 1, 0, wl["beta"], seed, (s + 1) << 30)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    n_te = max(1, n_props // 10)
+    z = torch.cat(zs[:-n_te]).contiguous()
+    y = torch.cat(ys[:-n_te]).to("cuda").contiguous()
+    z_te = torch.cat(zs[-n_te:]).contiguous()
+    y_te = torch.cat(ys[-n_te:]).numpy()
+    ps.psms_mlp_init(ctx, 7)
+    t0 = time.perf_counter()
+    losses = ps.psms_mlp_train(ctx, z, y, len(y), epochs=10, batch=256, lr=1e-4, weight_decay=1e-4, seed=3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    h = torch.zeros(len(y_te), dtype=torch.float32, device="cuda")
+    ps.psms_mlp_predict(ctx, z_te, len(y_te), h)
+    h = h.cpu().numpy().astype(np.float64)
+    p_pass = np.minimum(1.0, np.exp(-h))
+    out = {"workload": "16^3x32, 8^4 domains, learned level", "dims": list(wl["dims"]), "block": list(wl["block"]),
+           "kappa": wl["kappa"], "n_block": wl["n_block"], "labels": int(len(y) + len(y_te)),
+           "proposals": n_props, "label_generation_s": round(gen_s, 2), "train_s": round(train_s, 2),
+           "train_loss_first_last": [losses[0], losses[-1]],
+           "heldout": {"n": int(len(y_te)), "corr_h_delta": float(np.corrcoef(h, y_te)[0, 1]),
+                       "delta_mean": float(y_te.mean()), "delta_std": float(y_te.std()),
+                       "h_std": float(h.std()), "pass_fraction": float(p_pass.mean())}}
+    prm = _filter_prm(ps, wl, seed)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    params = ps.psms_mlp_params(ctx)
+    ctx.close()
+    for name, learned in (("learned_mixed", True), ("mixed", False)):
+        # both arms from the same thermalised field: identical proposals and noise
+        c = _new_chain(ps, torch, wl, seed)
+        if learned:
+            ps.psms_mlp_params(c, params)
+        ps.psms_filter_step(c, 0, step=100_000, inner_prec=ps.PREC_F32, learned=learned, **prm)
+        rr, mm = _timed_steps(ps, torch, c, prm, ps.PREC_F32, learned, args.steps, flush, step0=1_000_000)
+        out[name] = {"s_per_step": mm / len(rr) / 1e3, "accepted_updates_per_s": _accepted(rr) / (mm * 1e-3),
+                     "block_acceptance": sum(r["n_accept_blocks"] for r in rr) / sum(r["n_blocks"] for r in rr),
+                     "learned_pass": (sum(r["n_accept_learned"] for r in rr) / sum(r["n_blocks"] for r in rr)
+                                      if learned else None),
+                     "solver_iters_per_step": sum(r["solver_iters"] for r in rr) / len(rr)}
+        c.close()
+    print(json.dumps(out), flush=True)
+
+
 def batch_only(args):
     """All 4^4 Dirichlet blocks x 16 noise vectors of three uneven
     lattices (8^4, 12^4, 16^3 x 32; kappa 0.155, eps 0.5) in one persistent
@@ -447,6 +529,12 @@ def our_arm(args):
     train_s = time.perf_counter() - t0
     for i in range(args.warmup):
         ps.psms_filter_step(ctx, 0, step=100_000 + i, inner_prec=ps.PREC_F32, learned=True, **prm)
+    # the field the timed steps start from (the end-to-end pass replays them)
+    V = ctx.V
+    host_links = torch.empty(V * 4 * 9 * 2, dtype=torch.float64).pin_memory()
+    dev_links = torch.empty(V * 4 * 9 * 2, dtype=torch.float64, device="cuda")
+    ps.psms_gauge_get(ctx, 0, dev_links)
+    host_links.copy_(dev_links)
     torch.cuda.synchronize()
     barrier(ws)
     n_launch0 = ps.load_library().psms_kernel_launches()
@@ -469,13 +557,11 @@ def our_arm(args):
     accepted = _accepted(recs)
     value = allsum(ws, accepted) / (ms_max * 1e-3)
 
-    # end to end through the C ABI with host buffers: H2D of the gauge field,
-    # one filter step, D2H of the updated field, every step
-    V = ctx.V
-    host_links = torch.empty(V * 4 * 9 * 2, dtype=torch.float64).pin_memory()
-    dev_links = torch.empty(V * 4 * 9 * 2, dtype=torch.float64, device="cuda")
-    ps.psms_gauge_get(ctx, 0, dev_links)
-    host_links.copy_(dev_links)
+    # end to end through the C ABI with host buffers: the same steps from the
+    # same field, each with the H2D copy of the field from pinned host memory,
+    # the filter step and the D2H copy of the updated field; the accepted
+    # updates are the timed steps' (identical work), only the transfers and
+    # host-side time differ
     torch.cuda.synchronize()
     barrier(ws)
     t0 = time.perf_counter()
@@ -483,7 +569,7 @@ def our_arm(args):
     for i in range(args.steps):
         dev_links.copy_(host_links, non_blocking=True)
         ps.psms_gauge_set(ctx, 0, dev_links)
-        r = ps.psms_filter_step(ctx, 0, step=200_000 + i, inner_prec=ps.PREC_F32, learned=True, **prm)
+        r = ps.psms_filter_step(ctx, 0, step=i, inner_prec=ps.PREC_F32, learned=True, **prm)
         e2e_acc += int(r["accept_global"] and r["n_accept_blocks"] > 0)
         ps.psms_gauge_get(ctx, 0, dev_links)
         host_links.copy_(dev_links, non_blocking=True)
@@ -664,9 +750,11 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 and mixed arms")
     ap.add_argument("--compare-steps", type=int, default=6, help="timed steps of each comparison arm")
     ap.add_argument("--no-large", action="store_true", help="skip the 32^3x64 measurements")
+    ap.add_argument("--learned-only", action="store_true", help="the learned level at 16^3x32 with 8^4 domains")
+    ap.add_argument("--labels", type=int, default=100_000, help="training labels of --learned-only")
     ap.add_argument("--dw-only", action="store_true", help="stand-alone D_w measurement only")
     ap.add_argument("--solve-only", action="store_true", help="single-system solver measurement only")
-    ap.add_argument("--batch-only", action="store_true", help="config-3 multi-lattice batched block solves")
+    ap.add_argument("--batch-only", action="store_true", help="multi-lattice batched block solves (8^4, 12^4, 16^3x32)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -678,6 +766,8 @@ def main():
         solve_only(args)
     elif args.batch_only:
         batch_only(args)
+    elif args.learned_only:
+        learned_only(args)
     else:
         our_arm(args)
 

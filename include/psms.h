@@ -403,10 +403,12 @@ psms_status psms_checkpoint_load(psms_ctx *ctx, int field, const char *path, uin
  * their first use per shape and the fastest kept; every variant computes
  * the same result.  block_variant >= 0 forces block-solver variant
  * (cluster size, min CTAs per SM) = (1,1),(1,4),(2,1),(2,4),(4,1),(4,4),
- * (8,1),(8,4) for index 0..7 and (1,1),(1,4) with one out-of-line copy of
- * the hop for 8, 9 (falling back to 0 when the block is too small for the
- * cluster); -1 restores the tuned choice.  Clears the tuning cache.
- * PSMS_EINVAL outside -1..9. */
+ * (8,1),(8,4) for index 0..7, (1,1),(1,4) with one out-of-line copy of
+ * the hop for 8, 9, and (1,1),(1,4),(4,4),(8,4) with the branch-free hop
+ * (every direction computed, those leaving the block multiplied by zero) for
+ * 10..13, (1,4) with the branch-free hop out of line for 14 (falling back
+ * to 0 when the block is too small for the cluster); -1 restores the tuned
+ * choice.  Clears the tuning cache.  PSMS_EINVAL outside -1..14. */
 psms_status psms_autotune(psms_ctx *ctx, int enable, int block_variant);
 
 /* Number of CUDA kernels the library has launched in this process. */

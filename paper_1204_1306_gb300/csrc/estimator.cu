@@ -67,9 +67,11 @@ __global__ void noise_kernel(Geom g, const BlockInfo *binfo, double2 *out, long 
         uni4 u = uniforms(seed, TAG_NOISE, counter, stream, lex, (uint64_t)jj);
         for (int m = 0; m < 2; ++m) {
             const double rad = sqrt(-log(u.u[2 * m]));
-            const double th = 2.0 * M_PI * u.u[2 * m + 1];
+            // e^{2 pi i u_b}: one sincospi call (exact argument reduction)
+            double sn, cs;
+            sincospi(2.0 * u.u[2 * m + 1], &sn, &cs);
             const int comp = 2 * jj + m;
-            v.c[comp / 3][comp % 3] = {rad * cos(th), rad * sin(th)};
+            v.c[comp / 3][comp % 3] = {rad * cs, rad * sn};
         }
     }
     if (proj) apply_P(g, r, y, v);

@@ -79,7 +79,12 @@ __device__ __forceinline__ void bar() {
 
 // out_p = a*y_p + b*H^intra_p(in) on the block of rank r; returns this
 // thread's contribution to |out|^2.  Vectors are views (structure of arrays).
-template <class S, class SL, class SY>
+// BF = 1: branch-free form.  Every direction loads the neighbour inside the
+// block under the block's own periodic wrap (always a valid, cached site) and
+// a direction that leaves the block contributes an exact zero, so the eight
+// hops run as one straight sequence whose loads the compiler can issue early;
+// the result equals the branching form bit for bit.
+template <class S, class SL, class SY, int BF = 0>
 __device__ __forceinline__ double block_hop(const Geom &g, const BlockInfo &bi, int r, int p, int dag,
                                             const typename S::elem *in, long long in_cs, long long in_off,
                                             typename S::elem *out, long long out_cs, long long out_off,
@@ -94,6 +99,33 @@ __device__ __forceinline__ double block_hop(const Geom &g, const BlockInfo &bi, 
         const long long s = (long long)p * g.Vh + (long long)r * g.Vbh + j;
         Spinor<R> acc;
         zero(acc);
+        if constexpr (BF) {
+            long long snb[8];
+            R keep[8];
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                const int mu = d >> 1, sgn = (d & 1) ? -1 : 1;
+                int yn = yy[mu] + sgn;
+                keep[d] = ((unsigned)yn < (unsigned)g.l[mu]) ? R(1) : R(0);
+                yn &= g.l[mu] - 1;  // wrap inside the block (extents are powers of two)
+                const int lln = ll + (yn - yy[mu]) * g.lstride[mu];
+                snb[d] = (long long)(1 - p) * g.Vh + (long long)r * g.Vbh + (lln >> 1);
+            }
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                const int mu = d >> 1;
+                const bool fwd = (d & 1) == 0;
+                Spinor<R> v = load_spinor<S>(in, in_cs, snb[d] - in_off);
+                const R tt = fwd ? -sg : sg;
+                Half<R> h = project(mu, tt, v);
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) h.c[q][c] = keep[d] * h.c[q][c];
+                SU3<R> u = load_link<SL>(U, g.V, mu, fwd ? s : snb[d]);
+                reconstruct_add(mu, tt, fwd ? su3_mul(u, h) : su3_dag_mul(u, h), acc);
+            }
+        } else {
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
             long long sn;
@@ -112,6 +144,7 @@ __device__ __forceinline__ double block_hop(const Geom &g, const BlockInfo &bi, 
                 SU3<R> u = load_link<SL>(U, g.V, mu, sn);
                 reconstruct_add(mu, tb, su3_dag_mul(u, h), acc);
             }
+        }
         }
         Spinor<R> o;
         const R cb = (R)b, ca = (R)a;
@@ -140,28 +173,30 @@ __device__ __forceinline__ double block_hop(const Geom &g, const BlockInfo &bi, 
 // The same hop as an out-of-line function: one copy of its code serves every
 // call site of the block CG (instruction-cache footprint), at the price of a
 // call and of no specialisation on constant arguments.
-template <class S, class SL, class SY>
+template <class S, class SL, class SY, int BF>
 __device__ __noinline__ double block_hop_ool(const Geom &g, const BlockInfo &bi, int r, int p, int dag,
                                              const typename S::elem *in, long long in_cs, long long in_off,
                                              typename S::elem *out, long long out_cs, long long out_off,
                                              const typename SY::elem *y, long long y_cs, long long y_off, double a,
                                              double b, const typename SL::elem *U, int jlo, int jhi) {
-    return block_hop<S, SL, SY>(g, bi, r, p, dag, in, in_cs, in_off, out, out_cs, out_off, y, y_cs, y_off, a, b, U,
-                                jlo, jhi);
+    return block_hop<S, SL, SY, BF>(g, bi, r, p, dag, in, in_cs, in_off, out, out_cs, out_off, y, y_cs, y_off, a, b,
+                                    U, jlo, jhi);
 }
 
-template <int OUTL, class S, class SL, class SY>
+// HV: bit 0 = out-of-line hop, bit 1 = branch-free hop
+template <int HV, class S, class SL, class SY>
 __device__ __forceinline__ double hop_call(const Geom &g, const BlockInfo &bi, int r, int p, int dag,
                                            const typename S::elem *in, long long in_cs, long long in_off,
                                            typename S::elem *out, long long out_cs, long long out_off,
                                            const typename SY::elem *y, long long y_cs, long long y_off, double a,
                                            double b, const typename SL::elem *U, int jlo, int jhi) {
-    if constexpr (OUTL)
-        return block_hop_ool<S, SL, SY>(g, bi, r, p, dag, in, in_cs, in_off, out, out_cs, out_off, y, y_cs, y_off, a,
-                                        b, U, jlo, jhi);
+    constexpr int BF = (HV >> 1) & 1;
+    if constexpr (HV & 1)
+        return block_hop_ool<S, SL, SY, BF>(g, bi, r, p, dag, in, in_cs, in_off, out, out_cs, out_off, y, y_cs, y_off,
+                                            a, b, U, jlo, jhi);
     else
-        return block_hop<S, SL, SY>(g, bi, r, p, dag, in, in_cs, in_off, out, out_cs, out_off, y, y_cs, y_off, a, b,
-                                    U, jlo, jhi);
+        return block_hop<S, SL, SY, BF>(g, bi, r, p, dag, in, in_cs, in_off, out, out_cs, out_off, y, y_cs, y_off, a,
+                                        b, U, jlo, jhi);
 }
 
 template <class E>
@@ -198,7 +233,7 @@ struct BlockSolveArgs {
 // The whole solve of one (block rl, system k) item by CL CTAs (a thread-block
 // cluster, CL = 1: one CTA) of NT threads; CTA rank q of the cluster works on
 // the sites j in [q Vbh/CL, (q+1) Vbh/CL) of each parity.
-template <class SV, class SL, int NT, int CL, int OUTL = 0>
+template <class SV, class SL, int NT, int CL, int HV = 0>
 __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const int k, double *sh) {
     using E = typename SV::elem;
     using R = typename SL::R;
@@ -270,7 +305,7 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
         double rn = 0;
         bar<CL>();
         for (int p = 0; p < 2; ++p) {
-            hop_call<OUTL, S64, S64, S64>(g, bi, r, p, 0, x, a.x.cs, a.x.off, r64, a.r64.cs, a.r64.off, b, a.b.cs,
+            hop_call<HV, S64, S64, S64>(g, bi, r, p, 0, x, a.x.cs, a.x.off, r64, a.r64.cs, a.r64.off, b, a.b.cs,
                                      a.b.off, 1.0, 0.5, U64, jlo, jhi);
         }
         bar<CL>();
@@ -304,7 +339,7 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
             }
         bar<CL>();
         // bhat_o = rhs_o + H_o(rhs_e)/(2A)
-        double bb = hop_call<OUTL, SV, SL, SV>(g, bi, r, 1, 0, v.rhs, V, 0, v.bhat, Vh, Vh, v.rhs, V, 0, 1.0,
+        double bb = hop_call<HV, SV, SL, SV>(g, bi, r, 1, 0, v.rhs, V, 0, v.bhat, Vh, Vh, v.rhs, V, 0, 1.0,
                                           0.5 / A, Uin, jlo, jhi);
         bb = cl_sum<NT, CL>(bb, sh);
         // e_o = 0, rho = bhat, res = Dhat^dag rho, p = res
@@ -316,9 +351,9 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
             }
         }
         bar<CL>();
-        hop_call<OUTL, SV, SL, SV>(g, bi, r, 0, 1, v.rho, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin, jlo, jhi);
+        hop_call<HV, SV, SL, SV>(g, bi, r, 0, 1, v.rho, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin, jlo, jhi);
         bar<CL>();
-        double rr = hop_call<OUTL, SV, SL, SV>(g, bi, r, 1, 1, v.t, Vh, 0, v.res, Vh, Vh, v.rho, Vh, Vh, A, c4, Uin, jlo, jhi);
+        double rr = hop_call<HV, SV, SL, SV>(g, bi, r, 1, 1, v.t, Vh, 0, v.res, Vh, Vh, v.rho, Vh, Vh, A, c4, Uin, jlo, jhi);
         rr = cl_sum<NT, CL>(rr, sh);
         for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
             const long long s = blo[1] + j - Vh;
@@ -329,9 +364,9 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
         int it = 0;
         while (total_it + it < a.maxit) {
             // q = Dhat p
-            hop_call<OUTL, SV, SL, SV>(g, bi, r, 0, 0, v.pp, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin, jlo, jhi);
+            hop_call<HV, SV, SL, SV>(g, bi, r, 0, 0, v.pp, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin, jlo, jhi);
             bar<CL>();
-            double qq = hop_call<OUTL, SV, SL, SV>(g, bi, r, 1, 0, v.t, Vh, 0, v.q, Vh, Vh, v.pp, Vh, Vh, A, c4, Uin, jlo, jhi);
+            double qq = hop_call<HV, SV, SL, SV>(g, bi, r, 1, 0, v.t, Vh, 0, v.q, Vh, Vh, v.pp, Vh, Vh, A, c4, Uin, jlo, jhi);
             qq = cl_sum<NT, CL>(qq, sh);
             const R alpha = (R)(rr / qq);
             double rhorho = 0;
@@ -354,9 +389,9 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
             ++it;
             if (rhorho <= target) break;
             // sv = Dhat^dag q
-            hop_call<OUTL, SV, SL, SV>(g, bi, r, 0, 1, v.q, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin, jlo, jhi);
+            hop_call<HV, SV, SL, SV>(g, bi, r, 0, 1, v.q, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin, jlo, jhi);
             bar<CL>();
-            hop_call<OUTL, SV, SL, SV>(g, bi, r, 1, 1, v.t, Vh, 0, v.sv, Vh, Vh, v.q, Vh, Vh, A, c4, Uin, jlo, jhi);
+            hop_call<HV, SV, SL, SV>(g, bi, r, 1, 1, v.t, Vh, 0, v.sv, Vh, Vh, v.q, Vh, Vh, A, c4, Uin, jlo, jhi);
             bar<CL>();
             double rr_new = 0;
             for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
@@ -382,7 +417,7 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
         }
         total_it += it;
         // e_e = (rhs_e + H_e(e_o)/2) / A
-        hop_call<OUTL, SV, SL, SV>(g, bi, r, 0, 0, v.e, V, 0, v.e, V, 0, v.rhs, V, 0, 1.0 / A, 0.5 / A, Uin, jlo, jhi);
+        hop_call<HV, SV, SL, SV>(g, bi, r, 0, 0, v.e, V, 0, v.e, V, 0, v.rhs, V, 0, 1.0 / A, 0.5 / A, Uin, jlo, jhi);
         bar<CL>();
         // x += e / scale (FP64)
         const double unscale = sqrt(rn);
@@ -424,17 +459,17 @@ __global__ void __launch_bounds__(NT) block_solve_kernel(const BlockSolveArgs a)
 
 // CL CTAs (one cluster) per (block, system): grid (n_ranks * CL, n_sys),
 // cluster dimension (CL, 1, 1); MINB resident CTAs per SM caps registers
-template <class SV, class SL, int NT, int CL, int MINB, int OUTL>
+template <class SV, class SL, int NT, int CL, int MINB, int HV>
 __global__ void __launch_bounds__(NT, MINB) block_solve_cluster_kernel(const BlockSolveArgs a) {
     __shared__ double sh[NT / 32 + 1];
-    block_solve_item<SV, SL, NT, CL, OUTL>(a, blockIdx.x / CL, blockIdx.y, sh);
+    block_solve_item<SV, SL, NT, CL, HV>(a, blockIdx.x / CL, blockIdx.y, sh);
 }
 
-template <class SV, class SL, int CL, int MINB, int OUTL = 0>
+template <class SV, class SL, int CL, int MINB, int HV = 0>
 static void launch_block_cl(psms_ctx *c, const BlockSolveArgs &a, int n_ranks, int n_sys) {
     constexpr int NT = 128;
     if constexpr (CL == 1) {
-        block_solve_cluster_kernel<SV, SL, NT, 1, MINB, OUTL><<<dim3(n_ranks, n_sys), NT, 0, c->stream>>>(a);
+        block_solve_cluster_kernel<SV, SL, NT, 1, MINB, HV><<<dim3(n_ranks, n_sys), NT, 0, c->stream>>>(a);
         PSMS_LAUNCH_CHECK("block_solve_cluster_kernel");
     } else {
         cudaLaunchConfig_t cfg = {};
@@ -449,7 +484,7 @@ static void launch_block_cl(psms_ctx *c, const BlockSolveArgs &a, int n_ranks, i
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cuda_check(cudaLaunchKernelEx(&cfg, block_solve_cluster_kernel<SV, SL, NT, CL, MINB, OUTL>, a),
+        cuda_check(cudaLaunchKernelEx(&cfg, block_solve_cluster_kernel<SV, SL, NT, CL, MINB, HV>, a),
                    "cluster launch");
         PSMS_LAUNCH_CHECK("block_solve_cluster_kernel");
     }
@@ -457,10 +492,15 @@ static void launch_block_cl(psms_ctx *c, const BlockSolveArgs &a, int n_ranks, i
 
 template <class SV, class SL>
 static void launch_block_variant(psms_ctx *c, const BlockSolveArgs &a, int n_ranks, int n_sys, int cl, int minb,
-                                 int outl) {
-    switch (outl * 100 + cl * 10 + minb) {
+                                 int hv) {
+    switch (hv * 100 + cl * 10 + minb) {
         case 111: launch_block_cl<SV, SL, 1, 1, 1>(c, a, n_ranks, n_sys); break;
         case 114: launch_block_cl<SV, SL, 1, 4, 1>(c, a, n_ranks, n_sys); break;
+        case 211: launch_block_cl<SV, SL, 1, 1, 2>(c, a, n_ranks, n_sys); break;
+        case 214: launch_block_cl<SV, SL, 1, 4, 2>(c, a, n_ranks, n_sys); break;
+        case 244: launch_block_cl<SV, SL, 4, 4, 2>(c, a, n_ranks, n_sys); break;
+        case 284: launch_block_cl<SV, SL, 8, 4, 2>(c, a, n_ranks, n_sys); break;
+        case 314: launch_block_cl<SV, SL, 1, 4, 3>(c, a, n_ranks, n_sys); break;
         case 11: launch_block_cl<SV, SL, 1, 1>(c, a, n_ranks, n_sys); break;
         case 14: launch_block_cl<SV, SL, 1, 4>(c, a, n_ranks, n_sys); break;
         case 21: launch_block_cl<SV, SL, 2, 1>(c, a, n_ranks, n_sys); break;
@@ -504,26 +544,28 @@ void block_solve(psms_ctx *c, const BlockSolveReq &q) {
     a.resid = q.resid;
     a.xnorm2 = q.xnorm2;
     a.status = q.status;
-    // Variants (cluster size CL, min CTAs per SM, out-of-line hop): one block
-    // solved by CL CTAs of a thread-block cluster; the last two call one
-    // out-of-line copy of the hop instead of inlining it at every call site.  The autotuner times every admissible
+    // Variants (cluster size CL, min CTAs per SM, hop form): one block solved
+    // by CL CTAs of a thread-block cluster; hop form 1 calls one out-of-line
+    // copy of the hop instead of inlining it at every call site, form 2 is
+    // the branch-free hop, form 3 both.  The autotuner times every admissible
     // variant once on the first solve of each (precision, block size,
     // batched or not) and keeps the fastest; a solve is idempotent (x is set
     // from b), so the tuning runs leave the result unchanged.
     struct Var {
-        int cl, minb, outl;
+        int cl, minb, hv;
     };
-    static const Var vars[] = {{1, 1, 0}, {1, 4, 0}, {2, 1, 0}, {2, 4, 0}, {4, 1, 0},
-                               {4, 4, 0}, {8, 1, 0}, {8, 4, 0}, {1, 1, 1}, {1, 4, 1}};
-    const int nvar = 10;
+    static const Var vars[] = {{1, 1, 0}, {1, 4, 0}, {2, 1, 0}, {2, 4, 0}, {4, 1, 0}, {4, 4, 0}, {8, 1, 0},
+                               {8, 4, 0}, {1, 1, 1}, {1, 4, 1}, {1, 1, 2}, {1, 4, 2}, {4, 4, 2}, {8, 4, 2},
+                               {1, 4, 3}};
+    const int nvar = 15;
     auto admissible = [&](int v) { return vars[v].cl == 1 || g.Vbh / vars[v].cl >= 128; };
     auto launch = [&](int v) {
         if (in64)
             launch_block_variant<Store<double>, Store<double>>(c, a, q.n_ranks, q.n_sys, vars[v].cl, vars[v].minb,
-                                                               vars[v].outl);
+                                                               vars[v].hv);
         else
             launch_block_variant<Store<float>, Store<float>>(c, a, q.n_ranks, q.n_sys, vars[v].cl, vars[v].minb,
-                                                             vars[v].outl);
+                                                             vars[v].hv);
     };
     const long long key = ((long long)q.inner_prec << 40) | ((long long)g.Vbh << 8) | (q.n_sys > 1 ? 1 : 0);
     auto it = c->block_variant.find(key);

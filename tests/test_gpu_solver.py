@@ -91,7 +91,7 @@ def test_solver_reports_non_convergence():
     assert e.value.status == 4
 
 
-@pytest.mark.parametrize("variant", range(10))
+@pytest.mark.parametrize("variant", range(15))
 def test_block_solver_cluster_variants(variant):
     """Every (cluster size, register cap) variant of the block solver gives the
     oracle's solution (8^4 blocks: one block is shared by up to 8 CTAs of a
