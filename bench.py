@@ -362,7 +362,7 @@ def learned_only(args):
     h = torch.zeros(len(y_te), dtype=torch.float32, device="cuda")
     ps.psms_mlp_predict(ctx, z_te, len(y_te), h)
     h = h.cpu().numpy().astype(np.float64)
-    p_pass = np.minimum(1.0, np.exp(-h))
+    p_pass = np.exp(-np.clip(h, 0.0, 700.0))
     out = {"workload": "16^3x32, 8^4 domains, learned level", "dims": list(wl["dims"]), "block": list(wl["block"]),
            "kappa": wl["kappa"], "n_block": wl["n_block"], "labels": int(len(y) + len(y_te)),
            "proposals": n_props, "label_generation_s": round(gen_s, 2), "train_s": round(train_s, 2),

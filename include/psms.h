@@ -141,6 +141,12 @@ typedef struct {
     int gauge_fix;         /* 1: interpolate between relatively gauge-fixed
                               endpoints (Sec. 4.2) at levels 1 and 2          */
     psms_relgf_params relgf;
+    int proposal_field;    /* -1: level 0 is the domain sweep; else the slot
+                              holding an external proposal, which must differ
+                              from the field on active links only and be
+                              drawn by a symmetric proposal (detailed-balance
+                              tests); the slot is left unchanged             */
+    int translate;         /* 1: random translation after the global level */
 } psms_filter_params;
 
 typedef struct {
@@ -162,7 +168,8 @@ typedef struct {
     double lr;             /* AdamW step size                                  */
     double beta1, beta2, eps;
     double weight_decay;
-    int normalise;         /* 1: set input mean / scale and label scale from the data */
+    int normalise;         /* 1: set the input mean / scale and the output scale ys
+                              (spread of the labels about their mean) from the data */
     uint64_t seed;         /* minibatch shuffling                              */
 } psms_train_params;
 
@@ -190,6 +197,9 @@ psms_status psms_geometry_info(const psms_ctx *ctx, long long *n_blocks, long lo
  * Box-Muller), then reunitarised (Gram-Schmidt rows 0,1; row 2 = conj(r0 x r1)). */
 psms_status psms_gauge_init(psms_ctx *ctx, int field, double eps, uint64_t seed);
 /* Copy a canonical-layout FP64 field in / out of slot `field`. */
+/* psms_gauge_set rejects a field holding NaN or infinite values with
+ * PSMS_EINVAL before writing the slot; psms_spinor_import and psms_solve
+ * do the same for their input spinor. */
 psms_status psms_gauge_set(psms_ctx *ctx, int field, const double *links_dev);
 psms_status psms_gauge_get(psms_ctx *ctx, int field, double *links_dev);
 psms_status psms_gauge_copy(psms_ctx *ctx, int dst, int src);

@@ -111,7 +111,7 @@ def _merge(U, V, acc_b, geom, active):
     return out
 
 
-def filter_step(U, geom, prm, seed, step, h_override=None, gf_override=None):
+def filter_step(U, geom, prm, seed, step, h_override=None, gf_override=None, proposal=None, translate=True):
     """Returns (new field, record dict).
 
     With prm.learned (per-block decisions only) a learned level precedes
@@ -125,9 +125,16 @@ def filter_step(U, geom, prm, seed, step, h_override=None, gf_override=None):
     pair of (U, U'), level 2 between U and the field after level 1, whose
     fixed pair equals the level-1 one on accepted blocks and (U, U) on the
     others (the blocks decouple).  gf_override = (g_1, g_2) replaces the
-    oracle's own transformations with a device's."""
+    oracle's own transformations with a device's.
+
+    proposal: an external proposal (differing from U on active links only,
+    drawn symmetrically) replaces the domain sweep; translate=False skips
+    the translation (both for detailed-balance tests of the chain)."""
     active = geom.active_links()
-    Unew, _, failed = domain_sweep(U, geom, prm.beta0, prm.n_iter, prm.n_or, seed, step * SWEEP_STRIDE)
+    if proposal is None:
+        Unew, _, failed = domain_sweep(U, geom, prm.beta0, prm.n_iter, prm.n_or, seed, step * SWEEP_STRIDE)
+    else:
+        Unew, failed = np.array(proposal, copy=True), 0
     per_block = min(geom.block) >= 3
     passed = np.ones(geom.n_blocks, dtype=bool)
     h = np.zeros(geom.n_blocks)
@@ -184,6 +191,6 @@ def filter_step(U, geom, prm, seed, step, h_override=None, gf_override=None):
         rec["accept_global"] = acc_g
         if not acc_g:
             Ufin = U.copy()
-    s = philox.shift_vector(seed, step, geom.dims)
+    s = philox.shift_vector(seed, step, geom.dims) if translate else (0, 0, 0, 0)
     rec["shift"] = s
     return geom.translate(Ufin, s), rec

@@ -70,7 +70,8 @@ class FilterParams(ctypes.Structure):
                 ("n_block", ctypes.c_int), ("beta_block", ctypes.c_double), ("n_global", ctypes.c_int),
                 ("beta_global", ctypes.c_double), ("global_level", ctypes.c_int), ("tol", ctypes.c_double),
                 ("inner_prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("step", ctypes.c_uint64),
-                ("learned", ctypes.c_int), ("gauge_fix", ctypes.c_int), ("relgf", RelGFParams)]
+                ("learned", ctypes.c_int), ("gauge_fix", ctypes.c_int), ("relgf", RelGFParams),
+                ("proposal_field", ctypes.c_int), ("translate", ctypes.c_int)]
 
 
 class FilterResult(ctypes.Structure):
@@ -300,12 +301,14 @@ def psms_logdet_ratio(ctx, level, field_old, field_new, n, mode, seed, counter, 
 
 def psms_filter_step(ctx, field, *, beta0, n_iter=1, n_or=0, n_block=4, n_global=4, beta_block=0.0,
                      beta_global=0.0, global_level=True, tol=1e-10, inner_prec=PREC_F64, seed=0, step=0,
-                     learned=False, gauge_fix=None):
+                     learned=False, gauge_fix=None, proposal_field=-1, translate=True):
     """gauge_fix: None (off) or a dict of relative gauge-fixing parameters
-    (alpha0, alpha_min, dalpha, theta_tol, max_iter, prec; {} = defaults)."""
+    (alpha0, alpha_min, dalpha, theta_tol, max_iter, prec; {} = defaults).
+    proposal_field: -1 (domain sweep) or the slot of an external proposal."""
     p = FilterParams(float(beta0), int(n_iter), int(n_or), int(n_block), float(beta_block), int(n_global),
                      float(beta_global), int(bool(global_level)), float(tol), int(inner_prec), int(seed), int(step),
-                     int(bool(learned)), int(gauge_fix is not None), _relgf(**(gauge_fix or {})))
+                     int(bool(learned)), int(gauge_fix is not None), _relgf(**(gauge_fix or {})),
+                     int(proposal_field), int(bool(translate)))
     r = FilterResult()
     nb = int(np.prod([d // b for d, b in zip(ctx.dims, ctx.block)]))
     db = (_D * nb)()

@@ -360,10 +360,32 @@ psms_status psms_gauge_init(psms_ctx *ctx, int field, double eps, uint64_t seed)
     PSMS_CATCH(ctx)
 }
 
+__global__ void nonfinite_kernel(const double *p, long long n, unsigned int *count) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(p[i])) {
+            atomicAdd(count, 1u);
+            return;
+        }
+}
+
+// PSMS_EINVAL when any of the n doubles at p (device) is NaN or infinite
+static void require_finite(psms_ctx *c, const double *p, long long n, const char *what) {
+    unsigned int *d = (unsigned int *)scratch(c, "nonfinite", sizeof(unsigned int));
+    cuda_check(cudaMemsetAsync(d, 0, sizeof(unsigned int), c->stream), "nonfinite");
+    const long long blocks = std::min<long long>((n + 255) / 256, 152 * 16);
+    nonfinite_kernel<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, c->stream>>>(p, n, d);
+    PSMS_LAUNCH_CHECK("nonfinite");
+    unsigned int h = 0;
+    cuda_check(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "nonfinite");
+    cuda_check(cudaStreamSynchronize(c->stream), "nonfinite");
+    if (h) fail(PSMS_EINVAL, std::string(what) + " holds NaN or infinite values");
+}
+
 psms_status psms_gauge_set(psms_ctx *ctx, int field, const double *links) {
     PSMS_TRY(ctx)
     check_field(ctx, field);
     if (!links) fail(PSMS_EINVAL, "null links");
+    require_finite(ctx, links, 72 * ctx->g.V, "the gauge field");
     gauge_canonical(ctx, (const double2 *)links, ctx->U64[field], 1);
     touch_field(ctx, field);
     PSMS_CATCH(ctx)
@@ -439,6 +461,7 @@ psms_status psms_spinor_import(psms_ctx *ctx, const double *canon, void *nat, in
     PSMS_TRY(ctx)
     if (!canon || !nat) fail(PSMS_EINVAL, "null pointer");
     elem_size(prec);
+    require_finite(ctx, canon, 24 * ctx->g.V, "the spinor field");
     spinor_canonical(ctx, (const double2 *)canon, nat, prec, 1);
     PSMS_CATCH(ctx)
 }
@@ -488,6 +511,7 @@ psms_status psms_solve(psms_ctx *ctx, int field, int op, const void *b, void *x,
     if (!(tol > 0) || maxit < 1) fail(PSMS_EINVAL, "tol must be > 0 and maxit >= 1");
     elem_size(inner_prec);
     const long long V = ctx->g.V;
+    require_finite(ctx, (const double *)b, 24 * V, "the right-hand side");
     const float2 *U32 = inner_prec == P64 ? nullptr : links32(ctx, field);
     if (op == PSMS_OP_FULL) {
         FullSolveReq q;
@@ -637,11 +661,19 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
     double2 *prop = (double2 *)scratch(ctx, "fs_prop", fb);
     double2 *mid = (double2 *)scratch(ctx, "fs_mid", fb);
     cuda_check(cudaMemcpyAsync(old, cur, fb, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
-    cuda_check(cudaMemcpyAsync(prop, cur, fb, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
-    // level 0: proposal
-    const int failed = gauge_sweep(ctx, prop, PSMS_ACTIVE_BLOCKS, prm->n_iter, prm->n_or, prm->beta0, prm->seed,
-                                   prm->step << 20);
-    if (failed) fail(PSMS_EHEATBATH, "an SU(2) heatbath draw hit its attempt limit");
+    // level 0: proposal (domain sweep, or an external proposal slot)
+    int failed = 0;
+    if (prm->proposal_field >= 0) {
+        check_field(ctx, prm->proposal_field);
+        if (prm->proposal_field == field) fail(PSMS_EINVAL, "the proposal slot must differ from the field");
+        cuda_check(cudaMemcpyAsync(prop, ctx->U64[prm->proposal_field], fb, cudaMemcpyDeviceToDevice, ctx->stream),
+                   "copy");
+    } else {
+        cuda_check(cudaMemcpyAsync(prop, cur, fb, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
+        failed = gauge_sweep(ctx, prop, PSMS_ACTIVE_BLOCKS, prm->n_iter, prm->n_or, prm->beta0, prm->seed,
+                             prm->step << 20);
+        if (failed) fail(PSMS_EHEATBATH, "an SU(2) heatbath draw hit its attempt limit");
+    }
     const int nb = g.nblocks, N1 = prm->n_block;
     bool per_block = true;
     for (int m = 0; m < 4; ++m) per_block &= g.l[m] >= 3;
@@ -742,8 +774,8 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         if (!accg) fin = old;
     }
     // random translation
-    int sh[4];
-    {
+    int sh[4] = {0, 0, 0, 0};
+    if (prm->translate) {
         uni4 u = uniforms(prm->seed, TAG_SHIFT, prm->step, 0, 0, 0);
         for (int m = 0; m < 4; ++m) {
             int v = (int)std::floor(u.u[m] * g.L[m]);

@@ -22,6 +22,7 @@ struct Error {
 
 inline void cuda_check(cudaError_t e, const char *what) {
     if (e != cudaSuccess) {
+        cudaGetLastError();  // clear a non-sticky error so later launch checks do not report it
         psms_status st = (e == cudaErrorMemoryAllocation) ? PSMS_ENOMEM : PSMS_ECUDA;
         fail(st, std::string(what) + ": " + cudaGetErrorString(e));
     }

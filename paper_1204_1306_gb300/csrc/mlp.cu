@@ -678,9 +678,21 @@ psms_status psms_mlp_train(psms_ctx *ctx, const float *feats_dev, const double *
             hp[OFF_MU + col] = (float)mean;
             hp[OFF_SIG + col] = var > 1e-20 ? (float)std::sqrt(var) : 1.f;
         }
-        double ss = 0;
-        for (int i = 0; i < n; ++i) ss += hy[i] * hy[i];
-        hp[OFF_YS] = ss > 0 ? (float)std::sqrt(ss / n) : 1.f;
+        // output scale: the spread of the labels about their mean (an
+        // antisymmetric h cannot represent the mean, so scaling by the RMS
+        // would inflate h when the labels sit far from zero); the RMS if
+        // the labels do not vary
+        double sm = 0, ss = 0;
+        for (int i = 0; i < n; ++i) sm += hy[i];
+        const double mean = sm / n;
+        for (int i = 0; i < n; ++i) ss += (hy[i] - mean) * (hy[i] - mean);
+        double scale = std::sqrt(ss / n);
+        if (!(scale > 1e-12)) {
+            ss = 0;
+            for (int i = 0; i < n; ++i) ss += hy[i] * hy[i];
+            scale = std::sqrt(ss / n);
+        }
+        hp[OFF_YS] = scale > 0 ? (float)scale : 1.f;
         cuda_check(cudaMemcpy(m.p, hp.data(), sizeof(float) * N_PARAM, cudaMemcpyHostToDevice), "norm");
     }
     const int B = std::min(tp->batch, n);

@@ -165,3 +165,38 @@ def test_invalid_arguments_are_reported():
         ps.psms_dw_apply(ctx, 0, ps.OP_FULL, buf, buf, ps.PREC_F64)
     with pytest.raises(ps.PsmsError):
         ps.psms_dw_apply(ctx, 0, 99, buf, torch.zeros_like(buf), ps.PREC_F64)
+
+
+def test_nonfinite_inputs_and_allocation_failure():
+    """NaN / infinite inputs are rejected with PSMS_EINVAL before anything is
+    written; a lattice larger than the device memory fails with PSMS_ENOMEM
+    (a real allocation failure, no fault)."""
+    dims = (4, 4, 4, 4)
+    ctx = ps.psms_create(dims, (2, 2, 2, 2), 0.15, 1)
+    ps.psms_gauge_init(ctx, 0, 0.3, 1)
+    before = get_links(ctx, 0)
+    U = gauge.generate_links(dims, 0.3, 2)
+    U[1, 2, 3, 0, 1, 0, 2] = np.nan
+    with pytest.raises(ps.PsmsError) as e:
+        set_links(ctx, 0, U)
+    assert e.value.status == 1
+    assert np.array_equal(get_links(ctx, 0), before)
+    psi = seeded.spinor(dims, 3)
+    psi[0, 0, 0, 1, 2, 1] = np.inf
+    with pytest.raises(ps.PsmsError) as e:
+        native(ctx, psi)
+    assert e.value.status == 1
+    b = native(ctx, seeded.spinor(dims, 4))
+    bad = b.view(torch.float64).clone()
+    bad[17] = float("nan")
+    x = torch.zeros_like(b)
+    with pytest.raises(ps.PsmsError) as e:
+        ps.psms_solve(ctx, 0, ps.OP_FULL, bad.view(torch.uint8), x, 1e-10, 100, ps.PREC_F64)
+    assert e.value.status == 1
+    # 128^4 sites, two FP64 link slots of 155 GB each: above the device's
+    # memory, so the second allocation fails and everything is freed
+    with pytest.raises(ps.PsmsError) as e:
+        ps.psms_create((128, 128, 128, 128), (8, 8, 8, 8), 0.15, 2)
+    assert e.value.status == 2
+    # the library stays usable
+    ps.psms_dw_apply(ctx, 0, ps.OP_FULL, b, x, ps.PREC_F64)

@@ -95,6 +95,7 @@ def test_interpolation_telescopes():
 def test_estimator_closed_forms():
     """Sec. 4.1: at fixed (U, U'), E[e^-Delta] = det(M^dag M)^-1, E[Delta] =
     Tr(M^dag M - 1), Var[Delta] = sum_k (lambda_k - 1)^2 (Eq. (varstoch2)),
+    E[e^-2 Delta] = det(2 M^dag M - 1)^-1,
     with the oracle's Philox noise on one 2^4 Dirichlet block (192 dims)."""
     geom = lattice.Geometry((4, 4, 4, 4), (2, 2, 2, 2))
     U = gauge.generate_links(geom.dims, 0.3, 31)
@@ -114,6 +115,13 @@ def test_estimator_closed_forms():
     target = np.exp(-np.sum(np.log(lam)))
     sd = np.sqrt(np.exp(-np.sum(np.log(2 * lam - 1))) - target ** 2)
     assert abs(ew.mean() - target) < 5 * sd / np.sqrt(n)
+    # second moment (Sec. 4.1): E[e^-2Delta] = det(2 M^dag M - 1)^-1, with
+    # finite variance when lambda_min > 3/4 (E[e^-4Delta] = det(4 M^dag M - 3)^-1)
+    assert lam.min() > 0.75
+    ew2 = np.exp(-2 * delta)
+    target2 = np.exp(-np.sum(np.log(2 * lam - 1)))
+    sd2 = np.sqrt(np.exp(-np.sum(np.log(4 * lam - 3))) - target2 ** 2)
+    assert abs(ew2.mean() - target2) < 5 * sd2 / np.sqrt(n)
 
 
 # --- global (Schur) estimator --------------------------------------------------
