@@ -147,6 +147,13 @@ def allsum(ws, v):
     return float(t.item())
 
 
+# DRAM bytes / algorithmic bytes of one ncu capture of the kernel on the
+# bench's workload (profiles/block_solve_cluster_kernel_fp32_16x4.md: the
+# first timed block-solver launch, branch-free hop variant); None once the
+# kernel changes
+TRAFFIC_RATIO = {"block_solve_cluster_kernel": 0.148}
+
+
 def roofline_entry(kernel, n, ms, nbytes, peak, peak_kind):
     """achieved = algorithmic bytes of the kernel's launches in the timed steps
     / their summed CUDA-event durations (on the library's stream)."""
@@ -584,6 +591,14 @@ def our_arm(args):
                             hop_bytes, peak, peak_kind)
     rl_blk = roofline_entry("block_solve_cluster_kernel<float> (persistent Dirichlet-block CG, FP32 inner)", blk_n,
                             blk_ms, blk_bytes, peak, peak_kind)
+    ratio = TRAFFIC_RATIO.get("block_solve_cluster_kernel")
+    if ratio is not None and blk_n:
+        # DRAM bytes per launch, scaled from the capture by the algorithmic
+        # bytes (block-CG iterations x sites) of the timed launches
+        rl_blk["traffic"] = ratio * blk_bytes / blk_n
+        rl_blk["traffic_note"] = ("ncu dram__bytes_read+write of the first timed launch / its algorithmic bytes = "
+                                  f"{ratio}, times the mean algorithmic bytes per launch; the block vectors stay in "
+                                  "L1/L2 across iterations, so DRAM carries a fraction of the per-iteration bytes")
     # the dominant kernel of the step: the larger measured time
     rl_main, rl_other = (rl_blk, rl_hop) if blk_ms >= hop_ms else (rl_hop, rl_blk)
     if rank != 0:

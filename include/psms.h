@@ -390,6 +390,13 @@ psms_status psms_relative_gauge_fix(psms_ctx *ctx, int field_old, int field_new,
                                     const psms_relgf_params *prm, int *steps, double *alpha, double *theta,
                                     int *swapped, void *g_dev);
 
+/* Inner Krylov method of the whole-lattice solves (psms_solve with
+ * PSMS_OP_FULL and the global level): even-odd CGNR on Dhat^dag Dhat
+ * (default) or BiCGStab on Dhat; both run inside the same FP64 defect
+ * correction to the same true residual.  PSMS_EINVAL for another kind. */
+enum { PSMS_SOLVER_CGNR = 0, PSMS_SOLVER_BICGSTAB = 1 };
+psms_status psms_full_solver(psms_ctx *ctx, int kind);
+
 /* Force the Wilson-hop kernel variant (register cap and, for the whole
  * lattice, the branch-free specialisation; 8 variants for FP32 links in the
  * whole-lattice mode, 4 otherwise, used modulo their count) instead of the

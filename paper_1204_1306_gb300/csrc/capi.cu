@@ -827,6 +827,13 @@ long long psms_kernel_launches(void) { return launch_counter(); }
 // the MLP parameter block as float32
 static const char PSMS_MAGIC[8] = {'P', 'S', 'M', 'S', 'C', 'K', 'P', '1'};
 
+psms_status psms_full_solver(psms_ctx *ctx, int kind) {
+    PSMS_TRY(ctx)
+    if (kind != PSMS_SOLVER_CGNR && kind != PSMS_SOLVER_BICGSTAB) fail(PSMS_EINVAL, "unknown solver");
+    ctx->full_solver = kind;
+    PSMS_CATCH(ctx)
+}
+
 psms_status psms_hop_variant(psms_ctx *ctx, int variant, int *n_variants) {
     PSMS_TRY(ctx)
     if (variant < -1 || variant > 7) fail(PSMS_EINVAL, "hop variant must be -1 or 0..7");

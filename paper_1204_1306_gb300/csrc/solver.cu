@@ -816,6 +816,9 @@ __global__ void iters_kernel(const CGS *st, int *out, int n) {
     if (k < n) out[k] += st[k].iters;
 }
 
+struct BCS;
+__global__ void iters_bcg_kernel(const BCS *st, int *out, int n);
+
 template <class SV>
 static void inner_cg_full(psms_ctx *c, int n_sys, const void *Uin, long long U_bs, int prec, View<void> rhs,
                           View<void> e, const int *act_in, double delta, int maxit, int *iters_acc) {
@@ -965,6 +968,317 @@ static void inner_cg_full(psms_ctx *c, int n_sys, const void *Uin, long long U_b
     hop_launch(c, h);
 }
 
+// ---------------------------------------------------------------------------
+// BiCGStab on the even-odd operator Dhat (the paper leaves the solver open):
+// per system, with complex scalars kept on the device,
+//   rho = <rh, r>;  beta = (rho / rho_old)(alpha / omega);  p = r + beta (p - omega v)
+//   v = Dhat p;  alpha = rho / <rh, v>;  s = r - alpha v
+//   t = Dhat s;  omega = <t, s> / <t, t>;  x += alpha p + omega s;  r = s - omega t
+// with rh = r_0 = bhat.  A breakdown (<rh, v> = 0, omega = 0) or the
+// iteration cap ends the inner solve; the FP64 defect correction around it
+// restarts from the true residual.  Reductions: per-CTA partials in FP64,
+// finished in a fixed order (deterministic).
+// ---------------------------------------------------------------------------
+struct BCS {
+    double2 rho, alpha, omega, beta;
+    double rr, target;
+    int active, iters;
+};
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__global__ void bcg_init_kernel(BCS *st, const double *bb, int n, double delta, const int *act, int *flags) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    BCS s;
+    s.rho = make_double2(bb[k], 0.0);
+    s.alpha = s.omega = make_double2(1.0, 0.0);
+    s.beta = make_double2(0.0, 0.0);
+    s.rr = bb[k];
+    s.target = delta * delta * bb[k];
+    s.active = (act ? act[k] : 1) && bb[k] > 0.0;
+    s.iters = 0;
+    st[k] = s;
+    flags[k] = s.active;
+}
+
+// per-CTA partials of sum conj(a) b (complex) and, if p_aa, sum |a|^2
+template <class S, int NT>
+__global__ void __launch_bounds__(NT) bcg_dot_kernel(const BCS *st, View<typename S::elem> a, View<typename S::elem> b,
+                                                     long long s_lo, long long n, double *p_re, double *p_im,
+                                                     double *p_aa) {
+    using R = typename S::R;
+    __shared__ double sh[3][NT / 32];
+    const int k = blockIdx.y;
+    const long long slot = (long long)k * gridDim.x + blockIdx.x;
+    if (!st[k].active) {
+        if (threadIdx.x == 0) {
+            p_re[slot] = 0;
+            p_im[slot] = 0;
+            if (p_aa) p_aa[slot] = 0;
+        }
+        return;
+    }
+    double re = 0, im = 0, aa = 0;
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
+    if (i < n) {
+        const long long sx = s_lo + i;
+        for (int c = 0; c < 12; ++c) {
+            const cpx<R> x = S::ldi(a.p, k * a.bs + S::idx(c, a.cs, sx - a.off));
+            const cpx<R> y = S::ldi(b.p, k * b.bs + S::idx(c, b.cs, sx - b.off));
+            re += (double)x.re * y.re + (double)x.im * y.im;
+            im += (double)x.re * y.im - (double)x.im * y.re;
+            aa += (double)x.re * x.re + (double)x.im * x.im;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+        aa += __shfl_xor_sync(0xffffffffu, aa, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = re;
+        sh[1][threadIdx.x >> 5] = im;
+        sh[2][threadIdx.x >> 5] = aa;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t0 = 0, t1 = 0, t2 = 0;
+        for (int w = 0; w < NT / 32; ++w) {
+            t0 += sh[0][w];
+            t1 += sh[1][w];
+            t2 += sh[2][w];
+        }
+        p_re[slot] = t0;
+        p_im[slot] = t1;
+        if (p_aa) p_aa[slot] = t2;
+    }
+}
+
+// fixed-order sum of m per-CTA partials of system k (one warp per array)
+template <int NT>
+__device__ double finish_sum(const double *p, int k, int m, double *sh) {
+    double v = 0;
+    for (int i = threadIdx.x; i < m; i += NT) v += p[(long long)k * m + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0;
+    for (int i = 0; i < NT / 32; ++i) t += sh[i];
+    return t;
+}
+
+// stage: 0 alpha = rho / <rh, v>; 1 omega = <t, s> / <t, t>;
+//        2 rho_new = <rh, r>, rr = |r|^2, beta, convergence
+template <int NT>
+__global__ void __launch_bounds__(NT) bcg_scalar_kernel(BCS *st, const double *p_re, const double *p_im,
+                                                        const double *p_aa, int m, int stage, int maxit, int *flags) {
+    __shared__ double sh[NT / 32];
+    const int k = blockIdx.x;
+    if (!st[k].active) return;
+    const double re = finish_sum<NT>(p_re, k, m, sh);
+    const double im = finish_sum<NT>(p_im, k, m, sh);
+    const double aa = p_aa ? finish_sum<NT>(p_aa, k, m, sh) : 0.0;
+    if (threadIdx.x != 0) return;
+    BCS s = st[k];
+    const double2 d = make_double2(re, im);
+    if (stage == 0) {
+        if (!(re * re + im * im > 0.0)) {
+            s.active = 0;  // breakdown: <rh, v> = 0
+        } else {
+            s.alpha = cdiv(s.rho, d);
+        }
+    } else if (stage == 1) {
+        s.omega = aa > 0.0 ? make_double2(re / aa, im / aa) : make_double2(0.0, 0.0);
+    } else {
+        // the partials are sum conj(r) rh = conj(<rh, r>) and |r|^2 of the
+        // new residual
+        const double2 dr = make_double2(re, -im);
+        s.iters += 1;
+        s.rr = aa;
+        const bool stalled = !(s.omega.x * s.omega.x + s.omega.y * s.omega.y > 0.0) ||
+                             !(re * re + im * im > 0.0);
+        if (!stalled) s.beta = cmul2(cdiv(dr, s.rho), cdiv(s.alpha, s.omega));
+        s.rho = dr;
+        if (aa <= s.target || s.iters >= maxit || stalled || !(aa == aa)) s.active = 0;
+    }
+    st[k] = s;
+    flags[k] = s.active;
+}
+
+// mode 0: s = r - alpha v
+// mode 1: x += alpha p + omega s, r = s - omega t
+// mode 2: p = r + beta (p - omega v)
+template <class S, int NT>
+__global__ void __launch_bounds__(NT) bcg_axpy_kernel(const BCS *st, int mode, View<typename S::elem> x,
+                                                      View<typename S::elem> p, View<typename S::elem> r,
+                                                      View<typename S::elem> s_, View<typename S::elem> v,
+                                                      View<typename S::elem> t, long long s_lo, long long n) {
+    using R = typename S::R;
+    const int k = blockIdx.y;
+    if (!st[k].active) return;
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
+    if (i >= n) return;
+    const long long sx = s_lo + i;
+    const BCS bs = st[k];
+    auto ld = [&](const View<typename S::elem> &w, int c) { return S::ldi(w.p, k * w.bs + S::idx(c, w.cs, sx - w.off)); };
+    auto st_ = [&](View<typename S::elem> &w, int c, cpx<R> val) { S::sti(w.p, k * w.bs + S::idx(c, w.cs, sx - w.off), val); };
+    const cpx<R> al = {(R)bs.alpha.x, (R)bs.alpha.y}, om = {(R)bs.omega.x, (R)bs.omega.y},
+                 be = {(R)bs.beta.x, (R)bs.beta.y};
+    for (int c = 0; c < 12; ++c) {
+        if (mode == 0) {
+            st_(s_, c, ld(r, c) - cmul(al, ld(v, c)));
+        } else if (mode == 1) {
+            const cpx<R> sv = ld(s_, c);
+            st_(x, c, ld(x, c) + cmul(al, ld(p, c)) + cmul(om, sv));
+            st_(r, c, sv - cmul(om, ld(t, c)));
+        } else {
+            st_(p, c, ld(r, c) + cmul(be, ld(p, c) - cmul(om, ld(v, c))));
+        }
+    }
+}
+
+__global__ void iters_bcg_kernel(const BCS *st, int *out, int n) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] += st[k].iters;
+}
+
+template <class SV>
+static void inner_bicgstab_full(psms_ctx *c, int n_sys, const void *Uin, long long U_bs, int prec, View<void> rhs,
+                                View<void> e, const int *act_in, double delta, int maxit, int *iters_acc) {
+    using E = typename SV::elem;
+    const Geom &g = c->g;
+    const long long V = g.V, Vh = g.Vh;
+    const double A = c->A, c4 = -1.0 / (4.0 * A);
+    const size_t esz = sizeof(E);
+    // odd halves: bhat (= rh), r, p, v, s, t ; even half: te
+    E *base = (E *)scratch(c, "fs_inner", esz * (size_t)(7 * 12 * Vh) * n_sys);
+    auto half = [&](int i, long long off) {
+        View<void> v;
+        v.p = base + (long long)i * 12 * Vh * n_sys;
+        v.cs = Vh;
+        v.off = off;
+        v.bs = 12 * Vh;
+        return v;
+    };
+    View<void> rh = half(0, Vh), r = half(1, Vh), pp = half(2, Vh), vv = half(3, Vh), ss = half(4, Vh),
+               tt = half(5, Vh), te = half(6, 0);
+    auto tv = [](View<void> v) { return View<E>{(E *)v.p, v.cs, v.off, v.bs}; };
+    BCS *st = (BCS *)scratch(c, "fs_bcs", sizeof(BCS) * n_sys);
+    int *flags = (int *)scratch(c, "fs_flags", sizeof(int) * n_sys);
+    double *bb = (double *)scratch(c, "fs_bb", sizeof(double) * n_sys);
+    HopCall h;
+    h.prec = prec;
+    h.U = Uin;
+    h.U_bs = U_bs;
+    h.n_sys = n_sys;
+    h.active = act_in;
+    const int nct = hop_ctas(c, [&] { HopCall x; x.p = 1; return x; }());
+    double *p_a = (double *)scratch(c, "fs_pa", sizeof(double) * (size_t)nct * n_sys);
+    // rh = bhat_o = rhs_o + H_o(rhs_e)/(2A)
+    h.p = 1;
+    h.in = rhs;
+    h.out = rh;
+    h.y = rhs;
+    h.a = 1.0;
+    h.b = 0.5 / A;
+    h.partial = p_a;
+    hop_launch(c, h);
+    reduce_partials(c, p_a, nct, n_sys, bb);
+    cudaMemsetAsync((char *)e.p, 0, esz * (size_t)12 * V * n_sys, c->stream);
+    cudaMemcpyAsync(r.p, rh.p, esz * (size_t)12 * Vh * n_sys, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(pp.p, rh.p, esz * (size_t)12 * Vh * n_sys, cudaMemcpyDeviceToDevice, c->stream);
+    bcg_init_kernel<<<(n_sys + 63) / 64, 64, 0, c->stream>>>(st, bb, n_sys, delta, act_in, flags);
+    PSMS_LAUNCH_CHECK("bcg_init");
+    const int NT = 256;
+    const long long n = Vh;
+    const int nb = (int)((n + NT - 1) / NT);
+    dim3 grid(nb, n_sys);
+    double *q_re = (double *)scratch(c, "fs_qre", sizeof(double) * (size_t)nb * n_sys);
+    double *q_im = (double *)scratch(c, "fs_qim", sizeof(double) * (size_t)nb * n_sys);
+    double *q_aa = (double *)scratch(c, "fs_qaa", sizeof(double) * (size_t)nb * n_sys);
+    // w = Dhat u = A u + c4 H_o(H_e u)
+    auto apply_dhat = [&](View<void> u, View<void> w) {
+        h.dag = 0;
+        h.p = 0;
+        h.in = u;
+        h.out = te;
+        h.y = View<void>();
+        h.a = 0;
+        h.b = 1.0;
+        h.partial = nullptr;
+        hop_launch(c, h);
+        h.p = 1;
+        h.in = te;
+        h.out = w;
+        h.y = u;
+        h.a = A;
+        h.b = c4;
+        hop_launch(c, h);
+    };
+    int it = 0;
+    int chunk = 8;
+    std::vector<int> hflags(n_sys);
+    h.active = flags;
+    while (it < maxit) {
+        for (int i = 0; i < chunk && it < maxit; ++i, ++it) {
+            apply_dhat(pp, vv);
+            bcg_dot_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, tv(rh), tv(vv), Vh, n, q_re, q_im, nullptr);
+            PSMS_LAUNCH_CHECK("bcg_dot");
+            bcg_scalar_kernel<256><<<n_sys, 256, 0, c->stream>>>(st, q_re, q_im, nullptr, nb, 0, maxit, flags);
+            PSMS_LAUNCH_CHECK("bcg_alpha");
+            bcg_axpy_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, 0, tv(e), tv(pp), tv(r), tv(ss), tv(vv), tv(tt),
+                                                                Vh, n);
+            PSMS_LAUNCH_CHECK("bcg_s");
+            apply_dhat(ss, tt);
+            bcg_dot_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, tv(tt), tv(ss), Vh, n, q_re, q_im, q_aa);
+            PSMS_LAUNCH_CHECK("bcg_dot");
+            bcg_scalar_kernel<256><<<n_sys, 256, 0, c->stream>>>(st, q_re, q_im, q_aa, nb, 1, maxit, flags);
+            PSMS_LAUNCH_CHECK("bcg_omega");
+            bcg_axpy_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, 1, tv(e), tv(pp), tv(r), tv(ss), tv(vv), tv(tt),
+                                                                Vh, n);
+            PSMS_LAUNCH_CHECK("bcg_update");
+            // <rh, r> and |r|^2 (the dot kernel's |a|^2 is of its first argument)
+            bcg_dot_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, tv(r), tv(rh), Vh, n, q_re, q_im, q_aa);
+            PSMS_LAUNCH_CHECK("bcg_dot");
+            bcg_scalar_kernel<256><<<n_sys, 256, 0, c->stream>>>(st, q_re, q_im, q_aa, nb, 3, maxit, flags);
+            PSMS_LAUNCH_CHECK("bcg_beta");
+            bcg_axpy_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, 2, tv(e), tv(pp), tv(r), tv(ss), tv(vv), tv(tt),
+                                                                Vh, n);
+            PSMS_LAUNCH_CHECK("bcg_p");
+        }
+        cuda_check(cudaMemcpyAsync(hflags.data(), flags, sizeof(int) * n_sys, cudaMemcpyDeviceToHost, c->stream),
+                   "bcg flags");
+        cuda_check(cudaStreamSynchronize(c->stream), "bcg sync");
+        bool any = false;
+        for (int k = 0; k < n_sys; ++k) any |= hflags[k] != 0;
+        if (!any) break;
+        chunk = std::min(chunk * 2, 64);
+    }
+    iters_bcg_kernel<<<(n_sys + 63) / 64, 64, 0, c->stream>>>(st, iters_acc, n_sys);
+    PSMS_LAUNCH_CHECK("iters_kernel");
+    // e_e = (rhs_e + H_e(e_o)/2)/A
+    h.active = act_in;
+    h.dag = 0;
+    h.p = 0;
+    h.in = e;
+    h.out = e;
+    h.y = rhs;
+    h.a = 1.0 / A;
+    h.b = 0.5 / A;
+    h.partial = nullptr;
+    hop_launch(c, h);
+}
+
 void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info) {
     const Geom &g = c->g;
     const long long V = g.V;
@@ -1024,7 +1338,8 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
             scale_convert_kernel<Store<double>, NT><<<grid, NT, 0, c->stream>>>(
                 View<double2>{(double2 *)rin_p, V, 0, 12 * V}, r2, rn, 1, act, 0, V);
             PSMS_LAUNCH_CHECK("scale_convert_kernel");
-            inner_cg_full<Store<double>>(c, n, q.U64, q.U64_bs, P64, rin, ein, act, delta, q.maxit, iters);
+            (c->full_solver ? inner_bicgstab_full<Store<double>> : inner_cg_full<Store<double>>)(
+                c, n, q.U64, q.U64_bs, P64, rin, ein, act, delta, q.maxit, iters);
             accumulate_kernel<Store<double>, NT><<<grid, NT, 0, c->stream>>>(
                 View<double2>{(double2 *)q.x.p, q.x.cs, q.x.off, q.x.bs}, View<double2>{(double2 *)ein_p, V, 0, 12 * V},
                 rn, act, 0, V);
@@ -1033,7 +1348,8 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
             scale_convert_kernel<Store<float>, NT><<<grid, NT, 0, c->stream>>>(
                 View<float2>{(float2 *)rin_p, V, 0, 12 * V}, r2, rn, 1, act, 0, V);
             PSMS_LAUNCH_CHECK("scale_convert_kernel");
-            inner_cg_full<Store<float>>(c, n, q.U32, q.U64_bs, P32, rin, ein, act, delta, q.maxit, iters);
+            (c->full_solver ? inner_bicgstab_full<Store<float>> : inner_cg_full<Store<float>>)(
+                c, n, q.U32, q.U64_bs, P32, rin, ein, act, delta, q.maxit, iters);
             accumulate_kernel<Store<float>, NT><<<grid, NT, 0, c->stream>>>(
                 View<double2>{(double2 *)q.x.p, q.x.cs, q.x.off, q.x.bs}, View<float2>{(float2 *)ein_p, V, 0, 12 * V},
                 rn, act, 0, V);
@@ -1042,7 +1358,8 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
             scale_convert_kernel<Store<__nv_bfloat16>, NT><<<grid, NT, 0, c->stream>>>(
                 View<__nv_bfloat162>{(__nv_bfloat162 *)rin_p, V, 0, 12 * V}, r2, rn, 1, act, 0, V);
             PSMS_LAUNCH_CHECK("scale_convert_kernel");
-            inner_cg_full<Store<__nv_bfloat16>>(c, n, q.U32, q.U64_bs, PB16, rin, ein, act, delta, q.maxit, iters);
+            (c->full_solver ? inner_bicgstab_full<Store<__nv_bfloat16>> : inner_cg_full<Store<__nv_bfloat16>>)(
+                c, n, q.U32, q.U64_bs, PB16, rin, ein, act, delta, q.maxit, iters);
             accumulate_kernel<Store<__nv_bfloat16>, NT><<<grid, NT, 0, c->stream>>>(
                 View<double2>{(double2 *)q.x.p, q.x.cs, q.x.off, q.x.bs},
                 View<__nv_bfloat162>{(__nv_bfloat162 *)ein_p, V, 0, 12 * V}, rn, act, 0, V);

@@ -42,7 +42,7 @@ def test_external_proposal_parity():
     for step in range(3):
         r = ps.psms_filter_step(ctx, 0, inner_prec=ps.PREC_F64, seed=SEED, step=step, proposal_field=1,
                                 translate=False, **prm)
-        U, rec = ofilter.filter_step(U, geom, ofilter.FilterParams(kappa=KAPPA, beta0=5.3, **prm), SEED, step,
+        U, rec = ofilter.filter_step(U, geom, ofilter.FilterParams(kappa=KAPPA, **prm), SEED, step,
                                      proposal=Up, translate=False)
         assert r["accept_global"] == rec["accept_global"]
         assert np.array_equal(r["accept_block"], rec["accept_block"])

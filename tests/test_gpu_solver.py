@@ -13,10 +13,12 @@ from tests.gpu_util import canonical, native, rel_err
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("solver", [ps.SOLVER_CGNR, ps.SOLVER_BICGSTAB])
 @pytest.mark.parametrize("inner", [ps.PREC_F64, ps.PREC_F32, ps.PREC_BF16])
-def test_full_solve_parity(inner):
+def test_full_solve_parity(inner, solver):
     dims, block, kappa = (4, 4, 4, 4), (2, 2, 2, 2), 0.15
     ctx = ps.psms_create(dims, block, kappa, 1)
+    ps.psms_full_solver(ctx, solver)
     ps.psms_gauge_init(ctx, 0, 0.3, 0x50534D53)
     U = gauge.generate_links(dims, 0.3, 0x50534D53)
     b = seeded.spinor(dims, 1)
@@ -31,11 +33,14 @@ def test_full_solve_parity(inner):
     assert rel_err(got, ref) < 1e-11
 
 
-def test_full_solve_16x4_config():
+@pytest.mark.parametrize("solver", [ps.SOLVER_CGNR, ps.SOLVER_BICGSTAB])
+def test_full_solve_16x4_config(solver):
     """16^4, kappa = 0.156, eps = 0.5 links: mixed FP32 inner iterations in FP64
-    defect correction to 1e-10 (true residual checked with the oracle's D)."""
+    defect correction to 1e-10 (true residual checked with the oracle's D),
+    with either inner Krylov method."""
     dims, block, kappa = (16, 16, 16, 16), (4, 4, 4, 4), 0.156
     ctx = ps.psms_create(dims, block, kappa, 1)
+    ps.psms_full_solver(ctx, solver)
     ps.psms_gauge_init(ctx, 0, 0.5, 0x50534D53 + 1)
     U = gauge.generate_links(dims, 0.5, 0x50534D53 + 1)
     b = seeded.spinor(dims, 2)
@@ -75,6 +80,23 @@ def test_block_solve_parity(dims, block, inner):
     mask = (geom.block_index == blocks[-1])[..., None, None]
     assert np.abs(g1 * ~mask).max() == 0.0
     assert rel_err(g1 * mask, ref * mask) < 1e-11
+
+
+def test_bicgstab_batched_global_estimates_match():
+    """The global level (batched whole-lattice solves of the Schur estimator)
+    gives the same estimates with either inner method (both to 1e-13)."""
+    dims, block, kappa = (8, 8, 8, 8), (4, 4, 4, 4), 0.156
+    ctx = ps.psms_create(dims, block, kappa, 2)
+    ps.psms_gauge_init(ctx, 0, 0.5, 9)
+    ps.psms_gauge_copy(ctx, 1, 0)
+    ps.psms_gauge_sweep(ctx, 1, ps.ACTIVE_BLOCKS, 1, 1, 5.3, 3, 0)
+    got = []
+    for solver in (ps.SOLVER_CGNR, ps.SOLVER_BICGSTAB):
+        ps.psms_full_solver(ctx, solver)
+        got.append(ps.psms_logdet_ratio(ctx, ps.LEVEL_GLOBAL, 0, 1, 4, ps.EST_INTERP, 5, 0, 1e-13, ps.PREC_F32))
+    assert np.abs(got[0] - got[1]).max() < 1e-8
+    with pytest.raises(ps.PsmsError):
+        ps.psms_full_solver(ctx, 7)
 
 
 def test_solver_reports_non_convergence():
