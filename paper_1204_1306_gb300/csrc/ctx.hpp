@@ -60,11 +60,12 @@ struct psms_ctx {
     unsigned long long *d_prof_sites = nullptr;         // per pending launch: active output sites
     int prof_cap = 0;
     long long prof_launches = 0;
-    // autotuned hop-kernel variant per (storage precision, both parities)
+    // autotuned hop-kernel variant per (storage precision, both parities,
+    // whole lattice or not)
     int hop_variant[3][2][2] = {{{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}};
     bool autotune = true;
-    int forced_hop_variant = -1;
-    int full_solver = 0;  // inner Krylov method of whole-lattice solves: 0 CGNR, 1 BiCGStab  // -1: autotuned; else the variant index (mod the variant count)
+    int forced_hop_variant = -1;  // -1: autotuned; else the variant index (mod the variant count)
+    int full_solver = 1;          // inner Krylov method of whole-lattice solves: 0 CGNR, 1 BiCGStab
     // autotuned block-solver variant per (precision, block size, batched)
     std::map<long long, int> block_variant;
     int forced_block_variant = -1;
