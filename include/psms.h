@@ -397,6 +397,10 @@ psms_status psms_relative_gauge_fix(psms_ctx *ctx, int field_old, int field_new,
  * PSMS_EINVAL for another kind. */
 enum { PSMS_SOLVER_CGNR = 0, PSMS_SOLVER_BICGSTAB = 1 };
 psms_status psms_full_solver(psms_ctx *ctx, int kind);
+/* Inner Krylov method of the Dirichlet block solves (default CGNR; the
+ * autotuner then chooses among that method's variants only, so every tuned
+ * choice gives identical results).  PSMS_EINVAL for another kind. */
+psms_status psms_block_krylov(psms_ctx *ctx, int kind);
 
 /* Force the Wilson-hop kernel variant (register cap and, for the whole
  * lattice, the branch-free specialisation; 8 variants for FP32 links in the
@@ -424,9 +428,12 @@ psms_status psms_checkpoint_load(psms_ctx *ctx, int field, const char *path, uin
  * (8,1),(8,4) for index 0..7, (1,1),(1,4) with one out-of-line copy of
  * the hop for 8, 9, and (1,1),(1,4),(4,4),(8,4) with the branch-free hop
  * (every direction computed, those leaving the block multiplied by zero) for
- * 10..13, (1,4) with the branch-free hop out of line for 14 (falling back
- * to 0 when the block is too small for the cluster); -1 restores the tuned
- * choice.  Clears the tuning cache.  PSMS_EINVAL outside -1..14. */
+ * 10..13, (1,4) with the branch-free hop out of line for 14, and with
+ * BiCGStab on Dhat instead of CGNR: (1,4) branch-free for 15, (1,4) out of
+ * line for 16, (8,4) branch-free for 17 (falling back to 0 when the block is
+ * too small for the cluster); -1 restores the tuned choice.  Clears the
+ * tuning cache.  PSMS_EINVAL outside -1..17.  Variants of one Krylov method
+ * give identical results; the two methods agree to the solve tolerance. */
 psms_status psms_autotune(psms_ctx *ctx, int enable, int block_variant);
 
 /* Number of CUDA kernels the library has launched in this process. */

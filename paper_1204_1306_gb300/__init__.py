@@ -23,7 +23,7 @@ __all__ = [
     "psms_block_plan_destroy", "BlockPlan", "psms_autotune", "psms_profile_read_block",
     "psms_domain_features_pair", "psms_checkpoint_save", "psms_checkpoint_load",
     "psms_relative_gauge_fix", "psms_profile_block_launches", "psms_hop_variant", "psms_full_solver",
-    "SOLVER_CGNR", "SOLVER_BICGSTAB",
+    "psms_block_krylov", "SOLVER_CGNR", "SOLVER_BICGSTAB",
     "PREC_F64", "PREC_F32", "PREC_BF16", "OP_FULL", "OP_BLOCKS", "ACTIVE_BLOCKS", "ACTIVE_ALL",
     "LEVEL_BLOCK", "LEVEL_GLOBAL", "EST_INTERP", "EST_INDEPENDENT",
 ]
@@ -136,6 +136,7 @@ _SIGS = {
     "psms_profile_block_launches": [_P, _I, _P, _P, _P],
     "psms_hop_variant": [_P, _I, _P],
     "psms_full_solver": [_P, _I],
+    "psms_block_krylov": [_P, _I],
     "psms_checkpoint_load": [_P, _I, ctypes.c_char_p, ctypes.POINTER(_U64), ctypes.POINTER(_U64)],
     "psms_profile_read_block": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), ctypes.POINTER(_D)],
     "psms_profile_enable": [_P, _I],
@@ -451,6 +452,11 @@ SOLVER_CGNR, SOLVER_BICGSTAB = 0, 1
 def psms_full_solver(ctx, kind):
     """Inner Krylov method of whole-lattice solves: SOLVER_CGNR or SOLVER_BICGSTAB."""
     ctx.check(ctx.lib.psms_full_solver(ctx.handle, int(kind)))
+
+
+def psms_block_krylov(ctx, kind):
+    """Inner Krylov method of block solves: SOLVER_CGNR or SOLVER_BICGSTAB."""
+    ctx.check(ctx.lib.psms_block_krylov(ctx.handle, int(kind)))
 
 
 def psms_hop_variant(ctx, variant):

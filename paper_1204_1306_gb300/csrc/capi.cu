@@ -834,6 +834,13 @@ psms_status psms_full_solver(psms_ctx *ctx, int kind) {
     PSMS_CATCH(ctx)
 }
 
+psms_status psms_block_krylov(psms_ctx *ctx, int kind) {
+    PSMS_TRY(ctx)
+    if (kind != PSMS_SOLVER_CGNR && kind != PSMS_SOLVER_BICGSTAB) fail(PSMS_EINVAL, "unknown solver");
+    ctx->block_krylov = kind;
+    PSMS_CATCH(ctx)
+}
+
 psms_status psms_hop_variant(psms_ctx *ctx, int variant, int *n_variants) {
     PSMS_TRY(ctx)
     if (variant < -1 || variant > 7) fail(PSMS_EINVAL, "hop variant must be -1 or 0..7");
@@ -939,7 +946,7 @@ psms_status psms_profile_read_block(psms_ctx *ctx, long long *launches, double *
 
 psms_status psms_autotune(psms_ctx *ctx, int enable, int block_variant) {
     PSMS_TRY(ctx)
-    if (block_variant < -1 || block_variant > 14) fail(PSMS_EINVAL, "block_variant must be -1 or 0..14");
+    if (block_variant < -1 || block_variant > 17) fail(PSMS_EINVAL, "block_variant must be -1 or 0..17");
     ctx->autotune = enable != 0;
     ctx->forced_block_variant = block_variant;
     ctx->block_variant.clear();

@@ -342,6 +342,118 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
         double bb = hop_call<HV, SV, SL, SV>(g, bi, r, 1, 0, v.rhs, V, 0, v.bhat, Vh, Vh, v.rhs, V, 0, 1.0,
                                           0.5 / A, Uin, jlo, jhi);
         bb = cl_sum<NT, CL>(bb, sh);
+        int it = 0;
+        if constexpr ((HV >> 2) & 1) {
+            // BiCGStab on Dhat (hop form bit 2): rh = bhat, r = rho, p = pp,
+            // v = q, s = sv, t = res; complex scalars from cluster-wide sums
+            // that every thread receives alike
+            for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
+                const long long so = blo[1] + j;
+                for (int q = 0; q < 12; ++q) {
+                    SV::st(v.e, q, V, so, mk<R>(0, 0));
+                    const cpx<R> bv = SV::ld(v.bhat, q, Vh, so - Vh);
+                    SV::st(v.rho, q, Vh, so - Vh, bv);
+                    SV::st(v.pp, q, Vh, so - Vh, bv);
+                }
+            }
+            bar<CL>();
+            double rho_re = bb, rho_im = 0, al_re = 1, al_im = 0, om_re = 1, om_im = 0;
+            const double target = a.delta * a.delta * bb;
+            while (total_it + it < a.maxit) {
+                // v = Dhat p
+                hop_call<HV, SV, SL, SV>(g, bi, r, 0, 0, v.pp, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0,
+                                         1.0, Uin, jlo, jhi);
+                bar<CL>();
+                hop_call<HV, SV, SL, SV>(g, bi, r, 1, 0, v.t, Vh, 0, v.q, Vh, Vh, v.pp, Vh, Vh, A, c4, Uin, jlo,
+                                         jhi);
+                // <rh, v>
+                double d_re = 0, d_im = 0;
+                for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
+                    const long long sh_ = blo[1] + j - Vh;
+                    for (int q = 0; q < 12; ++q) {
+                        const cpx<R> x1 = SV::ld(v.bhat, q, Vh, sh_), y1 = SV::ld(v.q, q, Vh, sh_);
+                        d_re += (double)x1.re * y1.re + (double)x1.im * y1.im;
+                        d_im += (double)x1.re * y1.im - (double)x1.im * y1.re;
+                    }
+                }
+                d_re = cl_sum<NT, CL>(d_re, sh);
+                d_im = cl_sum<NT, CL>(d_im, sh);
+                const double dd = d_re * d_re + d_im * d_im;
+                if (!(dd > 0.0)) break;  // breakdown: the defect correction restarts
+                al_re = (rho_re * d_re + rho_im * d_im) / dd;
+                al_im = (rho_im * d_re - rho_re * d_im) / dd;
+                const cpx<R> alc = mk<R>((R)al_re, (R)al_im);
+                // s = r - alpha v
+                for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
+                    const long long sh_ = blo[1] + j - Vh;
+                    for (int q = 0; q < 12; ++q)
+                        SV::st(v.sv, q, Vh, sh_, SV::ld(v.rho, q, Vh, sh_) - cmul(alc, SV::ld(v.q, q, Vh, sh_)));
+                }
+                bar<CL>();
+                // t = Dhat s
+                hop_call<HV, SV, SL, SV>(g, bi, r, 0, 0, v.sv, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0,
+                                         1.0, Uin, jlo, jhi);
+                bar<CL>();
+                hop_call<HV, SV, SL, SV>(g, bi, r, 1, 0, v.t, Vh, 0, v.res, Vh, Vh, v.sv, Vh, Vh, A, c4, Uin, jlo,
+                                         jhi);
+                // omega = <t, s> / <t, t>
+                double ts_re = 0, ts_im = 0, tt = 0;
+                for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
+                    const long long sh_ = blo[1] + j - Vh;
+                    for (int q = 0; q < 12; ++q) {
+                        const cpx<R> tv = SV::ld(v.res, q, Vh, sh_), sv = SV::ld(v.sv, q, Vh, sh_);
+                        ts_re += (double)tv.re * sv.re + (double)tv.im * sv.im;
+                        ts_im += (double)tv.re * sv.im - (double)tv.im * sv.re;
+                        tt += (double)tv.re * tv.re + (double)tv.im * tv.im;
+                    }
+                }
+                ts_re = cl_sum<NT, CL>(ts_re, sh);
+                ts_im = cl_sum<NT, CL>(ts_im, sh);
+                tt = cl_sum<NT, CL>(tt, sh);
+                om_re = tt > 0.0 ? ts_re / tt : 0.0;
+                om_im = tt > 0.0 ? ts_im / tt : 0.0;
+                const cpx<R> omc = mk<R>((R)om_re, (R)om_im);
+                // e += alpha p + omega s ; r = s - omega t ; <rh, r>, |r|^2
+                double n_re = 0, n_im = 0, rr2 = 0;
+                for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
+                    const long long so = blo[1] + j;
+                    const long long sh_ = so - Vh;
+                    for (int q = 0; q < 12; ++q) {
+                        const cpx<R> sv = SV::ld(v.sv, q, Vh, sh_);
+                        SV::st(v.e, q, V, so,
+                               SV::ld(v.e, q, V, so) + cmul(alc, SV::ld(v.pp, q, Vh, sh_)) + cmul(omc, sv));
+                        const cpx<R> rv = sv - cmul(omc, SV::ld(v.res, q, Vh, sh_));
+                        SV::st(v.rho, q, Vh, sh_, rv);
+                        const cpx<R> hv = SV::ld(v.bhat, q, Vh, sh_);
+                        n_re += (double)hv.re * rv.re + (double)hv.im * rv.im;
+                        n_im += (double)hv.re * rv.im - (double)hv.im * rv.re;
+                        rr2 += (double)rv.re * rv.re + (double)rv.im * rv.im;
+                    }
+                }
+                n_re = cl_sum<NT, CL>(n_re, sh);
+                n_im = cl_sum<NT, CL>(n_im, sh);
+                rr2 = cl_sum<NT, CL>(rr2, sh);
+                ++it;
+                if (rr2 <= target) break;
+                const double oo = om_re * om_re + om_im * om_im, rr_ = rho_re * rho_re + rho_im * rho_im;
+                if (!(oo > 0.0) || !(n_re * n_re + n_im * n_im > 0.0) || !(rr_ > 0.0)) break;
+                // beta = (rho_new / rho)(alpha / omega)
+                const double q1_re = (n_re * rho_re + n_im * rho_im) / rr_, q1_im = (n_im * rho_re - n_re * rho_im) / rr_;
+                const double q2_re = (al_re * om_re + al_im * om_im) / oo, q2_im = (al_im * om_re - al_re * om_im) / oo;
+                const cpx<R> bec = mk<R>((R)(q1_re * q2_re - q1_im * q2_im), (R)(q1_re * q2_im + q1_im * q2_re));
+                rho_re = n_re;
+                rho_im = n_im;
+                // p = r + beta (p - omega v)
+                for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
+                    const long long sh_ = blo[1] + j - Vh;
+                    for (int q = 0; q < 12; ++q) {
+                        const cpx<R> pv = SV::ld(v.pp, q, Vh, sh_) - cmul(omc, SV::ld(v.q, q, Vh, sh_));
+                        SV::st(v.pp, q, Vh, sh_, SV::ld(v.rho, q, Vh, sh_) + cmul(bec, pv));
+                    }
+                }
+                bar<CL>();
+            }
+        } else {
         // e_o = 0, rho = bhat, res = Dhat^dag rho, p = res
         for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
             const long long s = blo[1] + j;
@@ -361,7 +473,6 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
         }
         bar<CL>();
         const double target = a.delta * a.delta * bb;
-        int it = 0;
         while (total_it + it < a.maxit) {
             // q = Dhat p
             hop_call<HV, SV, SL, SV>(g, bi, r, 0, 0, v.pp, Vh, Vh, v.t, Vh, 0, (const E *)nullptr, 0, 0, 0.0, 1.0, Uin, jlo, jhi);
@@ -415,7 +526,9 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
             }
             bar<CL>();
         }
+        }
         total_it += it;
+        bar<CL>();
         // e_e = (rhs_e + H_e(e_o)/2) / A
         hop_call<HV, SV, SL, SV>(g, bi, r, 0, 0, v.e, V, 0, v.e, V, 0, v.rhs, V, 0, 1.0 / A, 0.5 / A, Uin, jlo, jhi);
         bar<CL>();
@@ -501,6 +614,9 @@ static void launch_block_variant(psms_ctx *c, const BlockSolveArgs &a, int n_ran
         case 244: launch_block_cl<SV, SL, 4, 4, 2>(c, a, n_ranks, n_sys); break;
         case 284: launch_block_cl<SV, SL, 8, 4, 2>(c, a, n_ranks, n_sys); break;
         case 314: launch_block_cl<SV, SL, 1, 4, 3>(c, a, n_ranks, n_sys); break;
+        case 614: launch_block_cl<SV, SL, 1, 4, 6>(c, a, n_ranks, n_sys); break;
+        case 514: launch_block_cl<SV, SL, 1, 4, 5>(c, a, n_ranks, n_sys); break;
+        case 684: launch_block_cl<SV, SL, 8, 4, 6>(c, a, n_ranks, n_sys); break;
         case 11: launch_block_cl<SV, SL, 1, 1>(c, a, n_ranks, n_sys); break;
         case 14: launch_block_cl<SV, SL, 1, 4>(c, a, n_ranks, n_sys); break;
         case 21: launch_block_cl<SV, SL, 2, 1>(c, a, n_ranks, n_sys); break;
@@ -547,7 +663,8 @@ void block_solve(psms_ctx *c, const BlockSolveReq &q) {
     // Variants (cluster size CL, min CTAs per SM, hop form): one block solved
     // by CL CTAs of a thread-block cluster; hop form 1 calls one out-of-line
     // copy of the hop instead of inlining it at every call site, form 2 is
-    // the branch-free hop, form 3 both.  The autotuner times every admissible
+    // the branch-free hop, form 3 both; bit 2 (forms 5, 6) runs BiCGStab on
+    // Dhat instead of CGNR inside the same FP64 defect correction.  The autotuner times every admissible
     // variant once on the first solve of each (precision, block size,
     // batched or not) and keeps the fastest; a solve is idempotent (x is set
     // from b), so the tuning runs leave the result unchanged.
@@ -556,8 +673,8 @@ void block_solve(psms_ctx *c, const BlockSolveReq &q) {
     };
     static const Var vars[] = {{1, 1, 0}, {1, 4, 0}, {2, 1, 0}, {2, 4, 0}, {4, 1, 0}, {4, 4, 0}, {8, 1, 0},
                                {8, 4, 0}, {1, 1, 1}, {1, 4, 1}, {1, 1, 2}, {1, 4, 2}, {4, 4, 2}, {8, 4, 2},
-                               {1, 4, 3}};
-    const int nvar = 15;
+                               {1, 4, 3}, {1, 4, 6}, {1, 4, 5}, {8, 4, 6}};
+    const int nvar = 18;
     auto admissible = [&](int v) { return vars[v].cl == 1 || g.Vbh / vars[v].cl >= 128; };
     auto launch = [&](int v) {
         if (in64)
@@ -567,7 +684,11 @@ void block_solve(psms_ctx *c, const BlockSolveReq &q) {
             launch_block_variant<Store<float>, Store<float>>(c, a, q.n_ranks, q.n_sys, vars[v].cl, vars[v].minb,
                                                              vars[v].hv);
     };
-    const long long key = ((long long)q.inner_prec << 40) | ((long long)g.Vbh << 8) | (q.n_sys > 1 ? 1 : 0);
+    // the autotuner chooses among the variants of the context's Krylov
+    // method only, so that every tuned choice gives the same bits
+    auto method = [&](int v) { return (vars[v].hv >> 2) & 1; };
+    const long long key = ((long long)q.inner_prec << 40) | ((long long)c->block_krylov << 36) |
+                          ((long long)g.Vbh << 8) | (q.n_sys > 1 ? 1 : 0);
     auto it = c->block_variant.find(key);
     int choice = it == c->block_variant.end() ? -1 : it->second;
     if (c->forced_block_variant >= 0) choice = admissible(c->forced_block_variant) ? c->forced_block_variant : 0;
@@ -577,7 +698,7 @@ void block_solve(psms_ctx *c, const BlockSolveReq &q) {
         cuda_check(cudaEventCreate(&e1), "tune event");
         float best = 1e30f;
         for (int v = 0; v < nvar; ++v) {
-            if (!admissible(v)) continue;
+            if (!admissible(v) || method(v) != c->block_krylov) continue;
             cuda_check(cudaEventRecord(e0, c->stream), "tune record");
             launch(v);
             cuda_check(cudaEventRecord(e1, c->stream), "tune record");
@@ -592,7 +713,7 @@ void block_solve(psms_ctx *c, const BlockSolveReq &q) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }
-    if (choice < 0) choice = 0;
+    if (choice < 0) choice = c->block_krylov ? 15 : 0;
     if (c->forced_block_variant < 0) c->block_variant[key] = choice;
     const int slot = c->prof ? prof_block_begin(c) : -1;
     launch(choice);
@@ -1302,9 +1423,16 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
                    "zero x");
     set_int_kernel<<<(n + 63) / 64, 64, 0, c->stream>>>(iters, 0, n);
     PSMS_LAUNCH_CHECK("set_int_kernel");
-    const double delta = in64 ? std::max(0.1 * q.tol, 1e-15) : (q.inner_prec == P32 ? 2e-6 : 5e-3);
+    // BiCGStab's inner target is looser (its FP32 residual can stall near
+    // 1e-6); if an outer step fails to halve some system's true residual the
+    // remaining outer steps of this solve use CGNR
+    bool bicg = c->full_solver == 1;
+    auto delta_of = [&](bool b) {
+        return in64 ? std::max(0.1 * q.tol, 1e-15) : (q.inner_prec == P32 ? (b ? 1e-4 : 2e-6) : 5e-3);
+    };
     const int max_outer = in64 ? 6 : 30;
     std::vector<int> hact(n);
+    std::vector<double> hrn(n), hrn_prev(n, 0.0);
     int outer = 0;
     const int NT = 256;
     dim3 grid((unsigned)((V + NT - 1) / NT), n);
@@ -1328,17 +1456,23 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
         residual_flags_kernel<<<(n + 63) / 64, 64, 0, c->stream>>>(rn, bn, q.tol, act, rel, n);
         PSMS_LAUNCH_CHECK("residual_flags_kernel");
         cuda_check(cudaMemcpyAsync(hact.data(), act, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream), "act");
+        cuda_check(cudaMemcpyAsync(hrn.data(), rn, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "rn");
         cuda_check(cudaStreamSynchronize(c->stream), "solve sync");
         bool any = false;
         for (int k = 0; k < n; ++k) any |= hact[k] != 0;
         if (!any || outer >= max_outer) break;
+        if (bicg && outer > 0)
+            for (int k = 0; k < n; ++k)
+                if (hact[k] && !(hrn[k] <= 0.25 * hrn_prev[k])) bicg = false;
+        hrn_prev = hrn;
+        const double delta = delta_of(bicg);
         // inner rhs = r / |r|
         View<double2> r2{r64, V, 0, 12 * V};
         if (in64) {
             scale_convert_kernel<Store<double>, NT><<<grid, NT, 0, c->stream>>>(
                 View<double2>{(double2 *)rin_p, V, 0, 12 * V}, r2, rn, 1, act, 0, V);
             PSMS_LAUNCH_CHECK("scale_convert_kernel");
-            (c->full_solver ? inner_bicgstab_full<Store<double>> : inner_cg_full<Store<double>>)(
+            (bicg ? inner_bicgstab_full<Store<double>> : inner_cg_full<Store<double>>)(
                 c, n, q.U64, q.U64_bs, P64, rin, ein, act, delta, q.maxit, iters);
             accumulate_kernel<Store<double>, NT><<<grid, NT, 0, c->stream>>>(
                 View<double2>{(double2 *)q.x.p, q.x.cs, q.x.off, q.x.bs}, View<double2>{(double2 *)ein_p, V, 0, 12 * V},
@@ -1348,7 +1482,7 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
             scale_convert_kernel<Store<float>, NT><<<grid, NT, 0, c->stream>>>(
                 View<float2>{(float2 *)rin_p, V, 0, 12 * V}, r2, rn, 1, act, 0, V);
             PSMS_LAUNCH_CHECK("scale_convert_kernel");
-            (c->full_solver ? inner_bicgstab_full<Store<float>> : inner_cg_full<Store<float>>)(
+            (bicg ? inner_bicgstab_full<Store<float>> : inner_cg_full<Store<float>>)(
                 c, n, q.U32, q.U64_bs, P32, rin, ein, act, delta, q.maxit, iters);
             accumulate_kernel<Store<float>, NT><<<grid, NT, 0, c->stream>>>(
                 View<double2>{(double2 *)q.x.p, q.x.cs, q.x.off, q.x.bs}, View<float2>{(float2 *)ein_p, V, 0, 12 * V},
@@ -1358,7 +1492,7 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
             scale_convert_kernel<Store<__nv_bfloat16>, NT><<<grid, NT, 0, c->stream>>>(
                 View<__nv_bfloat162>{(__nv_bfloat162 *)rin_p, V, 0, 12 * V}, r2, rn, 1, act, 0, V);
             PSMS_LAUNCH_CHECK("scale_convert_kernel");
-            (c->full_solver ? inner_bicgstab_full<Store<__nv_bfloat16>> : inner_cg_full<Store<__nv_bfloat16>>)(
+            (bicg ? inner_bicgstab_full<Store<__nv_bfloat16>> : inner_cg_full<Store<__nv_bfloat16>>)(
                 c, n, q.U32, q.U64_bs, PB16, rin, ein, act, delta, q.maxit, iters);
             accumulate_kernel<Store<__nv_bfloat16>, NT><<<grid, NT, 0, c->stream>>>(
                 View<double2>{(double2 *)q.x.p, q.x.cs, q.x.off, q.x.bs},

@@ -52,13 +52,15 @@ def test_full_solve_16x4_config(solver):
     assert info["outer_iters"] >= 1
 
 
+@pytest.mark.parametrize("krylov", [ps.SOLVER_CGNR, ps.SOLVER_BICGSTAB])
 @pytest.mark.parametrize("inner", [ps.PREC_F64, ps.PREC_F32])
 @pytest.mark.parametrize("dims,block", [((4, 4, 4, 4), (2, 2, 2, 2)), ((8, 8, 8, 8), (4, 4, 4, 4)),
                                         ((8, 8, 8, 8), (8, 8, 8, 4))])
-def test_block_solve_parity(dims, block, inner):
+def test_block_solve_parity(dims, block, inner, krylov):
     kappa = 0.156
     geom = lattice.Geometry(dims, block)
     ctx = ps.psms_create(dims, block, kappa, 1)
+    ps.psms_block_krylov(ctx, krylov)
     ps.psms_gauge_init(ctx, 0, 0.5, 5)
     U = gauge.generate_links(dims, 0.5, 5)
     b = seeded.spinor(dims, 6)
@@ -113,7 +115,7 @@ def test_solver_reports_non_convergence():
     assert e.value.status == 4
 
 
-@pytest.mark.parametrize("variant", range(15))
+@pytest.mark.parametrize("variant", range(18))
 def test_block_solver_cluster_variants(variant):
     """Every (cluster size, register cap) variant of the block solver gives the
     oracle's solution (8^4 blocks: one block is shared by up to 8 CTAs of a
