@@ -747,11 +747,12 @@ def reference_arm(args):
 
 # (full-lattice-equivalent Krylov iterations per step, accepted updates per
 # step) of our arm's hierarchy on each workload, measured on GB300 by this
-# bench: 16^4 (learned + mixed + gauge-fixed, 10 timed steps): 5110
-# iterations, 4 accepted updates in 10 steps; 32^3x64 (8^4 domains): 284
-# iterations, no block accepted.  The 4^4 entry only serves the
-# multi-process smoke test of this arm (not a measured workload).
-STEP_MODEL = {"16^4": (5110, 0.4), "32^3x64": (284, 0.0), "4^4": (600, 0.3)}
+# bench: 16^4 (learned + mixed + gauge-fixed, BiCGStab whole-lattice
+# solves, 10 timed steps): 3834 iterations, 4 accepted updates in 10 steps;
+# 32^3x64 (8^4 domains): 284 iterations, no block accepted.  The 4^4 entry
+# only serves the multi-process smoke test of this arm (not a measured
+# workload).
+STEP_MODEL = {"16^4": (3834, 0.4), "32^3x64": (284, 0.0), "4^4": (600, 0.3)}
 
 
 def main():
