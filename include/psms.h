@@ -390,6 +390,11 @@ psms_status psms_relative_gauge_fix(psms_ctx *ctx, int field_old, int field_new,
                                     const psms_relgf_params *prm, int *steps, double *alpha, double *theta,
                                     int *swapped, void *g_dev);
 
+/* ---- implementation controls -------------------------------------------------
+ * The calls below choose how the library computes, not what: the paper has
+ * no counterpart for them (it does not fix the Krylov solver), and every
+ * choice reaches the same tolerances. */
+
 /* Inner Krylov method of the whole-lattice solves (psms_solve with
  * PSMS_OP_FULL and the global level): BiCGStab on Dhat (default; 16 % faster
  * on the 16^4 global level) or even-odd CGNR on Dhat^dag Dhat; both run
@@ -420,10 +425,10 @@ psms_status psms_hop_variant(psms_ctx *ctx, int variant, int *n_variants);
 psms_status psms_checkpoint_save(psms_ctx *ctx, int field, const char *path, uint64_t step, uint64_t seed);
 psms_status psms_checkpoint_load(psms_ctx *ctx, int field, const char *path, uint64_t *step, uint64_t *seed);
 
-/* Autotuning of launch variants (on by default).  The hop kernel's register
- * cap and the block solver's (cluster size, register cap) are timed on
- * their first use per shape and the fastest kept; every variant computes
- * the same result.  block_variant >= 0 forces block-solver variant
+/* Autotuning of launch variants (on by default; an implementation control).
+ * The hop kernel's register cap and branch-free specialisation and the
+ * block solver's (cluster size, register cap, hop form) are timed on their
+ * first use per shape and the fastest kept.  block_variant >= 0 forces block-solver variant
  * (cluster size, min CTAs per SM) = (1,1),(1,4),(2,1),(2,4),(4,1),(4,4),
  * (8,1),(8,4) for index 0..7, (1,1),(1,4) with one out-of-line copy of
  * the hop for 8, 9, and (1,1),(1,4),(4,4),(8,4) with the branch-free hop
