@@ -36,3 +36,16 @@ def test_binding_fails_loudly_without_library(tmp_path):
         ps._lib = None
         ps.load_library(str(tmp_path / "nope.so"))
     ps._lib = None
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No fallback: without the compiled library the binding raises."""
+    import pytest
+
+    import paper_1204_1306_gb300 as ps
+    cached, ps._lib = ps._lib, None
+    try:
+        with pytest.raises(RuntimeError):
+            ps.load_library(str(tmp_path / "libpsms.so"))
+    finally:
+        ps._lib = cached
