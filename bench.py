@@ -397,24 +397,18 @@ def learned_only(args):
     print(json.dumps(out), flush=True)
 
 
-def batch_only(args):
+def measure_batch(ps, torch, steps=3, warmup=3):
     """All 4^4 Dirichlet blocks x 16 noise vectors of three uneven
     lattices (8^4, 12^4, 16^3 x 32; kappa 0.155, eps 0.5) in one persistent
     graph-captured launch, FP32 inner / FP64 refinement to 1e-10, autotuned
-    schedule.  Reports the batch time, the mean time a CTA spends per system,
+    schedule.  Returns the batch time, the mean time a CTA spends per system,
     and the aggregate algorithmic GB/s (4416 B per half-block site per block
     CG iteration, FP32)."""
-    import torch
-
-    import paper_1204_1306_gb300 as ps
-    from paper_1204_1306_gb300 import build as _build
-
-    _build.build()
-    torch.cuda.set_device(0)
     n_rhs = 16
-    probs = []
+    probs, ctxs = [], []
     for i, dims in enumerate(((8, 8, 8, 8), (12, 12, 12, 12), (32, 16, 16, 16))):
         ctx = ps.psms_create(dims, (4, 4, 4, 4), 0.155, 1)
+        ps.psms_set_stream(ctx, torch.cuda.current_stream())
         ps.psms_gauge_init(ctx, 0, 0.5, SEED + 2 + i)
         nb = ps.psms_spinor_bytes(ctx, ps.PREC_F64)
         b = torch.empty(n_rhs * nb, dtype=torch.uint8, device="cuda")
@@ -422,28 +416,72 @@ def batch_only(args):
             canon = torch.randn(ctx.V * 24, dtype=torch.float64, device="cuda")
             ps.psms_spinor_import(ctx, canon, b[k * nb:(k + 1) * nb], ps.PREC_F64)
         probs.append((ctx, 0, n_rhs, b, torch.zeros_like(b)))
+        ctxs.append(ctx)
     torch.cuda.synchronize()
     plan = ps.psms_block_plan_create(probs, 1e-10, 20000, ps.PREC_F32)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plan.run()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    infos = [plan.run(stream) for _ in range(args.steps)]
+    infos = [plan.run(stream) for _ in range(steps)]
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     sched = plan.schedule()
     items = infos[0]["n_systems"]
     iters = infos[0]["inner_iters"]
     gbs = iters * 128 * 4416.0 / (ms * 1e-3) / 1e9
     peak, kind = peaks()
-    print(json.dumps({"workload": "8^4 + 12^4 + 16^3x32, 4^4 blocks x 16 noises", "systems": items,
-                      "batch_ms": round(ms, 3), "cta_ms_per_system": round(ms * sched["ctas"] / items, 4),
-                      "block_cg_iterations": iters, "algorithmic_GB/s": round(gbs, 1), "frac": round(gbs / peak, 4),
-                      "peak_gbs": peak, "peak_kind": kind, "schedule": sched,
-                      "true_residual": max(i["true_residual"] for i in infos)}), flush=True)
+    out = {"workload": "8^4 + 12^4 + 16^3x32, 4^4 blocks x 16 noises", "systems": items,
+           "batch_ms": round(ms, 3), "per_solve_latency_ms": round(ms * sched["ctas"] / items, 4),
+           "block_cg_iterations": iters, "algorithmic_GB/s": round(gbs, 1), "frac": round(gbs / peak, 4),
+           "peak_gbs": peak, "peak_kind": kind, "schedule": sched,
+           "true_residual": max(i["true_residual"] for i in infos)}
+    plan.close()
+    for c in ctxs:
+        c.close()
+    return out
+
+
+def batch_only(args):
+    """The batched multi-lattice block solves alone (see measure_batch)."""
+    import torch
+
+    import paper_1204_1306_gb300 as ps
+    from paper_1204_1306_gb300 import build as _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    print(json.dumps(measure_batch(ps, torch, steps=args.steps, warmup=args.warmup)), flush=True)
+
+
+def measure_estimators(ps, torch, wl, seed, n=12, reps=3):
+    """Det-ratio estimates per second on the workload lattice: the block
+    level (all blocks x n interpolation steps) and the global level (n
+    steps) between the gauge-fixed endpoints of one domain-sweep proposal,
+    FP32 inner iterations to the workload tolerance, CUDA events."""
+    ctx = _new_chain(ps, torch, wl, seed)
+    ps.psms_gauge_copy(ctx, 1, 0)
+    ps.psms_gauge_sweep(ctx, 1, ps.ACTIVE_BLOCKS, wl["n_iter"], wl["n_or"], wl["beta"], seed, 9 << 20)
+    ps.psms_relative_gauge_fix(ctx, 0, 1, 2, 3, prec=ps.PREC_F32)
+    nb = ps.psms_geometry_info(ctx)[0]
+    stream = torch.cuda.current_stream()
+    out = {"n": n}
+    for name, level, units in (("block", ps.LEVEL_BLOCK, nb * n), ("global", ps.LEVEL_GLOBAL, n)):
+        ps.psms_logdet_ratio(ctx, level, 2, 3, n, ps.EST_INTERP, seed, 0, wl["tol"], ps.PREC_F32)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for r in range(reps):
+            ps.psms_logdet_ratio(ctx, level, 2, 3, n, ps.EST_INTERP, seed, r + 1, wl["tol"], ps.PREC_F32)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s_per = e0.elapsed_time(e1) / reps * 1e-3
+        out[name] = {"estimates": units, "s": round(s_per, 4), "estimates_per_s": round(units / s_per, 1)}
+    ctx.close()
+    return out
 
 
 ARMS = (
@@ -632,6 +670,8 @@ def our_arm(args):
         arms["speedup_learned_mixed_vs_plain_fp64_s_per_step"] = (arms["plain_fp64"]["s_per_step"] /
                                                                   arms["learned_mixed"]["s_per_step"])
     large = None if args.no_large else large_workload(ps, torch)
+    estimators = None if args.no_compare else measure_estimators(ps, torch, wl, seed)
+    batched = None if args.no_compare else measure_batch(ps, torch)
     full_iters = sum(r["solver_iters"] for r in recs) / max(len(recs), 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -657,6 +697,8 @@ def our_arm(args):
         "gpu_launches": n_launch,
         "wall_s_timed": wall,
         "large_workload_32^3x64": large,
+        "det_ratio_estimates": estimators,
+        "batched_block_solves": batched,
     }
     line["clocks"] = clk.summary()
     if not args.no_cpu_baseline:

@@ -1146,17 +1146,23 @@ __global__ void __launch_bounds__(NT) bcg_dot_kernel(const BCS *st, View<typenam
         }
         return;
     }
+    // a thread's 12 components are summed in the inner precision (GB300's
+    // FP64 rate is 1/64 of FP32), the sums over threads and CTAs in FP64
     double re = 0, im = 0, aa = 0;
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
     if (i < n) {
         const long long sx = s_lo + i;
+        R tre = 0, tim = 0, taa = 0;
         for (int c = 0; c < 12; ++c) {
             const cpx<R> x = S::ldi(a.p, k * a.bs + S::idx(c, a.cs, sx - a.off));
             const cpx<R> y = S::ldi(b.p, k * b.bs + S::idx(c, b.cs, sx - b.off));
-            re += (double)x.re * y.re + (double)x.im * y.im;
-            im += (double)x.re * y.im - (double)x.im * y.re;
-            aa += (double)x.re * x.re + (double)x.im * x.im;
+            tre += x.re * y.re + x.im * y.im;
+            tim += x.re * y.im - x.im * y.re;
+            taa += x.re * x.re + x.im * x.im;
         }
+        re = (double)tre;
+        im = (double)tim;
+        aa = (double)taa;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
