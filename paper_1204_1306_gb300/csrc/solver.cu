@@ -162,10 +162,13 @@ __device__ __forceinline__ double block_hop(const Geom &g, const BlockInfo &bi, 
                 for (int c = 0; c < 3; ++c) o.c[q][c] = cb * acc.c[q][c];
         }
         store_spinor<S>(out, out_cs, s - out_off, o);
+        // a site's 12 components summed in the inner precision, sites in FP64
+        R t = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) nrm += (double)norm2(o.c[q][c]);
+            for (int c = 0; c < 3; ++c) t += norm2(o.c[q][c]);
+        nrm += (double)t;
     }
     return nrm;
 }
@@ -484,6 +487,7 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
             for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
                 const long long so = blo[1] + j;
                 const long long sh_ = so - Vh;
+                R tsum = 0;
                 for (int q = 0; q < 12; ++q) {
                     cpx<R> e = SV::ld(v.e, q, V, so);
                     cpx<R> pv = SV::ld(v.pp, q, Vh, sh_);
@@ -493,8 +497,9 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
                     ro = ro - alpha * qv;
                     SV::st(v.e, q, V, so, e);
                     SV::st(v.rho, q, Vh, sh_, ro);
-                    rhorho += (double)norm2(ro);
+                    tsum += norm2(ro);
                 }
+                rhorho += (double)tsum;
             }
             rhorho = cl_sum<NT, CL>(rhorho, sh);
             ++it;
@@ -507,12 +512,14 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
             double rr_new = 0;
             for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
                 const long long sh_ = blo[1] + j - Vh;
+                R tsum = 0;
                 for (int q = 0; q < 12; ++q) {
                     cpx<R> rv = SV::ld(v.res, q, Vh, sh_);
                     rv = rv - alpha * SV::ld(v.sv, q, Vh, sh_);
                     SV::st(v.res, q, Vh, sh_, rv);
-                    rr_new += (double)norm2(rv);
+                    tsum += norm2(rv);
                 }
+                rr_new += (double)tsum;
             }
             rr_new = cl_sum<NT, CL>(rr_new, sh);
             const R beta = (R)(rr_new / rr);
