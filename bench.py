@@ -149,9 +149,10 @@ def allsum(ws, v):
 
 # DRAM bytes / algorithmic bytes of one ncu capture of the kernel on the
 # bench's workload (profiles/block_solve_cluster_kernel_fp32_16x4.md: the
-# first timed block-solver launch, branch-free hop variant); None once the
-# kernel changes
-TRAFFIC_RATIO = {"block_solve_cluster_kernel": 0.148}
+# first timed block-solver launch, branch-free hop variant: 0.148); None
+# once the kernel changes.  The kernel has changed since that capture (the
+# per-site norm sums), so no ratio is applied.
+TRAFFIC_RATIO = {"block_solve_cluster_kernel": None}
 
 
 def roofline_entry(kernel, n, ms, nbytes, peak, peak_kind):
