@@ -229,9 +229,11 @@ psms_status psms_spinor_export(psms_ctx *ctx, const void *native_dev, double *ca
 psms_status psms_dw_apply(psms_ctx *ctx, int field, int op, const void *in_dev, void *out_dev, int prec);
 
 /* Solve op(U_field) x = b to |b - op x| <= tol |b| in FP64 (true residual),
- * with inner Krylov iterations (even-odd preconditioned CGNR) in
- * inner_prec inside FP64 defect correction.  b, x: native FP64 buffers.
- * PSMS_ENOCONV if maxit inner iterations do not reach tol. */
+ * with inner Krylov iterations on the even-odd operator in inner_prec inside
+ * FP64 defect correction: BiCGStab (whole lattice, default) or CGNR (blocks,
+ * default), see psms_full_solver / psms_block_krylov.  b, x: native FP64
+ * buffers.  PSMS_ENOCONV if maxit inner iterations do not reach tol;
+ * PSMS_EINVAL for a non-finite b. */
 psms_status psms_solve(psms_ctx *ctx, int field, int op, const void *b_dev, void *x_dev, double tol,
                        int maxit, int inner_prec, psms_solve_info *info);
 
