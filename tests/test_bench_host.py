@@ -1,0 +1,53 @@
+"""Host-side logic of bench.py (no GPU): the roofline arithmetic and the
+parsing of the nvidia-smi clock record that decides whether a run counts."""
+import os
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_roofline_entry_arithmetic():
+    # 10 launches, 2 ms in total, 6.7619e9 algorithmic bytes -> 3380.95 GB/s
+    e = bench.roofline_entry("k", 10, 2.0, 6.7619e9, 6761.9, "measured")
+    assert e["achieved"] == pytest.approx(3380.95, abs=0.1)
+    assert e["frac"] == pytest.approx(0.5, abs=1e-4)
+    assert e["avg_launch_ms"] == pytest.approx(0.2)
+    assert e["bound"] == "hbm" and e["unit"] == "GB/s" and e["traffic"] is None
+    assert bench.roofline_entry("k", 0, 0.0, 0.0, 6761.9, "measured")["achieved"] == 0.0
+
+
+def _summary(lines):
+    c = bench.ClockSampler(0)
+    c.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    c.f.write("\n".join(lines) + "\n")
+    c.f.flush()
+    try:
+        return c.summary()
+    finally:
+        os.unlink(c.f.name)
+
+
+def test_clock_summary_reasons_and_median():
+    rows = [
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1200.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 1980, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+    ]
+    s = _summary(rows)
+    assert s["samples"] == 3
+    assert s["sm_mhz"] == 2055.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+    s = _summary(["0, 1500, 2070, 800, 0x40, Not Active, Active, Not Active, Not Active"])
+    assert s["reasons"] == ["hw_thermal_slowdown"]
+
+
+def test_step_model_covers_every_workload():
+    assert set(bench.STEP_MODEL) == set(bench.WORKLOADS)
+    for iters, acc in bench.STEP_MODEL.values():
+        assert iters > 0 and 0.0 <= acc <= 1.0
