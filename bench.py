@@ -523,6 +523,27 @@ def _timed_steps(ps, torch, ctx, prm, inner, learned, steps, flush, step0=0):
     return recs, ms
 
 
+def delta_stats(recs):
+    """Per level: mean and variance of the estimates Delta, the measured
+    acceptance, and the acceptance a Gaussian Delta with that variance would
+    have under detailed balance, erfc(sqrt(Sigma^2 / 8)) (Sec. 2, the
+    expectation of min{1, e^-Delta} over proposals)."""
+    out = {}
+    blocks = np.concatenate([np.asarray(r["delta_block"], dtype=np.float64) for r in recs]) if recs else np.zeros(0)
+    acc_b = np.concatenate([np.asarray(r["accept_block"], dtype=bool) for r in recs]) if recs else np.zeros(0, bool)
+    if blocks.size:
+        var = float(blocks.var())
+        out["block"] = {"mean": float(blocks.mean()), "var": var, "acceptance": float(acc_b.mean()),
+                        "gaussian_prediction": math.erfc(math.sqrt(var / 8.0))}
+    glob = [r["delta_global"] for r in recs if r.get("n_accept_blocks", 0) > 0]
+    if len(glob) > 1:
+        g = np.asarray(glob, dtype=np.float64)
+        acc_g = [bool(r["accept_global"]) for r in recs if r.get("n_accept_blocks", 0) > 0]
+        out["global"] = {"mean": float(g.mean()), "var": float(g.var()), "acceptance": float(np.mean(acc_g)),
+                         "gaussian_prediction": math.erfc(math.sqrt(float(g.var()) / 8.0)), "n": len(glob)}
+    return out
+
+
 def _accepted(recs):
     """Accepted updates: steps whose global level accepted a changed field."""
     return sum(1 for r in recs if r["accept_global"] and r["n_accept_blocks"] > 0)
@@ -692,6 +713,7 @@ def our_arm(args):
         "acceptance": {"global": sum(r["accept_global"] for r in recs) / len(recs),
                        "blocks": sum(r["n_accept_blocks"] for r in recs) / sum(r["n_blocks"] for r in recs)},
         "solver_iters_per_step": full_iters,
+        "delta_statistics": delta_stats(recs),
         "gauge_fix_steps_per_step": sum(r["gf_steps"] for r in recs) / len(recs),
         "plaquette_start": plaq0,
         "roofline": rl_main,

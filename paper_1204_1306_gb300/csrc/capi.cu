@@ -5,9 +5,14 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define PSMS_HAVE_NVTX 1
+#endif
 #include "estimator.hpp"
 #include "gauge.hpp"
 #include "gaugefix.hpp"
@@ -614,6 +619,23 @@ static GaugeFixParams gf_params(const psms_relgf_params &p) {
     return q;
 }
 
+// NVTX range for one level of the filter step (visible to Nsight tools, a
+// no-op otherwise)
+struct Range {
+    explicit Range(const char *name) {
+#ifdef PSMS_HAVE_NVTX
+        nvtxRangePushA(name);
+#else
+        (void)name;
+#endif
+    }
+    ~Range() {
+#ifdef PSMS_HAVE_NVTX
+        nvtxRangePop();
+#endif
+    }
+};
+
 psms_status psms_relative_gauge_fix(psms_ctx *ctx, int field_old, int field_new, int out_old, int out_new,
                                     const psms_relgf_params *prm, int *steps, double *alpha, double *theta,
                                     int *swapped, void *g_dev) {
@@ -662,7 +684,9 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
     double2 *mid = (double2 *)scratch(ctx, "fs_mid", fb);
     cuda_check(cudaMemcpyAsync(old, cur, fb, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
     // level 0: proposal (domain sweep, or an external proposal slot)
+    Range r_step("psms_filter_step");
     int failed = 0;
+    std::unique_ptr<Range> r_lvl(new Range("level 0: proposal"));
     if (prm->proposal_field >= 0) {
         check_field(ctx, prm->proposal_field);
         if (prm->proposal_field == field) fail(PSMS_EINVAL, "the proposal slot must differ from the field");
@@ -678,6 +702,8 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
     bool per_block = true;
     for (int m = 0; m < 4; ++m) per_block &= g.l[m] >= 3;
     if (prm->beta_block != 0.0) fail(PSMS_EINVAL, "beta_block != 0 is not supported");
+    r_lvl.reset();  // pop before the next push (NVTX ranges nest as a stack)
+    r_lvl.reset(new Range("learned level"));
     // learned level (before level 1): h_b, accept with min{1, exp(-h_b)}
     const int *d_mask = nullptr;
     double *d_h = nullptr;
@@ -701,6 +727,8 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         for (int v : h3) n_learned += v;
         d_mask = d_acc3;
     }
+    r_lvl.reset();  // pop before the next push (NVTX ranges nest as a stack)
+    r_lvl.reset(new Range("relative gauge fixing"));
     // relative gauge fixing: the estimators interpolate between U^{g_1} and
     // U'^{g_2} (Sec. 4.2); blocks decouple, so the level-2 endpoints are the
     // level-1 ones on accepted blocks and U elsewhere
@@ -717,6 +745,8 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         cuda_check(cudaStreamSynchronize(ctx->stream), "gf");
         for (int v : hs) gf_steps += v;
     }
+    r_lvl.reset();  // pop before the next push (NVTX ranges nest as a stack)
+    r_lvl.reset(new Range("level 1: block det ratios"));
     // level 1: block det ratios (blocks that passed the learned level)
     double *d_db = (double *)scratch(ctx, "fs_dblk", sizeof(double) * nb * N1);
     long long iters = 0;
@@ -741,6 +771,8 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         nacc += ha[b];
         dsum += hd[b];
     }
+    r_lvl.reset();  // pop before the next push (NVTX ranges nest as a stack)
+    r_lvl.reset(new Range("level 2: global det ratio"));
     // level 2: global Schur det ratio (a field equal to the old one has
     // Delta = 0 exactly: every M_i is the identity)
     double dglob = 0;
@@ -773,6 +805,7 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         accg = (dglob <= 0.0 || u < std::exp(-dglob)) ? 1 : 0;
         if (!accg) fin = old;
     }
+    r_lvl.reset();
     // random translation
     int sh[4] = {0, 0, 0, 0};
     if (prm->translate) {

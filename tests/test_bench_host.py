@@ -51,3 +51,28 @@ def test_step_model_covers_every_workload():
     assert set(bench.STEP_MODEL) == set(bench.WORKLOADS)
     for iters, acc in bench.STEP_MODEL.values():
         assert iters > 0 and 0.0 <= acc <= 1.0
+
+
+def test_delta_statistics_and_gaussian_prediction():
+    import math
+
+    import numpy as np
+    recs = [{"delta_block": np.array([1.0, 3.0]), "accept_block": np.array([True, False]),
+             "delta_global": 0.5, "accept_global": True, "n_accept_blocks": 1},
+            {"delta_block": np.array([-1.0, 1.0]), "accept_block": np.array([True, True]),
+             "delta_global": 1.5, "accept_global": False, "n_accept_blocks": 2},
+            {"delta_block": np.array([0.0, 0.0]), "accept_block": np.array([False, False]),
+             "delta_global": 0.0, "accept_global": True, "n_accept_blocks": 0}]
+    st = bench.delta_stats(recs)
+    b = np.array([1.0, 3.0, -1.0, 1.0, 0.0, 0.0])
+    assert st["block"]["mean"] == pytest.approx(b.mean())
+    assert st["block"]["var"] == pytest.approx(b.var())
+    assert st["block"]["acceptance"] == pytest.approx(3 / 6)
+    assert st["block"]["gaussian_prediction"] == pytest.approx(math.erfc(math.sqrt(b.var() / 8)))
+    # the global level counts only steps that changed the field
+    assert st["global"]["n"] == 2 and st["global"]["mean"] == pytest.approx(1.0)
+    assert st["global"]["acceptance"] == pytest.approx(0.5)
+    # Sigma^2 = 0 predicts certain acceptance
+    assert bench.delta_stats([{"delta_block": np.zeros(3), "accept_block": np.ones(3, bool),
+                               "delta_global": 0.0, "accept_global": True,
+                               "n_accept_blocks": 0}])["block"]["gaussian_prediction"] == 1.0
