@@ -27,6 +27,11 @@ filter     accept/reject decisions and one hierarchical filter step
            (Eq. (hierarchy), Sec. 3 and App. A).
 mlp        learned delayed-acceptance level: domain features and an FP64
            MLP forward/backward.
+gaugefix   relative gauge fixing of a pair of fields (Sec. 4.2, App. B).
+recursive  recursive domain decomposition (Eq. (ddrec)): nested blocks, the
+           Schur complements of the outer blocks and their stochastic
+           estimate, and the filter step with one level of recursion
+           (Eq. (4step)).
 
 Pins: functions are checked in ``tests/test_oracle_*.py`` against closed forms,
 library routines and numbers printed in the paper (``tests/golden``).
