@@ -28,6 +28,9 @@ filter     accept/reject decisions and one hierarchical filter step
 mlp        learned delayed-acceptance level: domain features and an FP64
            MLP forward/backward.
 gaugefix   relative gauge fixing of a pair of fields (Sec. 4.2, App. B).
+hyp        one level of HYP smearing and the block HYP plaquette action of
+           the parametrised levels (App. C, Sec. 5).
+params     coefficients of the parametrised levels (App. C, Eq. (paramsi)).
 recursive  recursive domain decomposition (Eq. (ddrec)): nested blocks, the
            Schur complements of the outer blocks and their stochastic
            estimate, and the filter step with one level of recursion

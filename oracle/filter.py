@@ -49,6 +49,9 @@ class FilterParams:
     global_level: bool = True
     learned: object = None   # MLP parameter dict (oracle.mlp) or None
     gauge_fix: object = None  # relative gauge fixing (Sec. 4.2): dict of oracle.gaugefix parameters, or None
+    hyp_level: object = None  # (beta_1^(0), beta_1^(1)) of the HYP plaquette level (App. C), or None
+    beta_block_hyp: float = 0.0   # beta^(1) of the block level (HYP action)
+    beta_global_hyp: float = 0.0  # beta^(1) of the global level (HYP action)
 
 
 def gaussian_acceptance(sigma2):
@@ -114,6 +117,15 @@ def _merge(U, V, acc_b, geom, active):
 def filter_step(U, geom, prm, seed, step, h_override=None, gf_override=None, proposal=None, translate=True):
     """Returns (new field, record dict).
 
+    With prm.hyp_level = (b0, b1) a parametrised level precedes the others
+    (App. C; the first filter of Tables 1 and 2): per block,
+    Delta_b = b0 dS_w,b + b1 dS_HYP,b with the block HYP action of
+    oracle.hyp, counter (step, 5, b), or one decision on the sum for blocks
+    of extent <= 2 (counter (step, 5, 0)).  Blocks it rejects keep their
+    links and skip the later block levels.  beta_block_hyp and
+    beta_global_hyp add the HYP action's change to the block and global
+    levels.
+
     With prm.learned (per-block decisions only) a learned level precedes
     level 1: h_b from the surrogate (or h_override, the values a device
     computed, so that both sides decide on the same numbers), accepted with
@@ -137,6 +149,20 @@ def filter_step(U, geom, prm, seed, step, h_override=None, gf_override=None, pro
         Unew, failed = np.array(proposal, copy=True), 0
     per_block = min(geom.block) >= 3
     passed = np.ones(geom.n_blocks, dtype=bool)
+    use_hyp = prm.hyp_level is not None or prm.beta_block_hyp != 0.0 or prm.beta_global_hyp != 0.0
+    ds_hyp = None
+    rec_hyp = None
+    if use_hyp:
+        from .hyp import block_hyp_change
+        ds_hyp = block_hyp_change(U, Unew, geom)
+    if prm.hyp_level is not None:
+        b0, b1 = prm.hyp_level
+        d_hyp = b0 * per_block_action_change(U, Unew, geom) + b1 * ds_hyp
+        if per_block:
+            passed = np.array([accept(d_hyp[b], philox.accept_uniform(seed, step, 5, b)) for b in range(geom.n_blocks)])
+        else:
+            passed = np.full(geom.n_blocks, accept(d_hyp.sum(), philox.accept_uniform(seed, step, 5, 0)))
+        rec_hyp = (d_hyp, passed.copy())
     h = np.zeros(geom.n_blocks)
     rec_h = None
     if prm.learned is not None:
@@ -144,7 +170,8 @@ def filter_step(U, geom, prm, seed, step, h_override=None, gf_override=None, pro
         assert per_block
         z = pair_features(U, Unew, geom)
         h = antisym(prm.learned, z) if h_override is None else np.asarray(h_override, dtype=np.float64)
-        passed = np.array([accept(h[b], philox.accept_uniform(seed, step, 3, b)) for b in range(geom.n_blocks)])
+        passed = passed & np.array([accept(h[b], philox.accept_uniform(seed, step, 3, b))
+                                    for b in range(geom.n_blocks)])
         rec_h = h
 
     E0, EN = U, Unew
@@ -164,18 +191,22 @@ def filter_step(U, geom, prm, seed, step, h_override=None, gf_override=None, pro
         d_blk[blocks] = d_all[blocks].sum(axis=1)
     if prm.beta_block != 0.0:
         d_blk = d_blk + prm.beta_block * per_block_action_change(U, Unew, geom)
+    if prm.beta_block_hyp != 0.0:
+        d_blk = d_blk + prm.beta_block_hyp * ds_hyp
     d_blk = d_blk - h
     if per_block:
         acc_b = np.array([passed[b] and accept(d_blk[b], philox.accept_uniform(seed, step, 1, b))
                           for b in range(geom.n_blocks)])
     else:
-        a = accept(d_blk.sum(), philox.accept_uniform(seed, step, 1, 0))
+        a = bool(passed.all()) and accept(d_blk.sum(), philox.accept_uniform(seed, step, 1, 0))
         acc_b = np.full(geom.n_blocks, a)
 
     Umid = _merge(U, Unew, acc_b, geom, active)
 
     rec = {"delta_block": d_blk, "accept_block": acc_b, "hb_failed": failed, "h": rec_h,
-           "passed_learned": passed, "gauge_fix": rec_gf}
+           "passed_learned": passed, "gauge_fix": rec_gf,
+           "delta_hyp": None if rec_hyp is None else rec_hyp[0],
+           "accept_hyp": None if rec_hyp is None else rec_hyp[1]}
     Ufin = Umid
     if prm.global_level:
         G0, GN = U, Umid
@@ -185,6 +216,8 @@ def filter_step(U, geom, prm, seed, step, h_override=None, gf_override=None, pro
         d = float(dg.sum())
         if prm.beta_global != 0.0:
             d += prm.beta_global * (wilson_action(Umid) - wilson_action(U))
+        if prm.beta_global_hyp != 0.0:
+            d += prm.beta_global_hyp * float(ds_hyp[acc_b].sum())
         acc_g = accept(d, philox.accept_uniform(seed, step, 2, 0))
         rec["delta_global"] = d
         rec["delta_global_terms"] = dg
