@@ -443,6 +443,35 @@ psms_status psms_checkpoint_load(psms_ctx *ctx, int field, const char *path, uin
  * give identical results; the two methods agree to the solve tolerance. */
 psms_status psms_autotune(psms_ctx *ctx, int enable, int block_variant);
 
+/* ---- coefficients of the parametrised levels (App. C) ------------------------
+ * Host functions: no context, no device memory, no kernel; callable without
+ * a GPU.  They return a status only (psms_last_error needs a context).
+ *
+ * psms_level_covariance: C^(jk) of Eq. (sigmaDeltaSiparams) from n_samples
+ * rows of n_actions action changes (Delta S^(0), ..., Delta S^(i)), samples
+ * row-major [n_samples][n_actions]; cov receives the n_actions x n_actions
+ * matrix (row-major), normalised by n_samples.  PSMS_EINVAL for null
+ * pointers, n_samples < 2, n_actions outside 1..64 or a non-finite sample.
+ *
+ * psms_level_coefficients: the coefficients beta_i^(j) of Eq. (Si) for
+ * levels i = 0..n_levels (level 0 is the pure-gauge proposal), written to
+ * beta as a row-major (n_levels+1)^2 lower-triangular matrix, row i =
+ * level, column j = action.  covs packs the covariance of level i = 1..n
+ * ((i+1) x (i+1), actions 0..i, row-major) one after the other; targets[j]
+ * is beta^(j), the value every action's coefficients must sum to (the
+ * plaquette's beta, 0 for an auxiliary action, 1 for a determinant);
+ * stochastic (optional, n_levels+1 flags) marks actions estimated
+ * stochastically, which take no coefficient at later levels.  From the last
+ * level down the level's own coefficient follows from its target and the
+ * free ones minimise the level's variance beta^T C_i beta, i.e. solve
+ * sum_k C^(jk) beta_i^(k) = -C^(ji) beta_i^(i) (Eq. (paramsi) read as the
+ * stationarity condition of Eq. (sigmaDeltaSiparams)); beta_0^(0) closes the
+ * plaquette constraint.  PSMS_EINVAL for null pointers, n_levels outside
+ * 1..63, a non-finite input or a singular system of free actions. */
+psms_status psms_level_covariance(const double *samples, long long n_samples, int n_actions, double *cov);
+psms_status psms_level_coefficients(int n_levels, const double *covs, const double *targets,
+                                    const int *stochastic, double *beta);
+
 /* Number of CUDA kernels the library has launched in this process. */
 long long psms_kernel_launches(void);
 

@@ -23,7 +23,7 @@ __all__ = [
     "psms_block_plan_destroy", "BlockPlan", "psms_autotune", "psms_profile_read_block",
     "psms_domain_features_pair", "psms_checkpoint_save", "psms_checkpoint_load",
     "psms_relative_gauge_fix", "psms_profile_block_launches", "psms_hop_variant", "psms_full_solver",
-    "psms_block_krylov", "SOLVER_CGNR", "SOLVER_BICGSTAB",
+    "psms_block_krylov", "SOLVER_CGNR", "SOLVER_BICGSTAB", "psms_level_covariance", "psms_level_coefficients",
     "PREC_F64", "PREC_F32", "PREC_BF16", "OP_FULL", "OP_BLOCKS", "ACTIVE_BLOCKS", "ACTIVE_ALL",
     "LEVEL_BLOCK", "LEVEL_GLOBAL", "EST_INTERP", "EST_INDEPENDENT",
 ]
@@ -141,6 +141,8 @@ _SIGS = {
     "psms_profile_read_block": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), ctypes.POINTER(_D)],
     "psms_profile_enable": [_P, _I],
     "psms_profile_read": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    "psms_level_covariance": [_P, ctypes.c_longlong, _I, _P],
+    "psms_level_coefficients": [_I, _P, _P, _P, _P],
 }
 
 _lib = None
@@ -510,3 +512,41 @@ def psms_profile_read(ctx):
     n, ms, by = ctypes.c_longlong(), _D(), _D()
     ctx.check(ctx.lib.psms_profile_read(ctx.handle, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
     return n.value, ms.value, by.value
+
+
+def _host_check(st, name):
+    if st != 0:
+        raise PsmsError(st, name + " failed")
+
+
+def psms_level_covariance(samples):
+    """Covariance [n_actions, n_actions] of action-change samples
+    [n_samples, n_actions] (host function of the library)."""
+    x = np.ascontiguousarray(samples, dtype=np.float64)
+    if x.ndim != 2:
+        raise ValueError("samples must be [n_samples, n_actions]")
+    out = np.empty((x.shape[1], x.shape[1]), dtype=np.float64)
+    _host_check(load_library().psms_level_covariance(x.ctypes.data, x.shape[0], x.shape[1], out.ctypes.data),
+                "psms_level_covariance")
+    return out
+
+
+def psms_level_coefficients(covs, targets, stochastic=None):
+    """beta_i^(j) [n+1, n+1] of the parametrised levels from the level
+    covariances covs[i-1] ((i+1) x (i+1), i = 1..n), the targets beta^(j)
+    and optional stochastic flags per action (host function of the library)."""
+    n = len(targets) - 1
+    packed = np.concatenate([np.ascontiguousarray(c, dtype=np.float64).reshape(-1) for c in covs]) \
+        if n >= 1 else np.zeros(0)
+    for i, c in enumerate(covs, start=1):
+        if np.shape(c) != (i + 1, i + 1):
+            raise ValueError(f"covariance of level {i} must be {(i + 1, i + 1)}")
+    if len(covs) != n:
+        raise ValueError("one covariance per level 1..n")
+    t = np.ascontiguousarray(targets, dtype=np.float64)
+    st = None if stochastic is None else np.ascontiguousarray(stochastic, dtype=np.int32)
+    out = np.empty((n + 1, n + 1), dtype=np.float64)
+    _host_check(load_library().psms_level_coefficients(n, packed.ctypes.data, t.ctypes.data,
+                                                       None if st is None else st.ctypes.data, out.ctypes.data),
+                "psms_level_coefficients")
+    return out
