@@ -443,6 +443,27 @@ psms_status psms_checkpoint_load(psms_ctx *ctx, int field, const char *path, uin
  * give identical results; the two methods agree to the solve tolerance. */
 psms_status psms_autotune(psms_ctx *ctx, int enable, int block_variant);
 
+/* ---- HYP-smeared links and the block HYP plaquette action (App. C, Sec. 5) ----
+ * One level of HYP smearing of gauge slot `field`: three steps, each a
+ * weighted sum of a link and its staples projected onto SU(3), confined to
+ * the hypercubes attached to the link, with parameters alpha = (a1, a2, a3)
+ * (NULL: (0.75, 0.6, 0.3), the HYP construction's; each must lie in
+ * [0, 1], else PSMS_EINVAL).  The projection is the unitary polar factor
+ * with the determinant's phase removed by the principal cube root.  FP64.
+ *
+ * psms_hyp_smear writes the fat links to links_dev (canonical layout,
+ * 4V x 9 complex doubles, caller-owned device memory).
+ *
+ * psms_hyp_block_action writes S_HYP,b for every block (lexicographic
+ * block index) to s_host[n_blocks]: Eq. (Sw) without beta on the fat links,
+ * restricted to the plaquettes whose four corners lie in block b.  With
+ * blocks of extent >= 3 it depends only on the block's active links and on
+ * links that are never active, so its change factorises over blocks.
+ * PSMS_ESPECTRUM if a smearing sum was singular (non-finite result).
+ * Synchronises the context's stream. */
+psms_status psms_hyp_smear(psms_ctx *ctx, int field, const double *alpha, double *links_dev);
+psms_status psms_hyp_block_action(psms_ctx *ctx, int field, const double *alpha, double *s_host);
+
 /* ---- coefficients of the parametrised levels (App. C) ------------------------
  * Host functions: no context, no device memory, no kernel; callable without
  * a GPU.  They return a status only (psms_last_error needs a context).

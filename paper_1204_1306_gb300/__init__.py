@@ -24,6 +24,7 @@ __all__ = [
     "psms_domain_features_pair", "psms_checkpoint_save", "psms_checkpoint_load",
     "psms_relative_gauge_fix", "psms_profile_block_launches", "psms_hop_variant", "psms_full_solver",
     "psms_block_krylov", "SOLVER_CGNR", "SOLVER_BICGSTAB", "psms_level_covariance", "psms_level_coefficients",
+    "psms_hyp_smear", "psms_hyp_block_action",
     "PREC_F64", "PREC_F32", "PREC_BF16", "OP_FULL", "OP_BLOCKS", "ACTIVE_BLOCKS", "ACTIVE_ALL",
     "LEVEL_BLOCK", "LEVEL_GLOBAL", "EST_INTERP", "EST_INDEPENDENT",
 ]
@@ -142,6 +143,8 @@ _SIGS = {
     "psms_profile_enable": [_P, _I],
     "psms_profile_read": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), ctypes.POINTER(_D)],
     "psms_level_covariance": [_P, ctypes.c_longlong, _I, _P],
+    "psms_hyp_smear": [_P, _I, _P, _P],
+    "psms_hyp_block_action": [_P, _I, _P, _P],
     "psms_level_coefficients": [_I, _P, _P, _P, _P],
 }
 
@@ -549,4 +552,22 @@ def psms_level_coefficients(covs, targets, stochastic=None):
     _host_check(load_library().psms_level_coefficients(n, packed.ctypes.data, t.ctypes.data,
                                                        None if st is None else st.ctypes.data, out.ctypes.data),
                 "psms_level_coefficients")
+    return out
+
+
+def _alpha(alpha):
+    return None if alpha is None else (ctypes.c_double * 3)(*[float(a) for a in alpha])
+
+
+def psms_hyp_smear(ctx, field, out_dev, alpha=None):
+    """Fat links of one level of HYP smearing into out_dev (canonical layout,
+    4V x 9 complex doubles on the device)."""
+    ctx.check(ctx.lib.psms_hyp_smear(ctx.handle, field, _alpha(alpha), _ptr(out_dev)))
+
+
+def psms_hyp_block_action(ctx, field, alpha=None):
+    """S_HYP,b per block (lexicographic block index)."""
+    nb = int(psms_geometry_info(ctx)[0])
+    out = np.empty(nb, dtype=np.float64)
+    ctx.check(ctx.lib.psms_hyp_block_action(ctx.handle, field, _alpha(alpha), out.ctypes.data))
     return out

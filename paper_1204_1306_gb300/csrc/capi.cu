@@ -16,6 +16,7 @@
 #include "estimator.hpp"
 #include "gauge.hpp"
 #include "gaugefix.hpp"
+#include "hyp.hpp"
 #include "mlp.hpp"
 #include "solver.hpp"
 
@@ -401,6 +402,43 @@ psms_status psms_gauge_get(psms_ctx *ctx, int field, double *links) {
     check_field(ctx, field);
     if (!links) fail(PSMS_EINVAL, "null links");
     gauge_canonical(ctx, (const double2 *)links, ctx->U64[field], 0);
+    PSMS_CATCH(ctx)
+}
+
+// HYP smearing parameters: the caller's (each in [0, 1]) or those of the
+// HYP construction, (0.75, 0.6, 0.3)
+static void hyp_alpha(const double *alpha, double a[3]) {
+    const double def[3] = {0.75, 0.6, 0.3};
+    for (int i = 0; i < 3; ++i) {
+        a[i] = alpha ? alpha[i] : def[i];
+        if (!(a[i] >= 0.0 && a[i] <= 1.0)) fail(PSMS_EINVAL, "HYP parameters must lie in [0, 1]");
+    }
+}
+
+psms_status psms_hyp_smear(psms_ctx *ctx, int field, const double *alpha, double *links_dev) {
+    PSMS_TRY(ctx)
+    check_field(ctx, field);
+    if (!links_dev) fail(PSMS_EINVAL, "null links");
+    double a[3];
+    hyp_alpha(alpha, a);
+    const double2 *F1 = hyp_smear(ctx, ctx->U64[field], a, nullptr);
+    gauge_canonical(ctx, (const double2 *)links_dev, const_cast<double2 *>(F1), 0);
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_hyp_block_action(psms_ctx *ctx, int field, const double *alpha, double *s_host) {
+    PSMS_TRY(ctx)
+    check_field(ctx, field);
+    if (!s_host) fail(PSMS_EINVAL, "null output");
+    double a[3];
+    hyp_alpha(alpha, a);
+    const int nb = ctx->g.nblocks;
+    double *d = (double *)scratch(ctx, "hyp_action", sizeof(double) * nb);
+    hyp_block_action(ctx, ctx->U64[field], a, d);
+    cuda_check(cudaMemcpyAsync(s_host, d, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream), "hyp action");
+    cuda_check(cudaStreamSynchronize(ctx->stream), "hyp action");
+    for (int b = 0; b < nb; ++b)
+        if (!std::isfinite(s_host[b])) fail(PSMS_ESPECTRUM, "non-finite HYP action (singular smearing sum)");
     PSMS_CATCH(ctx)
 }
 
