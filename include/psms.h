@@ -128,7 +128,8 @@ typedef struct {
     int n_or;
     /* level 1: block det ratios, N = n_block interpolation steps (Eq. (staccN)) */
     int n_block;
-    double beta_block;     /* coefficient of dS_w at level 1 (App. C)          */
+    double beta_block;     /* coefficient of dS_w,b at level 1 (App. C; dS_w,b as
+                              in psms_block_action_change)                     */
     /* level 2: global Schur-complement det ratio                              */
     int n_global;
     double beta_global;    /* coefficient of dS_w at level 2 (App. C)          */
@@ -442,6 +443,16 @@ psms_status psms_checkpoint_load(psms_ctx *ctx, int field, const char *path, uin
  * tuning cache.  PSMS_EINVAL outside -1..17.  Variants of one Krylov method
  * give identical results; the two methods agree to the solve tolerance. */
 psms_status psms_autotune(psms_ctx *ctx, int enable, int block_variant);
+
+/* Per-block change of the plaquette action, dS_w,b = S_w,b(new) - S_w,b(old)
+ * (Eq. (Sw) without beta), for every block (lexicographic block index) into
+ * ds_host[n_blocks].  A plaquette whose links changed belongs to the block
+ * of the starting site of its first changed link in the order (x,mu),
+ * (x+mu,nu), (x+nu,mu), (x,nu) (a link changed when any of its numbers
+ * differs); the sum over blocks is the change of S_w.  It is the term
+ * psms_filter_params.beta_block multiplies.  FP64, deterministic;
+ * synchronises the context's stream. */
+psms_status psms_block_action_change(psms_ctx *ctx, int field_old, int field_new, double *ds_host);
 
 /* ---- HYP-smeared links and the block HYP plaquette action (App. C, Sec. 5) ----
  * One level of HYP smearing of gauge slot `field`: three steps, each a

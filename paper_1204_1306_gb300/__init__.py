@@ -24,7 +24,7 @@ __all__ = [
     "psms_domain_features_pair", "psms_checkpoint_save", "psms_checkpoint_load",
     "psms_relative_gauge_fix", "psms_profile_block_launches", "psms_hop_variant", "psms_full_solver",
     "psms_block_krylov", "SOLVER_CGNR", "SOLVER_BICGSTAB", "psms_level_covariance", "psms_level_coefficients",
-    "psms_hyp_smear", "psms_hyp_block_action",
+    "psms_hyp_smear", "psms_hyp_block_action", "psms_block_action_change",
     "PREC_F64", "PREC_F32", "PREC_BF16", "OP_FULL", "OP_BLOCKS", "ACTIVE_BLOCKS", "ACTIVE_ALL",
     "LEVEL_BLOCK", "LEVEL_GLOBAL", "EST_INTERP", "EST_INDEPENDENT",
 ]
@@ -144,6 +144,7 @@ _SIGS = {
     "psms_profile_read": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), ctypes.POINTER(_D)],
     "psms_level_covariance": [_P, ctypes.c_longlong, _I, _P],
     "psms_hyp_smear": [_P, _I, _P, _P],
+    "psms_block_action_change": [_P, _I, _I, _P],
     "psms_hyp_block_action": [_P, _I, _P, _P],
     "psms_level_coefficients": [_I, _P, _P, _P, _P],
 }
@@ -570,4 +571,12 @@ def psms_hyp_block_action(ctx, field, alpha=None):
     nb = int(psms_geometry_info(ctx)[0])
     out = np.empty(nb, dtype=np.float64)
     ctx.check(ctx.lib.psms_hyp_block_action(ctx.handle, field, _alpha(alpha), out.ctypes.data))
+    return out
+
+
+def psms_block_action_change(ctx, field_old, field_new):
+    """dS_w,b of field_old -> field_new per block (lexicographic block index)."""
+    nb = int(psms_geometry_info(ctx)[0])
+    out = np.empty(nb, dtype=np.float64)
+    ctx.check(ctx.lib.psms_block_action_change(ctx.handle, field_old, field_new, out.ctypes.data))
     return out

@@ -1,0 +1,15 @@
+// Per-block change of the plaquette action (App. C beta terms, block level).
+#pragma once
+
+#include "kernels.hpp"
+
+namespace psms {
+
+// dS_w,b (Eq. (Sw) without beta) of U -> Up for every block, lexicographic
+// block index, into d_out[n_blocks]; plaquettes attributed to the block of
+// their first changed link (block_action.cuh)
+void block_action_change(psms_ctx *c, const double2 *U, const double2 *Up, double *d_out);
+// d_out[b] = beta * d_ds[b] - d_h[b] (d_h may be null)
+void block_extra(psms_ctx *c, const double *d_ds, double beta, const double *d_h, double *d_out);
+
+}  // namespace psms

@@ -17,6 +17,7 @@
 #include "gauge.hpp"
 #include "gaugefix.hpp"
 #include "hyp.hpp"
+#include "block_action.hpp"
 #include "mlp.hpp"
 #include "solver.hpp"
 
@@ -442,6 +443,19 @@ psms_status psms_hyp_block_action(psms_ctx *ctx, int field, const double *alpha,
     PSMS_CATCH(ctx)
 }
 
+psms_status psms_block_action_change(psms_ctx *ctx, int field_old, int field_new, double *ds_host) {
+    PSMS_TRY(ctx)
+    check_field(ctx, field_old);
+    check_field(ctx, field_new);
+    if (!ds_host) fail(PSMS_EINVAL, "null output");
+    const int nb = ctx->g.nblocks;
+    double *d = (double *)scratch(ctx, "bac_out", sizeof(double) * nb);
+    block_action_change(ctx, ctx->U64[field_old], ctx->U64[field_new], d);
+    cuda_check(cudaMemcpyAsync(ds_host, d, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream), "dS_w");
+    cuda_check(cudaStreamSynchronize(ctx->stream), "dS_w");
+    PSMS_CATCH(ctx)
+}
+
 psms_status psms_gauge_copy(psms_ctx *ctx, int dst, int src) {
     PSMS_TRY(ctx)
     check_field(ctx, dst);
@@ -739,7 +753,7 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
     const int nb = g.nblocks, N1 = prm->n_block;
     bool per_block = true;
     for (int m = 0; m < 4; ++m) per_block &= g.l[m] >= 3;
-    if (prm->beta_block != 0.0) fail(PSMS_EINVAL, "beta_block != 0 is not supported");
+    if (!std::isfinite(prm->beta_block)) fail(PSMS_EINVAL, "beta_block must be finite");
     r_lvl.reset();  // pop before the next push (NVTX ranges nest as a stack)
     r_lvl.reset(new Range("learned level"));
     // learned level (before level 1): h_b, accept with min{1, exp(-h_b)}
@@ -795,7 +809,18 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         cuda_check(cudaMemsetAsync(d_db, 0, sizeof(double) * nb * N1, ctx->stream), "dblk");
     double *d_dsum = (double *)scratch(ctx, "fs_dsum", sizeof(double) * (nb + 1));
     int *d_acc = (int *)scratch(ctx, "fs_acc", sizeof(int) * nb);
-    decide(ctx, d_db, nb, N1, per_block ? 1 : 0, prm->seed, prm->step, PSMS_LEVEL_BLOCK, 0.0, d_h, -1.0, d_dsum,
+    // per-block extra term: beta_block dS_w,b (App. C) minus the learned h_b
+    const double *d_extra = d_h;
+    double coef = -1.0;
+    if (prm->beta_block != 0.0) {
+        double *d_ds = (double *)scratch(ctx, "fs_dsw", sizeof(double) * nb);
+        double *d_ex = (double *)scratch(ctx, "fs_extra", sizeof(double) * nb);
+        block_action_change(ctx, old, prop, d_ds);
+        block_extra(ctx, d_ds, prm->beta_block, d_h, d_ex);
+        d_extra = d_ex;
+        coef = 1.0;
+    }
+    decide(ctx, d_db, nb, N1, per_block ? 1 : 0, prm->seed, prm->step, PSMS_LEVEL_BLOCK, 0.0, d_extra, coef, d_dsum,
            d_acc, d_mask);
     merge_blocks(ctx, old, prop, mid, d_acc);
     std::vector<double> hd(nb + 1);

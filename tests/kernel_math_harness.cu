@@ -1,9 +1,11 @@
-// Test harness: the library's HYP arithmetic (csrc/hyp.cuh), the same code
-// the kernels run, compiled for the host and driven over canonical arrays,
-// so that the tests can compare it with the oracle without a GPU.  Not part
-// of the library.
+// Test harness: per-thread arithmetic of the library's kernels (the HYP
+// smearing of csrc/hyp.cuh and the per-block action change of
+// csrc/block_action.cuh), the same code the kernels run, compiled for the
+// host and driven over canonical arrays, so that the tests can compare it
+// with the oracle without a GPU.  Not part of the library.
 #include <vector>
 
+#include "../paper_1204_1306_gb300/csrc/block_action.cuh"
 #include "../paper_1204_1306_gb300/csrc/hyp.cuh"
 
 using psms::hyp::M;
@@ -100,4 +102,43 @@ extern "C" void hyp_project_host(const double *m, int n, double *out) {
     const M *in = reinterpret_cast<const M *>(m);
     M *o = reinterpret_cast<M *>(out);
     for (int i = 0; i < n; ++i) o[i] = psms::hyp::project_su3(in[i]);
+}
+
+namespace {
+
+struct PairHostLd {
+    int L[4];
+    const M *U0, *U1;  // canonical [site][mu]
+
+    __host__ __device__ M operator()(int f, int mu, const int x[4]) const {
+        int y[4];
+        for (int m = 0; m < 4; ++m) y[m] = ((x[m] % L[m]) + L[m]) % L[m];
+        const long long s = ((long long)(y[0] * L[1] + y[1]) * L[2] + y[2]) * L[3] + y[3];
+        return (f ? U1 : U0)[s * 4 + mu];
+    }
+};
+
+}  // namespace
+
+// dS_w,b per block (lexicographic) of U0 -> U1, scanning each block the way
+// the kernel does (one thread)
+extern "C" void block_change_host(const double *U0, const double *U1, const int *L, const int *l, double *out) {
+    PairHostLd ld;
+    psms::act::Grid g;
+    for (int m = 0; m < 4; ++m) {
+        ld.L[m] = g.L[m] = L[m];
+        g.l[m] = l[m];
+        g.nb[m] = L[m] / l[m];
+    }
+    ld.U0 = reinterpret_cast<const M *>(U0);
+    ld.U1 = reinterpret_cast<const M *>(U1);
+    const int nb = g.nb[0] * g.nb[1] * g.nb[2] * g.nb[3];
+    for (int b = 0; b < nb; ++b) {
+        int B[4], q = b;
+        for (int m = 3; m >= 0; --m) {
+            B[m] = q % g.nb[m];
+            q /= g.nb[m];
+        }
+        out[b] = psms::act::block_change_partial(ld, g, B, b, 0, 1);
+    }
 }
