@@ -148,6 +148,19 @@ typedef struct {
                               drawn by a symmetric proposal (detailed-balance
                               tests); the slot is left unchanged             */
     int translate;         /* 1: random translation after the global level */
+    /* parametrised HYP level (App. C; the first filter of Tables 1 and 2):
+       with hyp_level = 1 a level before the learned and block levels accepts
+       block b with min{1, exp(-Delta_b)}, Delta_b = hyp_beta[0] dS_w,b +
+       hyp_beta[1] dS_HYP,b (psms_block_action_change,
+       psms_hyp_block_action with the default smearing), decision counter
+       (step, 5, b), or one decision on the sum (counter (step, 5, 0)) for
+       block extents <= 2; blocks it rejects keep their links and skip the
+       later block levels.  beta_block_hyp and beta_global_hyp add the HYP
+       action's change to the block and global levels.                    */
+    int hyp_level;
+    double hyp_beta[2];
+    double beta_block_hyp;
+    double beta_global_hyp;
 } psms_filter_params;
 
 typedef struct {
@@ -161,6 +174,7 @@ typedef struct {
     int hb_failed;
     int n_accept_learned;  /* blocks passing the learned level (-1: no level)  */
     long long gf_steps;    /* gauge-fixing steps summed over blocks            */
+    int n_accept_hyp;      /* blocks passing the HYP level (-1: no level)      */
 } psms_filter_result;
 
 typedef struct {

@@ -73,14 +73,17 @@ class FilterParams(ctypes.Structure):
                 ("beta_global", ctypes.c_double), ("global_level", ctypes.c_int), ("tol", ctypes.c_double),
                 ("inner_prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("step", ctypes.c_uint64),
                 ("learned", ctypes.c_int), ("gauge_fix", ctypes.c_int), ("relgf", RelGFParams),
-                ("proposal_field", ctypes.c_int), ("translate", ctypes.c_int)]
+                ("proposal_field", ctypes.c_int), ("translate", ctypes.c_int), ("hyp_level", ctypes.c_int),
+                ("hyp_beta", ctypes.c_double * 2), ("beta_block_hyp", ctypes.c_double),
+                ("beta_global_hyp", ctypes.c_double)]
 
 
 class FilterResult(ctypes.Structure):
     _fields_ = [("n_blocks", ctypes.c_int), ("n_accept_blocks", ctypes.c_int), ("accept_global", ctypes.c_int),
                 ("shift", ctypes.c_int * 4), ("delta_global", ctypes.c_double),
                 ("delta_block_sum", ctypes.c_double), ("solver_iters", ctypes.c_longlong),
-                ("hb_failed", ctypes.c_int), ("n_accept_learned", ctypes.c_int), ("gf_steps", ctypes.c_longlong)]
+                ("hb_failed", ctypes.c_int), ("n_accept_learned", ctypes.c_int), ("gf_steps", ctypes.c_longlong),
+                ("n_accept_hyp", ctypes.c_int)]
 
 
 class BlockProblem(ctypes.Structure):
@@ -310,14 +313,18 @@ def psms_logdet_ratio(ctx, level, field_old, field_new, n, mode, seed, counter, 
 
 def psms_filter_step(ctx, field, *, beta0, n_iter=1, n_or=0, n_block=4, n_global=4, beta_block=0.0,
                      beta_global=0.0, global_level=True, tol=1e-10, inner_prec=PREC_F64, seed=0, step=0,
-                     learned=False, gauge_fix=None, proposal_field=-1, translate=True):
+                     learned=False, gauge_fix=None, proposal_field=-1, translate=True, hyp_level=None,
+                     beta_block_hyp=0.0, beta_global_hyp=0.0):
     """gauge_fix: None (off) or a dict of relative gauge-fixing parameters
     (alpha0, alpha_min, dalpha, theta_tol, max_iter, prec; {} = defaults).
-    proposal_field: -1 (domain sweep) or the slot of an external proposal."""
+    proposal_field: -1 (domain sweep) or the slot of an external proposal.
+    hyp_level: None (off) or the coefficients (b0, b1) of the HYP level."""
+    hb = (0.0, 0.0) if hyp_level is None else tuple(float(v) for v in hyp_level)
     p = FilterParams(float(beta0), int(n_iter), int(n_or), int(n_block), float(beta_block), int(n_global),
                      float(beta_global), int(bool(global_level)), float(tol), int(inner_prec), int(seed), int(step),
                      int(bool(learned)), int(gauge_fix is not None), _relgf(**(gauge_fix or {})),
-                     int(proposal_field), int(bool(translate)))
+                     int(proposal_field), int(bool(translate)), int(hyp_level is not None), (_D * 2)(*hb),
+                     float(beta_block_hyp), float(beta_global_hyp))
     r = FilterResult()
     nb = int(np.prod([d // b for d, b in zip(ctx.dims, ctx.block)]))
     db = (_D * nb)()
@@ -326,7 +333,7 @@ def psms_filter_step(ctx, field, *, beta0, n_iter=1, n_or=0, n_block=4, n_global
     return {"n_blocks": r.n_blocks, "n_accept_blocks": r.n_accept_blocks, "accept_global": bool(r.accept_global),
             "shift": tuple(r.shift), "delta_global": r.delta_global, "delta_block_sum": r.delta_block_sum,
             "solver_iters": r.solver_iters, "hb_failed": r.hb_failed, "n_accept_learned": r.n_accept_learned,
-            "gf_steps": r.gf_steps,
+            "gf_steps": r.gf_steps, "n_accept_hyp": r.n_accept_hyp,
             "delta_block": np.frombuffer(db, dtype=np.float64).copy(),
             "accept_block": np.frombuffer(ab, dtype=np.int32).astype(bool)}
 

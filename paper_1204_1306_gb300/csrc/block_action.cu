@@ -51,9 +51,15 @@ __global__ void __launch_bounds__(kNT) block_change_kernel(Geom g, const BlockIn
     }
 }
 
-__global__ void combine_kernel(const double *ds, double beta, const double *h, double *out, int nb) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < nb) out[b] = beta * ds[b] - (h ? h[b] : 0.0);
+__global__ void lincomb_kernel(double a, const double *x, double b, const double *y, double e, const double *z,
+                               double *out, int nb) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    double v = 0.0;
+    if (x) v += a * x[k];
+    if (y) v += b * y[k];
+    if (z) v += e * z[k];
+    out[k] = v;
 }
 
 }  // namespace
@@ -63,10 +69,11 @@ void block_action_change(psms_ctx *c, const double2 *U, const double2 *Up, doubl
     PSMS_LAUNCH_CHECK("block_action_change");
 }
 
-void block_extra(psms_ctx *c, const double *d_ds, double beta, const double *d_h, double *d_out) {
+void block_lincomb(psms_ctx *c, double a, const double *x, double b, const double *y, double e, const double *z,
+                   double *d_out) {
     const int nb = c->g.nblocks;
-    combine_kernel<<<(nb + 127) / 128, 128, 0, c->stream>>>(d_ds, beta, d_h, d_out, nb);
-    PSMS_LAUNCH_CHECK("block_extra");
+    lincomb_kernel<<<(nb + 127) / 128, 128, 0, c->stream>>>(a, x, b, y, e, z, d_out, nb);
+    PSMS_LAUNCH_CHECK("block_lincomb");
 }
 
 }  // namespace psms

@@ -9,7 +9,8 @@ namespace psms {
 // block index, into d_out[n_blocks]; plaquettes attributed to the block of
 // their first changed link (block_action.cuh)
 void block_action_change(psms_ctx *c, const double2 *U, const double2 *Up, double *d_out);
-// d_out[b] = beta * d_ds[b] - d_h[b] (d_h may be null)
-void block_extra(psms_ctx *c, const double *d_ds, double beta, const double *d_h, double *d_out);
+// d_out[b] = a x[b] + b y[b] + e z[b], null terms left out (in that order)
+void block_lincomb(psms_ctx *c, double a, const double *x, double b, const double *y, double e, const double *z,
+                   double *d_out);
 
 }  // namespace psms

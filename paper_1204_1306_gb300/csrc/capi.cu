@@ -753,11 +753,48 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
     const int nb = g.nblocks, N1 = prm->n_block;
     bool per_block = true;
     for (int m = 0; m < 4; ++m) per_block &= g.l[m] >= 3;
-    if (!std::isfinite(prm->beta_block)) fail(PSMS_EINVAL, "beta_block must be finite");
+    if (!std::isfinite(prm->beta_block) || !std::isfinite(prm->beta_block_hyp) ||
+        !std::isfinite(prm->beta_global_hyp) || !std::isfinite(prm->hyp_beta[0]) || !std::isfinite(prm->hyp_beta[1]))
+        fail(PSMS_EINVAL, "filter coefficients must be finite");
+    r_lvl.reset();  // pop before the next push (NVTX ranges nest as a stack)
+    r_lvl.reset(new Range("HYP level"));
+    // per-block action changes of the proposal: dS_w,b (beta_block and the
+    // HYP level) and dS_HYP,b (the HYP terms, App. C)
+    const bool need_dsw = prm->beta_block != 0.0 || prm->hyp_level;
+    const bool need_hyp = prm->hyp_level || prm->beta_block_hyp != 0.0 || prm->beta_global_hyp != 0.0;
+    double *d_dsw = nullptr, *d_dhyp = nullptr;
+    if (need_dsw) {
+        d_dsw = (double *)scratch(ctx, "fs_dsw", sizeof(double) * nb);
+        block_action_change(ctx, old, prop, d_dsw);
+    }
+    if (need_hyp) {
+        const double alpha[3] = {0.75, 0.6, 0.3};
+        double *d_s0 = (double *)scratch(ctx, "fs_hyp0", sizeof(double) * nb);
+        double *d_s1 = (double *)scratch(ctx, "fs_hyp1", sizeof(double) * nb);
+        d_dhyp = (double *)scratch(ctx, "fs_dhyp", sizeof(double) * nb);
+        hyp_block_action(ctx, old, alpha, d_s0);
+        hyp_block_action(ctx, prop, alpha, d_s1);
+        block_lincomb(ctx, 1.0, d_s1, -1.0, d_s0, 0.0, nullptr, d_dhyp);
+    }
+    // HYP level: Delta_b = b0 dS_w,b + b1 dS_HYP,b, decision counter (step, 5, b)
+    const int *d_mask = nullptr;
+    int n_hyp = -1;
+    if (prm->hyp_level) {
+        double *d_dl = (double *)scratch(ctx, "fs_dhl", sizeof(double) * nb);
+        block_lincomb(ctx, prm->hyp_beta[0], d_dsw, prm->hyp_beta[1], d_dhyp, 0.0, nullptr, d_dl);
+        double *d_hs5 = (double *)scratch(ctx, "fs_hs5", sizeof(double) * (nb + 1));
+        int *d_acc5 = (int *)scratch(ctx, "fs_acc5", sizeof(int) * nb);
+        decide(ctx, d_dl, nb, 1, per_block ? 1 : 0, prm->seed, prm->step, 5, 0.0, nullptr, 0.0, d_hs5, d_acc5);
+        std::vector<int> h5(nb);
+        cuda_check(cudaMemcpyAsync(h5.data(), d_acc5, sizeof(int) * nb, cudaMemcpyDeviceToHost, ctx->stream), "l5");
+        cuda_check(cudaStreamSynchronize(ctx->stream), "l5");
+        n_hyp = 0;
+        for (int v : h5) n_hyp += v;
+        d_mask = d_acc5;
+    }
     r_lvl.reset();  // pop before the next push (NVTX ranges nest as a stack)
     r_lvl.reset(new Range("learned level"));
     // learned level (before level 1): h_b, accept with min{1, exp(-h_b)}
-    const int *d_mask = nullptr;
     double *d_h = nullptr;
     int n_learned = -1;
     if (prm->learned) {
@@ -771,7 +808,7 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         float_to_double(ctx, hf, d_h, nb);
         int *d_acc3 = (int *)scratch(ctx, "fs_acc3", sizeof(int) * nb);
         double *d_hs = (double *)scratch(ctx, "fs_hsum", sizeof(double) * (nb + 1));
-        decide(ctx, d_h, nb, 1, 1, prm->seed, prm->step, 3, 0.0, nullptr, 0.0, d_hs, d_acc3);
+        decide(ctx, d_h, nb, 1, 1, prm->seed, prm->step, 3, 0.0, nullptr, 0.0, d_hs, d_acc3, d_mask);
         std::vector<int> h3(nb);
         cuda_check(cudaMemcpyAsync(h3.data(), d_acc3, sizeof(int) * nb, cudaMemcpyDeviceToHost, ctx->stream), "l3");
         cuda_check(cudaStreamSynchronize(ctx->stream), "l3");
@@ -802,26 +839,29 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
     // level 1: block det ratios (blocks that passed the learned level)
     double *d_db = (double *)scratch(ctx, "fs_dblk", sizeof(double) * nb * N1);
     long long iters = 0;
-    if (n_learned != 0)
+    const int n_pass = n_learned >= 0 ? n_learned : n_hyp;  // -1: every block
+    if (n_pass != 0)
         iters = block_level(ctx, e0, eN, N1, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol, prm->inner_prec,
                             d_db, d_mask);
     else
         cuda_check(cudaMemsetAsync(d_db, 0, sizeof(double) * nb * N1, ctx->stream), "dblk");
     double *d_dsum = (double *)scratch(ctx, "fs_dsum", sizeof(double) * (nb + 1));
     int *d_acc = (int *)scratch(ctx, "fs_acc", sizeof(int) * nb);
-    // per-block extra term: beta_block dS_w,b (App. C) minus the learned h_b
+    // per-block extra term: beta_block dS_w,b + beta_block_hyp dS_HYP,b
+    // (App. C) minus the learned h_b
     const double *d_extra = d_h;
     double coef = -1.0;
-    if (prm->beta_block != 0.0) {
-        double *d_ds = (double *)scratch(ctx, "fs_dsw", sizeof(double) * nb);
+    if (prm->beta_block != 0.0 || prm->beta_block_hyp != 0.0) {
         double *d_ex = (double *)scratch(ctx, "fs_extra", sizeof(double) * nb);
-        block_action_change(ctx, old, prop, d_ds);
-        block_extra(ctx, d_ds, prm->beta_block, d_h, d_ex);
+        block_lincomb(ctx, prm->beta_block, prm->beta_block != 0.0 ? d_dsw : nullptr, prm->beta_block_hyp,
+                      prm->beta_block_hyp != 0.0 ? d_dhyp : nullptr, -1.0, d_h, d_ex);
         d_extra = d_ex;
         coef = 1.0;
     }
     decide(ctx, d_db, nb, N1, per_block ? 1 : 0, prm->seed, prm->step, PSMS_LEVEL_BLOCK, 0.0, d_extra, coef, d_dsum,
            d_acc, d_mask);
+    if (!per_block && n_hyp == 0)  // one decision on the sum: a rejected HYP level rejects the step
+        cuda_check(cudaMemsetAsync(d_acc, 0, sizeof(int) * nb, ctx->stream), "reject");
     merge_blocks(ctx, old, prop, mid, d_acc);
     std::vector<double> hd(nb + 1);
     std::vector<int> ha(nb);
@@ -863,6 +903,17 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
             cuda_check(cudaStreamSynchronize(ctx->stream), "plaq");
             dglob += prm->beta_global * (-(hp[0] - hp[1]) / 3.0);
         }
+        if (prm->beta_global_hyp != 0.0) {
+            // S_HYP changes on the accepted blocks only (it factorises over blocks)
+            std::vector<double> hh(nb);
+            cuda_check(cudaMemcpyAsync(hh.data(), d_dhyp, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream),
+                       "dS_HYP");
+            cuda_check(cudaStreamSynchronize(ctx->stream), "dS_HYP");
+            double sh = 0.0;
+            for (int b = 0; b < nb; ++b)
+                if (ha[b]) sh += hh[b];
+            dglob += prm->beta_global_hyp * sh;
+        }
         if (!std::isfinite(dglob)) fail(PSMS_ESPECTRUM, "non-finite global estimate");
         const double u = uniforms(prm->seed, TAG_ACCEPT, prm->step, PSMS_LEVEL_GLOBAL, 0, 0).u[0];
         accg = (dglob <= 0.0 || u < std::exp(-dglob)) ? 1 : 0;
@@ -892,6 +943,7 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         res->hb_failed = failed;
         res->n_accept_learned = n_learned;
         res->gf_steps = gf_steps;
+        res->n_accept_hyp = n_hyp;
     }
     if (delta_block_out)
         for (int b = 0; b < nb; ++b) delta_block_out[b] = hd[b];
