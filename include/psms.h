@@ -80,7 +80,7 @@ enum {
 };
 
 /* Estimator levels / modes of psms_logdet_ratio. */
-enum { PSMS_LEVEL_BLOCK = 1, PSMS_LEVEL_GLOBAL = 2 };
+enum { PSMS_LEVEL_BLOCK = 1, PSMS_LEVEL_GLOBAL = 2, PSMS_LEVEL_SUB = 4 };
 enum { PSMS_EST_INTERP = 0, PSMS_EST_INDEPENDENT = 1 };
 
 typedef struct psms_ctx psms_ctx;
@@ -161,6 +161,10 @@ typedef struct {
     double hyp_beta[2];
     double beta_block_hyp;
     double beta_global_hyp;
+    /* recursive decomposition (psms_set_outer_blocks): stage 2 with n_sub
+       interpolation steps (0: off) and the coefficient of dS_w           */
+    int n_sub;
+    double beta_sub;
 } psms_filter_params;
 
 typedef struct {
@@ -175,6 +179,7 @@ typedef struct {
     int n_accept_learned;  /* blocks passing the learned level (-1: no level)  */
     long long gf_steps;    /* gauge-fixing steps summed over blocks            */
     int n_accept_hyp;      /* blocks passing the HYP level (-1: no level)      */
+    int n_accept_sub;      /* outer blocks accepted at stage 2 (-1: no stage)  */
 } psms_filter_result;
 
 typedef struct {
@@ -467,6 +472,32 @@ psms_status psms_autotune(psms_ctx *ctx, int enable, int block_variant);
  * psms_filter_params.beta_block multiplies.  FP64, deterministic;
  * synchronises the context's stream. */
 psms_status psms_block_action_change(psms_ctx *ctx, int field_old, int field_new, double *ds_host);
+
+/* ---- recursive domain decomposition (Eq. (ddrec), the 5-step filter) --------
+ * psms_set_outer_blocks: outer blocks of extents outer[4] tiled by the
+ * context's blocks (outer = NULL or outer[0] = 0: off).  Each outer extent
+ * must be an even multiple of the block extent and divide the lattice
+ * extent an even number of times (PSMS_EINVAL otherwise).  With outer
+ * blocks set:
+ *  - psms_logdet_ratio(level = PSMS_LEVEL_SUB) estimates, for every outer
+ *    block b, ln |det D-hat_b(U) / det D-hat_b(U')|^2 with D-hat_b the Schur
+ *    complement of b's black and white blocks (Dirichlet on b's faces):
+ *    Eq. (staccN) with M_i = (1 - P_b Q_b(U_{i+1}))^-1 (1 - P_b Q_b(U_i)) on
+ *    range(P_b), P_b the projector onto the faces of black blocks that lie
+ *    inside b; noise stream level 4; delta_out[b*n + i], b the lexicographic
+ *    outer block index;
+ *  - psms_logdet_ratio(level = PSMS_LEVEL_GLOBAL) uses the Schur complement
+ *    of the outer decomposition;
+ *  - psms_filter_step with n_sub >= 1 runs the filter with one level of
+ *    recursion (Eq. (4step)): after the block level, every outer block with
+ *    an accepted block is accepted with min{1, exp(-Delta_b)},
+ *    Delta_b = beta_sub sum dS_w (its accepted blocks) + the SUB estimate
+ *    between U and the field after the block level (counter (step, 4, b);
+ *    one decision on the sum for block extents <= 2); a rejected outer block
+ *    restores all its blocks; the global level then uses the outer blocks.
+ *    Not combined with the learned, HYP or gauge-fixing options
+ *    (PSMS_EINVAL). */
+psms_status psms_set_outer_blocks(psms_ctx *ctx, const int *outer);
 
 /* ---- HYP-smeared links and the block HYP plaquette action (App. C, Sec. 5) ----
  * One level of HYP smearing of gauge slot `field`: three steps, each a

@@ -26,13 +26,13 @@ __all__ = [
     "psms_block_krylov", "SOLVER_CGNR", "SOLVER_BICGSTAB", "psms_level_covariance", "psms_level_coefficients",
     "psms_hyp_smear", "psms_hyp_block_action", "psms_block_action_change",
     "PREC_F64", "PREC_F32", "PREC_BF16", "OP_FULL", "OP_BLOCKS", "ACTIVE_BLOCKS", "ACTIVE_ALL",
-    "LEVEL_BLOCK", "LEVEL_GLOBAL", "EST_INTERP", "EST_INDEPENDENT",
+    "LEVEL_BLOCK", "LEVEL_GLOBAL", "LEVEL_SUB", "EST_INTERP", "EST_INDEPENDENT", "psms_set_outer_blocks",
 ]
 
 PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
 OP_FULL, OP_BLOCKS = -1, -2
 ACTIVE_BLOCKS, ACTIVE_ALL = 0, 1
-LEVEL_BLOCK, LEVEL_GLOBAL = 1, 2
+LEVEL_BLOCK, LEVEL_GLOBAL, LEVEL_SUB = 1, 2, 4
 EST_INTERP, EST_INDEPENDENT = 0, 1
 
 STATUS = {0: "PSMS_OK", 1: "PSMS_EINVAL", 2: "PSMS_ENOMEM", 3: "PSMS_ECUDA", 4: "PSMS_ENOCONV",
@@ -75,7 +75,7 @@ class FilterParams(ctypes.Structure):
                 ("learned", ctypes.c_int), ("gauge_fix", ctypes.c_int), ("relgf", RelGFParams),
                 ("proposal_field", ctypes.c_int), ("translate", ctypes.c_int), ("hyp_level", ctypes.c_int),
                 ("hyp_beta", ctypes.c_double * 2), ("beta_block_hyp", ctypes.c_double),
-                ("beta_global_hyp", ctypes.c_double)]
+                ("beta_global_hyp", ctypes.c_double), ("n_sub", ctypes.c_int), ("beta_sub", ctypes.c_double)]
 
 
 class FilterResult(ctypes.Structure):
@@ -83,7 +83,7 @@ class FilterResult(ctypes.Structure):
                 ("shift", ctypes.c_int * 4), ("delta_global", ctypes.c_double),
                 ("delta_block_sum", ctypes.c_double), ("solver_iters", ctypes.c_longlong),
                 ("hb_failed", ctypes.c_int), ("n_accept_learned", ctypes.c_int), ("gf_steps", ctypes.c_longlong),
-                ("n_accept_hyp", ctypes.c_int)]
+                ("n_accept_hyp", ctypes.c_int), ("n_accept_sub", ctypes.c_int)]
 
 
 class BlockProblem(ctypes.Structure):
@@ -148,6 +148,7 @@ _SIGS = {
     "psms_level_covariance": [_P, ctypes.c_longlong, _I, _P],
     "psms_hyp_smear": [_P, _I, _P, _P],
     "psms_block_action_change": [_P, _I, _I, _P],
+    "psms_set_outer_blocks": [_P, _P],
     "psms_hyp_block_action": [_P, _I, _P, _P],
     "psms_level_coefficients": [_I, _P, _P, _P, _P],
 }
@@ -207,6 +208,7 @@ class Context:
         self.kappa = kappa
         self.n_fields = n_fields
         self.V = int(np.prod(dims))
+        self.outer = None  # outer blocks of the recursive decomposition
 
     def check(self, st):
         if st:
@@ -303,18 +305,30 @@ def psms_solve(ctx, field, op, b_dev, x_dev, tol, maxit, inner_prec):
 
 def psms_logdet_ratio(ctx, level, field_old, field_new, n, mode, seed, counter, tol, inner_prec):
     nb = int(np.prod([d // b for d, b in zip(ctx.dims, ctx.block)]))
-    size = nb * n if level == LEVEL_BLOCK else n
+    if level == LEVEL_SUB:
+        outer = getattr(ctx, "outer", None)
+        if outer is None:
+            raise ValueError("LEVEL_SUB needs outer blocks (psms_set_outer_blocks)")
+        nb = int(np.prod([d // b for d, b in zip(ctx.dims, outer)]))
+    size = nb * n if level in (LEVEL_BLOCK, LEVEL_SUB) else n
     out = (_D * size)()
     ctx.check(ctx.lib.psms_logdet_ratio(ctx.handle, level, field_old, field_new, int(n), mode, int(seed),
                                         int(counter), float(tol), inner_prec, out))
     a = np.frombuffer(out, dtype=np.float64).copy()
-    return a.reshape(nb, n) if level == LEVEL_BLOCK else a
+    return a.reshape(nb, n) if level in (LEVEL_BLOCK, LEVEL_SUB) else a
+
+
+def psms_set_outer_blocks(ctx, outer):
+    """Outer blocks of the recursive decomposition (None: off)."""
+    arr = None if outer is None else (_I * 4)(*[int(v) for v in outer])
+    ctx.check(ctx.lib.psms_set_outer_blocks(ctx.handle, arr))
+    ctx.outer = None if outer is None else tuple(int(v) for v in outer)
 
 
 def psms_filter_step(ctx, field, *, beta0, n_iter=1, n_or=0, n_block=4, n_global=4, beta_block=0.0,
                      beta_global=0.0, global_level=True, tol=1e-10, inner_prec=PREC_F64, seed=0, step=0,
                      learned=False, gauge_fix=None, proposal_field=-1, translate=True, hyp_level=None,
-                     beta_block_hyp=0.0, beta_global_hyp=0.0):
+                     beta_block_hyp=0.0, beta_global_hyp=0.0, n_sub=0, beta_sub=0.0):
     """gauge_fix: None (off) or a dict of relative gauge-fixing parameters
     (alpha0, alpha_min, dalpha, theta_tol, max_iter, prec; {} = defaults).
     proposal_field: -1 (domain sweep) or the slot of an external proposal.
@@ -324,7 +338,7 @@ def psms_filter_step(ctx, field, *, beta0, n_iter=1, n_or=0, n_block=4, n_global
                      float(beta_global), int(bool(global_level)), float(tol), int(inner_prec), int(seed), int(step),
                      int(bool(learned)), int(gauge_fix is not None), _relgf(**(gauge_fix or {})),
                      int(proposal_field), int(bool(translate)), int(hyp_level is not None), (_D * 2)(*hb),
-                     float(beta_block_hyp), float(beta_global_hyp))
+                     float(beta_block_hyp), float(beta_global_hyp), int(n_sub), float(beta_sub))
     r = FilterResult()
     nb = int(np.prod([d // b for d, b in zip(ctx.dims, ctx.block)]))
     db = (_D * nb)()
@@ -333,7 +347,7 @@ def psms_filter_step(ctx, field, *, beta0, n_iter=1, n_or=0, n_block=4, n_global
     return {"n_blocks": r.n_blocks, "n_accept_blocks": r.n_accept_blocks, "accept_global": bool(r.accept_global),
             "shift": tuple(r.shift), "delta_global": r.delta_global, "delta_block_sum": r.delta_block_sum,
             "solver_iters": r.solver_iters, "hb_failed": r.hb_failed, "n_accept_learned": r.n_accept_learned,
-            "gf_steps": r.gf_steps, "n_accept_hyp": r.n_accept_hyp,
+            "gf_steps": r.gf_steps, "n_accept_hyp": r.n_accept_hyp, "n_accept_sub": r.n_accept_sub,
             "delta_block": np.frombuffer(db, dtype=np.float64).copy(),
             "accept_block": np.frombuffer(ab, dtype=np.int32).astype(bool)}
 

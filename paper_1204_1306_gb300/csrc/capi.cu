@@ -18,6 +18,7 @@
 #include "gaugefix.hpp"
 #include "hyp.hpp"
 #include "block_action.hpp"
+#include "outer.hpp"
 #include "mlp.hpp"
 #include "solver.hpp"
 
@@ -443,6 +444,12 @@ psms_status psms_hyp_block_action(psms_ctx *ctx, int field, const double *alpha,
     PSMS_CATCH(ctx)
 }
 
+psms_status psms_set_outer_blocks(psms_ctx *ctx, const int *outer) {
+    PSMS_TRY(ctx)
+    set_outer(ctx, outer);
+    PSMS_CATCH(ctx)
+}
+
 psms_status psms_block_action_change(psms_ctx *ctx, int field_old, int field_new, double *ds_host) {
     PSMS_TRY(ctx)
     check_field(ctx, field_old);
@@ -645,12 +652,17 @@ psms_status psms_logdet_ratio(psms_ctx *ctx, int level, int field_old, int field
         double *d = (double *)scratch(ctx, "ld_delta", sizeof(double) * nb * n);
         block_level(ctx, ctx->U64[field_old], ctx->U64[field_new], n, mode, seed, counter, tol, inner_prec, d);
         cuda_check(cudaMemcpyAsync(delta_out, d, sizeof(double) * nb * n, cudaMemcpyDeviceToHost, ctx->stream), "out");
+    } else if (level == PSMS_LEVEL_GLOBAL && has_outer(ctx)) {
+        outer_global_level(ctx, ctx->U64[field_old], ctx->U64[field_new], n, mode, seed, counter, tol, inner_prec,
+                           delta_out);
     } else if (level == PSMS_LEVEL_GLOBAL) {
         double *d = (double *)scratch(ctx, "ld_delta", sizeof(double) * n);
         global_level(ctx, ctx->U64[field_old], ctx->U64[field_new], n, mode, seed, counter, tol, inner_prec, d);
         cuda_check(cudaMemcpyAsync(delta_out, d, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream), "out");
+    } else if (level == PSMS_LEVEL_SUB) {
+        sub_level(ctx, ctx->U64[field_old], ctx->U64[field_new], n, mode, seed, counter, tol, inner_prec, delta_out);
     } else {
-        fail(PSMS_EINVAL, "level must be PSMS_LEVEL_BLOCK or PSMS_LEVEL_GLOBAL");
+        fail(PSMS_EINVAL, "level must be PSMS_LEVEL_BLOCK, PSMS_LEVEL_GLOBAL or PSMS_LEVEL_SUB");
     }
     cuda_check(cudaStreamSynchronize(ctx->stream), "logdet sync");
     PSMS_CATCH(ctx)
@@ -760,7 +772,15 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
     r_lvl.reset(new Range("HYP level"));
     // per-block action changes of the proposal: dS_w,b (beta_block and the
     // HYP level) and dS_HYP,b (the HYP terms, App. C)
-    const bool need_dsw = prm->beta_block != 0.0 || prm->hyp_level;
+    const bool recursive = prm->n_sub > 0;
+    if (recursive) {
+        if (!has_outer(ctx)) fail(PSMS_EINVAL, "n_sub >= 1 needs outer blocks (psms_set_outer_blocks)");
+        if (prm->learned || prm->hyp_level || prm->gauge_fix || prm->beta_block_hyp != 0.0 ||
+            prm->beta_global_hyp != 0.0)
+            fail(PSMS_EINVAL, "the recursive filter does not combine with the learned, HYP or gauge-fixing options");
+        if (!std::isfinite(prm->beta_sub)) fail(PSMS_EINVAL, "beta_sub must be finite");
+    }
+    const bool need_dsw = prm->beta_block != 0.0 || prm->hyp_level || (recursive && prm->beta_sub != 0.0);
     const bool need_hyp = prm->hyp_level || prm->beta_block_hyp != 0.0 || prm->beta_global_hyp != 0.0;
     double *d_dsw = nullptr, *d_dhyp = nullptr;
     if (need_dsw) {
@@ -874,6 +894,74 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         nacc += ha[b];
         dsum += hd[b];
     }
+    // stage 2 of the recursive decomposition (Eq. (4step)): the Schur
+    // complements of the outer blocks that changed, between U and the field
+    // after the block level
+    int n_sub_acc = -1;
+    if (recursive) {
+        r_lvl.reset();
+        r_lvl.reset(new Range("stage 2: outer-block Schur ratios"));
+        const int no = n_outer(ctx);
+        std::vector<int> oo(nb);  // outer block of every block (lexicographic indices)
+        for (int b = 0; b < nb; ++b) {
+            int B[4], q = b;
+            for (int m = 3; m >= 0; --m) {
+                B[m] = q % g.nb[m];
+                q /= g.nb[m];
+            }
+            int o = 0;
+            for (int m = 0; m < 4; ++m) o = o * (g.L[m] / ctx->outer[m]) + B[m] * g.l[m] / ctx->outer[m];
+            oo[b] = o;
+        }
+        std::vector<char> changed(no, 0);
+        bool any = false;
+        for (int b = 0; b < nb; ++b)
+            if (ha[b]) changed[oo[b]] = 1, any = true;
+        std::vector<double> dsub(no, 0.0);
+        if (any) {
+            std::vector<double> hs((long long)no * prm->n_sub);
+            iters += sub_level(ctx, old, mid, prm->n_sub, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol,
+                               prm->inner_prec, hs.data());
+            for (int o = 0; o < no; ++o)
+                if (changed[o])
+                    for (int i = 0; i < prm->n_sub; ++i) dsub[o] += hs[(long long)o * prm->n_sub + i];
+        }
+        if (prm->beta_sub != 0.0) {
+            std::vector<double> dw(nb);
+            cuda_check(cudaMemcpyAsync(dw.data(), d_dsw, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream),
+                       "dS_w");
+            cuda_check(cudaStreamSynchronize(ctx->stream), "dS_w");
+            std::vector<double> acc_ds(no, 0.0);
+            for (int b = 0; b < nb; ++b)
+                if (ha[b]) acc_ds[oo[b]] += dw[b];
+            for (int o = 0; o < no; ++o) dsub[o] += prm->beta_sub * acc_ds[o];
+        }
+        for (int o = 0; o < no; ++o)
+            if (!std::isfinite(dsub[o])) fail(PSMS_ESPECTRUM, "non-finite outer-block estimate");
+        std::vector<char> acc_o(no, 1);
+        if (per_block) {
+            for (int o = 0; o < no; ++o)
+                if (changed[o]) {
+                    const double u = uniforms(prm->seed, TAG_ACCEPT, prm->step, PSMS_LEVEL_SUB, (uint64_t)o, 0).u[0];
+                    acc_o[o] = (dsub[o] <= 0.0 || u < std::exp(-dsub[o])) ? 1 : 0;
+                }
+        } else if (any) {
+            double tot = 0.0;
+            for (int o = 0; o < no; ++o) tot += dsub[o];
+            const double u = uniforms(prm->seed, TAG_ACCEPT, prm->step, PSMS_LEVEL_SUB, 0, 0).u[0];
+            const char a = (tot <= 0.0 || u < std::exp(-tot)) ? 1 : 0;
+            for (int o = 0; o < no; ++o) acc_o[o] = a;
+        }
+        n_sub_acc = 0;
+        for (int o = 0; o < no; ++o) n_sub_acc += changed[o] && acc_o[o];
+        nacc = 0;
+        for (int b = 0; b < nb; ++b) {
+            ha[b] = ha[b] && acc_o[oo[b]];
+            nacc += ha[b];
+        }
+        cuda_check(cudaMemcpyAsync(d_acc, ha.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, ctx->stream), "acc2");
+        merge_blocks(ctx, old, prop, mid, d_acc);
+    }
     r_lvl.reset();  // pop before the next push (NVTX ranges nest as a stack)
     r_lvl.reset(new Range("level 2: global det ratio"));
     // level 2: global Schur det ratio (a field equal to the old one has
@@ -888,11 +976,17 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
             merge_blocks(ctx, old, e0, e0, d_acc);
             merge_blocks(ctx, old, eN, eN, d_acc);
         }
-        iters += global_level(ctx, e0, prm->gauge_fix ? eN : mid, N2, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol,
-                              prm->inner_prec, d_dg);
         std::vector<double> hg(N2);
-        cuda_check(cudaMemcpyAsync(hg.data(), d_dg, sizeof(double) * N2, cudaMemcpyDeviceToHost, ctx->stream), "dg");
-        cuda_check(cudaStreamSynchronize(ctx->stream), "dg");
+        if (recursive) {
+            iters += outer_global_level(ctx, old, mid, N2, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol,
+                                        prm->inner_prec, hg.data());
+        } else {
+            iters += global_level(ctx, e0, prm->gauge_fix ? eN : mid, N2, PSMS_EST_INTERP, prm->seed, prm->step,
+                                  prm->tol, prm->inner_prec, d_dg);
+            cuda_check(cudaMemcpyAsync(hg.data(), d_dg, sizeof(double) * N2, cudaMemcpyDeviceToHost, ctx->stream),
+                       "dg");
+            cuda_check(cudaStreamSynchronize(ctx->stream), "dg");
+        }
         for (int i = 0; i < N2; ++i) dglob += hg[i];
         if (prm->beta_global != 0.0) {
             double *pd = (double *)scratch(ctx, "fs_plaq", sizeof(double) * 2);
@@ -944,6 +1038,7 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         res->n_accept_learned = n_learned;
         res->gf_steps = gf_steps;
         res->n_accept_hyp = n_hyp;
+        res->n_accept_sub = n_sub_acc;
     }
     if (delta_block_out)
         for (int b = 0; b < nb; ++b) delta_block_out[b] = hd[b];

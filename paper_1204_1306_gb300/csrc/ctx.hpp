@@ -67,6 +67,7 @@ struct psms_ctx {
     int forced_hop_variant = -1;  // -1: autotuned; else the variant index (mod the variant count)
     int full_solver = 1;          // inner Krylov method of whole-lattice solves: 0 CGNR, 1 BiCGStab
     int block_krylov = 0;         // inner Krylov method of block solves: 0 CGNR, 1 BiCGStab
+    int outer[4] = {0, 0, 0, 0};  // outer blocks of the recursive decomposition (0: none)
     // autotuned block-solver variant per (precision, block size, batched)
     std::map<long long, int> block_variant;
     int forced_block_variant = -1;

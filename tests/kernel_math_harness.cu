@@ -7,6 +7,7 @@
 
 #include "../paper_1204_1306_gb300/csrc/block_action.cuh"
 #include "../paper_1204_1306_gb300/csrc/hyp.cuh"
+#include "../paper_1204_1306_gb300/csrc/outer.cuh"
 
 using psms::hyp::M;
 
@@ -140,5 +141,32 @@ extern "C" void block_change_host(const double *U0, const double *U1, const int 
             q /= g.nb[m];
         }
         out[b] = psms::act::block_change_partial(ld, g, B, b, 0, 1);
+    }
+}
+
+// faces / colour of the recursive decomposition for every site of the
+// lattice L with blocks l and outer blocks B: out[4 * s + (0..3)] =
+// (colour, number of faces, mu of the last face, its sign)
+extern "C" void outer_faces_host(const int *L, const int *l, const int *B, int mode, int *out) {
+    const long long V = (long long)L[0] * L[1] * L[2] * L[3];
+    for (long long s = 0; s < V; ++s) {
+        int x[4];
+        coords(L, s, x);
+        int fmu, ft;
+        const int nf = psms::outer::faces(mode, x, l, B, fmu, ft);
+        out[4 * s + 0] = psms::outer::colour(mode, x, l, B);
+        out[4 * s + 1] = nf;
+        out[4 * s + 2] = fmu;
+        out[4 * s + 3] = ft;
+    }
+}
+
+// 1 where the link (x, mu) crosses an outer face
+extern "C" void outer_crossing_host(const int *L, const int *B, int *out) {
+    const long long V = (long long)L[0] * L[1] * L[2] * L[3];
+    for (long long s = 0; s < V; ++s) {
+        int x[4];
+        coords(L, s, x);
+        for (int mu = 0; mu < 4; ++mu) out[4 * s + mu] = psms::outer::crossing(x, mu, B) ? 1 : 0;
     }
 }

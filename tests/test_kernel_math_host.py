@@ -12,7 +12,7 @@ import subprocess
 import numpy as np
 import pytest
 
-from oracle import filter as ofilter, gauge, hyp, lattice
+from oracle import dirac, filter as ofilter, gauge, hyp, lattice
 from tests import seeded
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -27,7 +27,8 @@ def harness(tmp_path_factory):
     subprocess.run([nvcc, "-O2", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-o", out,
                     os.path.join(HERE, "kernel_math_harness.cu")], check=True, capture_output=True)
     lib = ctypes.CDLL(out)
-    for f in (lib.hyp_smear_host, lib.hyp_block_action_host, lib.hyp_project_host, lib.block_change_host):
+    for f in (lib.hyp_smear_host, lib.hyp_block_action_host, lib.hyp_project_host, lib.block_change_host,
+              lib.outer_faces_host, lib.outer_crossing_host):
         f.restype = None
     return lib
 
@@ -93,3 +94,42 @@ def test_block_action_change_matches_oracle(harness, dims, block, which):
     ref = ofilter.per_block_action_change(U, Up, geom)
     assert np.abs(out - ref).max() < 1e-11
     assert abs(out.sum() - (gauge.wilson_action(Up) - gauge.wilson_action(U))) < 1e-9
+
+
+def _projector_from_faces(info):
+    """Per-site spin projector from (colour, faces, mu, sign) as the kernels
+    apply it: (1 + t gamma_mu)/2 for one face, 1 for more, 0 otherwise."""
+    from oracle.gamma import GAMMA
+    P = np.zeros(info.shape[:-1] + (4, 4), dtype=np.complex128)
+    col, nf, mu, t = (info[..., k] for k in range(4))
+    one = (col == 0) & (nf == 1)
+    for m in range(4):
+        for sg in (1, -1):
+            sel = one & (mu == m) & (t == sg)
+            P[sel] = 0.5 * (np.eye(4) + sg * GAMMA[m])
+    P[(col == 0) & (nf >= 2)] = np.eye(4)
+    return P
+
+
+@pytest.mark.parametrize("dims,outer,inner", [((16, 8, 8, 8), (8, 4, 4, 4), (4, 2, 2, 2)),
+                                              ((8, 8, 8, 8), (4, 4, 4, 4), (2, 2, 2, 2))])
+def test_outer_projectors_and_masks_match_oracle(harness, dims, outer, inner):
+    """The recursive decomposition's face logic: the SUB projector equals
+    the oracle's P_b on every outer block, the OUTER projector the oracle's
+    projector of the outer blocks, and the masked links are exactly those
+    whose hop leaves an outer block."""
+    from oracle import recursive
+    nest = recursive.Nested(dims, outer, inner)
+    L, l, B = (ctypes.c_int * 4)(*dims), (ctypes.c_int * 4)(*inner), (ctypes.c_int * 4)(*outer)
+    info = np.empty(dims + (4,), dtype=np.int32)
+    harness.outer_faces_host(L, l, B, 0, info.ctypes.data)
+    Psub = _projector_from_faces(info)
+    Pb = recursive.sub_projector(nest)
+    for b in range(nest.outer.n_blocks):
+        assert np.array_equal(dirac.extract_block(Psub, nest.outer, b), Pb)
+    harness.outer_faces_host(L, l, B, 1, info.ctypes.data)
+    assert np.array_equal(_projector_from_faces(info), nest.outer.projector())
+    cr = np.empty(dims + (4,), dtype=np.int32)
+    harness.outer_crossing_host(L, B, cr.ctypes.data)
+    for mu in range(4):
+        assert np.array_equal(cr[..., mu].astype(bool), ~nest.outer.fwd_intra(mu))
