@@ -458,6 +458,75 @@ def batch_only(args):
     print(json.dumps(measure_batch(ps, torch, steps=args.steps, warmup=args.warmup)), flush=True)
 
 
+def levels_only(args):
+    """The parametrised levels (App. C) and the recursive decomposition on the
+    16^4 workload: the block HYP action (one smearing + per-block plaquette
+    sums, FP64), the per-block plaquette-action change, the outer-block
+    Schur estimates (8^4 outer blocks of 4^4 blocks), and filter steps with
+    the HYP level and with one level of recursion, each timed with CUDA
+    events after warm-up.  An auxiliary measurement (one JSON line)."""
+    import torch
+
+    import paper_1204_1306_gb300 as ps
+    from paper_1204_1306_gb300 import build as _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    wl = WORKLOADS["16^4"]
+    seed = SEED + 77
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ctx = _new_chain(ps, torch, wl, seed)
+    ps.psms_gauge_copy(ctx, 1, 0)
+    ps.psms_gauge_sweep(ctx, 1, ps.ACTIVE_BLOCKS, wl["n_iter"], wl["n_or"], wl["beta"], seed, 9 << 20)
+    V = float(np.prod(wl["dims"]))
+    out = {"workload": "16^4", "data": "synthetic"}
+    ms = timed(lambda: ps.psms_hyp_block_action(ctx, 0), max(3, args.steps))
+    flop = 55e3 * V  # per-site model of one smearing (fat links dominate)
+    out["hyp_block_action"] = {"ms": round(ms, 3), "model_gflops_fp64": round(flop / ms * 1e-6, 1),
+                               "frac_of_nominal_fp64": round(flop / ms * 1e-9 / 1.25, 4)}
+    ms = timed(lambda: ps.psms_block_action_change(ctx, 0, 1), max(3, args.steps))
+    out["block_action_change"] = {"ms": round(ms, 3)}
+    ps.psms_set_outer_blocks(ctx, (8, 8, 8, 8))
+    n_sub = 12
+    ms = timed(lambda: ps.psms_logdet_ratio(ctx, ps.LEVEL_SUB, 0, 1, n_sub, ps.EST_INTERP, seed, 0, wl["tol"],
+                                            ps.PREC_F32), 1)
+    n_o = int(np.prod([d // 8 for d in wl["dims"]]))
+    out["sub_level"] = {"outer_blocks": n_o, "n": n_sub, "ms": round(ms, 2),
+                        "estimates_per_s": round(n_o * n_sub / ms * 1e3, 1)}
+    ps.psms_set_outer_blocks(ctx, None)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    prm = _filter_prm(ps, wl, seed)
+    for name, extra in (("hyp_level", dict(hyp_level=(-0.0196, 0.0963), beta_block_hyp=-0.0614)),
+                        ("recursive_5step", dict(n_sub=n_sub))):
+        chain = _new_chain(ps, torch, wl, seed)
+        kw = dict(prm, **extra)
+        if name == "recursive_5step":
+            ps.psms_set_outer_blocks(chain, (8, 8, 8, 8))
+            kw.pop("gauge_fix", None)
+        _timed_steps(ps, torch, chain, kw, ps.PREC_F32, False, args.warmup, flush)
+        recs, ms = _timed_steps(ps, torch, chain, kw, ps.PREC_F32, False, args.steps, flush, step0=1000)
+        out[name] = {"ms_per_step": round(ms / args.steps, 2), "accepted_updates": _accepted(recs),
+                     "blocks_accepted": int(sum(r["n_accept_blocks"] for r in recs)),
+                     "n_accept_hyp": [r["n_accept_hyp"] for r in recs],
+                     "n_accept_sub": [r["n_accept_sub"] for r in recs]}
+        chain.close()
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def measure_estimators(ps, torch, wl, seed, n=12, reps=3):
     """Det-ratio estimates per second on the workload lattice: the block
     level (all blocks x n interpolation steps) and the global level (n
@@ -840,6 +909,8 @@ def main():
     ap.add_argument("--dw-only", action="store_true", help="stand-alone D_w measurement only")
     ap.add_argument("--solve-only", action="store_true", help="single-system solver measurement only")
     ap.add_argument("--batch-only", action="store_true", help="multi-lattice batched block solves (8^4, 12^4, 16^3x32)")
+    ap.add_argument("--levels-only", action="store_true",
+                    help="parametrised levels and the recursive decomposition on 16^4 (auxiliary line)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -853,6 +924,8 @@ def main():
         batch_only(args)
     elif args.learned_only:
         learned_only(args)
+    elif args.levels_only:
+        levels_only(args)
     else:
         our_arm(args)
 
