@@ -49,6 +49,8 @@ class FilterParams:
     global_level: bool = True
     learned: object = None   # MLP parameter dict (oracle.mlp) or None
     gauge_fix: object = None  # relative gauge fixing (Sec. 4.2): dict of oracle.gaugefix parameters, or None
+    exact_block: bool = False    # block level with exact determinants (Sec. 3, dense LU) instead of Eq. (staccN)
+    beta_global_blockdet: float = 0.0  # coefficient of the block-determinant action at the global level (App. C)
     hyp_level: object = None  # (beta_1^(0), beta_1^(1)) of the HYP plaquette level (App. C), or None
     beta_block_hyp: float = 0.0   # beta^(1) of the block level (HYP action)
     beta_global_hyp: float = 0.0  # beta^(1) of the global level (HYP action)
@@ -80,6 +82,25 @@ def stochastic_acceptance(lam):
 
 def accept(delta, u):
     return bool(delta <= 0.0 or u < np.exp(-delta))
+
+
+def block_logdet(U, geom, b, kappa):
+    """ln|det D_b(U)| of one Dirichlet block, by LU of its dense matrix."""
+    from .dirac import apply_D_open, dense_matrix, extract_block
+    Ub = extract_block(U, geom, b)
+    Db = dense_matrix(lambda v: apply_D_open(Ub, v, kappa), geom.Vb, geom.block + (4, 3))
+    return float(np.linalg.slogdet(Db)[1])
+
+
+def exact_block_change(U, Up, geom, kappa, blocks=None):
+    """Change of the block-determinant action S_b = -2 ln|det D_b| (so that
+    exp(-S_b) is the block's fermion weight |det D_b|^2, N_f = 2) from U to
+    U' for the listed blocks (others 0): the exact value of the stochastic
+    block estimate, E[exp(-Delta_b)] = exp(-dS_b) (Sec. 4.1)."""
+    out = np.zeros(geom.n_blocks)
+    for b in (range(geom.n_blocks) if blocks is None else blocks):
+        out[b] = 2.0 * (block_logdet(U, geom, b, kappa) - block_logdet(Up, geom, b, kappa))
+    return out
 
 
 def per_block_action_change(U, Up, geom):
@@ -116,6 +137,13 @@ def _merge(U, V, acc_b, geom, active):
 
 def filter_step(U, geom, prm, seed, step, h_override=None, gf_override=None, proposal=None, translate=True):
     """Returns (new field, record dict).
+
+    With prm.exact_block the block level uses the exact change of the
+    block-determinant action (dense LU, the paper's own method for blocks of
+    up to about 6^4 sites, Sec. 3) instead of the stochastic estimate; that
+    action may then also enter the global level with beta_global_blockdet
+    (Tables 1 and 2 carry such a coefficient; App. C allows it only for
+    exactly evaluated actions).
 
     With prm.hyp_level = (b0, b1) a parametrised level precedes the others
     (App. C; the first filter of Tables 1 and 2): per block,
@@ -186,7 +214,12 @@ def filter_step(U, geom, prm, seed, step, h_override=None, gf_override=None, pro
 
     blocks = [b for b in range(geom.n_blocks) if passed[b]]
     d_blk = np.zeros(geom.n_blocks)
-    if blocks:
+    ds_det = None
+    if prm.exact_block or prm.beta_global_blockdet != 0.0:
+        ds_det = exact_block_change(U, Unew, geom, prm.kappa)
+    if blocks and prm.exact_block:
+        d_blk[blocks] = ds_det[blocks]
+    elif blocks:
         d_all = block_level(E0, EN, geom, prm.kappa, prm.n_block, seed, step, tol=prm.tol, blocks=blocks)
         d_blk[blocks] = d_all[blocks].sum(axis=1)
     if prm.beta_block != 0.0:
@@ -218,6 +251,8 @@ def filter_step(U, geom, prm, seed, step, h_override=None, gf_override=None, pro
             d += prm.beta_global * (wilson_action(Umid) - wilson_action(U))
         if prm.beta_global_hyp != 0.0:
             d += prm.beta_global_hyp * float(ds_hyp[acc_b].sum())
+        if prm.beta_global_blockdet != 0.0:
+            d += prm.beta_global_blockdet * float(ds_det[acc_b].sum())
         acc_g = accept(d, philox.accept_uniform(seed, step, 2, 0))
         rec["delta_global"] = d
         rec["delta_global_terms"] = dg

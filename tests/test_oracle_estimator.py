@@ -200,3 +200,52 @@ def test_stochastic_acceptance_formula():
     u = philox.uniforms(13, philox.TAG_ACCEPT, philox.make_ctr(2, 3, np.arange(ns)))[:, 0]
     acc = np.mean([ofilter.accept(d, x) for d, x in zip(delta, u)])
     assert abs(acc - p_fwd) < 5 * np.sqrt(p_fwd * (1 - p_fwd) / ns)
+
+
+# --- exact block level ------------------------------------------------------------
+
+def test_exact_block_change_is_the_estimator_target():
+    """dS_b = 2 (ln|det D_b(U)| - ln|det D_b(U')|) equals -ln det(M^dag M)^-1
+    with M = D_b(U')^-1 D_b(U) (the target of E[e^-Delta], Sec. 4.1), and
+    summing it over blocks with the exact Schur factor gives the change of
+    ln|det D|^2 (Eq. (ddfactor))."""
+    geom = lattice.Geometry((4, 4, 2, 2), (2, 2, 1, 1))
+    U = gauge.generate_links(geom.dims, 0.4, 81)
+    Up = _perturbed(U, 0.2, 82)
+    ds = ofilter.exact_block_change(U, Up, geom, K)
+    for b in (0, 5):
+        shape = geom.block + (4, 3)
+        A = _dense(lambda v: dirac.apply_D_open(dirac.extract_block(U, geom, b), v, K), geom.Vb, shape)
+        B = _dense(lambda v: dirac.apply_D_open(dirac.extract_block(Up, geom, b), v, K), geom.Vb, shape)
+        M = np.linalg.solve(B, A)
+        assert abs(ds[b] - np.linalg.slogdet(M.conj().T @ M)[1]) < 1e-10
+    black = np.repeat(geom.black_sites().reshape(-1), 12)
+
+    def logdets(F):
+        D = _dense(lambda v: dirac.apply_D(F, v, K), geom.V, geom.dims + (4, 3))
+        Dbb, Dbw = D[np.ix_(black, black)], D[np.ix_(black, ~black)]
+        Dwb, Dww = D[np.ix_(~black, black)], D[np.ix_(~black, ~black)]
+        schur = np.eye(black.sum()) - np.linalg.solve(Dbb, Dbw @ np.linalg.solve(Dww, Dwb))
+        return np.linalg.slogdet(D)[1], np.linalg.slogdet(schur)[1]
+
+    (f0, s0), (f1, s1) = logdets(U), logdets(Up)
+    assert abs(ds.sum() + 2 * (s0 - s1) - 2 * (f0 - f1)) < 1e-9
+
+
+def test_filter_with_exact_block_level():
+    """The block level's Delta_b is the exact dS_b (plus the beta terms), and
+    the global level adds beta_global_blockdet times dS_b of the accepted
+    blocks."""
+    geom = lattice.Geometry((4, 4, 4, 4), (2, 2, 2, 2))
+    U = gauge.generate_links(geom.dims, 0.5, 83)
+    prm = dict(kappa=K, beta0=5.3, n_iter=1, n_or=1, n_global=2, tol=1e-12, exact_block=True, beta_block=0.2)
+    U2, rec = ofilter.filter_step(U, geom, ofilter.FilterParams(**prm), 17, 1)
+    Unew, _, _ = gauge.domain_sweep(U, geom, 5.3, 1, 1, 17, 1 * ofilter.SWEEP_STRIDE)
+    ds = ofilter.exact_block_change(U, Unew, geom, K)
+    ref = ds + 0.2 * ofilter.per_block_action_change(U, Unew, geom)
+    assert np.abs(rec["delta_block"] - ref).max() < 1e-10
+    U3, rec3 = ofilter.filter_step(U, geom, ofilter.FilterParams(beta_global_blockdet=-0.07, **prm), 17, 1)
+    assert np.array_equal(rec3["accept_block"], rec["accept_block"])
+    assert rec["accept_block"].any()
+    extra = -0.07 * ds[rec["accept_block"]].sum()
+    assert abs(rec3["delta_global"] - rec["delta_global"] - extra) < 1e-9
