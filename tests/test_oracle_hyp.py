@@ -6,7 +6,6 @@ enumeration, and the block factorisation of the action."""
 import itertools
 
 import numpy as np
-import pytest
 from scipy.optimize import minimize
 
 from oracle import gauge, hyp, lattice
@@ -25,8 +24,8 @@ def _su3_exp(omega):
 # --- projection -----------------------------------------------------------------
 
 def test_projection_properties():
-    g = np.random.default_rng(1)
-    M = seeded.complex_matrix(3, 2)[None].repeat(1, 0)
+    """SU(3) output, SU(3) and positive multiples of it fixed, gauge
+    covariance Proj[G M H^dag] = G Proj[M] H^dag."""
     M = np.stack([seeded.complex_matrix(3, s) for s in range(20)])
     W = hyp.project_su3(M)
     assert np.abs(W @ dag(W) - np.eye(3)).max() < 1e-14
