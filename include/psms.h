@@ -79,8 +79,11 @@ enum {
     PSMS_ACTIVE_ALL = 1     /* every link (pure-gauge thermalisation)          */
 };
 
-/* Estimator levels / modes of psms_logdet_ratio. */
-enum { PSMS_LEVEL_BLOCK = 1, PSMS_LEVEL_GLOBAL = 2, PSMS_LEVEL_SUB = 4 };
+/* Estimator levels / modes of psms_logdet_ratio.  PSMS_LEVEL_GLOBAL always
+ * means the global Schur complement of the context's blocks;
+ * PSMS_LEVEL_SUB and PSMS_LEVEL_OUTER_GLOBAL need outer blocks
+ * (psms_set_outer_blocks). */
+enum { PSMS_LEVEL_BLOCK = 1, PSMS_LEVEL_GLOBAL = 2, PSMS_LEVEL_SUB = 4, PSMS_LEVEL_OUTER_GLOBAL = 6 };
 enum { PSMS_EST_INTERP = 0, PSMS_EST_INDEPENDENT = 1 };
 
 typedef struct psms_ctx psms_ctx;
@@ -281,6 +284,23 @@ psms_status psms_logdet_ratio(psms_ctx *ctx, int level, int field_old, int field
 psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params *prm,
                              psms_filter_result *res, double *delta_block_out, int *accept_block_out);
 
+/* Per-block records of the last psms_filter_step on ctx, for callers that
+ * check or log what a level decided on.  what selects the record and n the
+ * capacity of out (host):
+ *   PSMS_REC_H          n_blocks: the learned level's h_b as the step used it
+ *                       (0 where the level is off);
+ *   PSMS_REC_DELTA_HYP  n_blocks: Delta_b of the HYP level (0 when off);
+ *   PSMS_REC_ACCEPT_BLOCK n_blocks: level-1 decisions (1 / 0) before stage 2;
+ *   PSMS_REC_DELTA_SUB  n_outer: Delta_b of stage 2 per outer block (0 for
+ *                       outer blocks that were not estimated);
+ *   PSMS_REC_ACCEPT_SUB n_outer: stage-2 decisions per outer block (1 / 0).
+ * Blocks in lexicographic order.  Returns the record's length in *n_out.
+ * PSMS_EINVAL for an unknown record, n too small, or no step with that
+ * record yet. */
+enum { PSMS_REC_H = 0, PSMS_REC_DELTA_HYP = 1, PSMS_REC_ACCEPT_BLOCK = 2, PSMS_REC_DELTA_SUB = 3,
+       PSMS_REC_ACCEPT_SUB = 4 };
+psms_status psms_filter_record(psms_ctx *ctx, int what, double *out, int n, int *n_out);
+
 /* ---- batched block solves over several lattices ---------------------------
  * All Dirichlet blocks x all right-hand sides of several lattices (each its
  * own context, possibly of different sizes; same device) solved by one
@@ -429,6 +449,11 @@ psms_status psms_full_solver(psms_ctx *ctx, int kind);
  * choice gives identical results).  PSMS_EINVAL for another kind. */
 psms_status psms_block_krylov(psms_ctx *ctx, int kind);
 
+/* Largest number of interpolation steps (systems) batched into one launch
+ * by the estimators; 0 (default) sizes the batches from a device-memory
+ * estimate.  Any value gives the same estimates.  PSMS_EINVAL for n < 0. */
+psms_status psms_max_chunk(psms_ctx *ctx, int n);
+
 /* Force the Wilson-hop kernel variant (register cap and, for the whole
  * lattice, the branch-free specialisation; 8 variants for FP32 links in the
  * whole-lattice mode, 4 otherwise, used modulo their count) instead of the
@@ -486,15 +511,20 @@ psms_status psms_block_action_change(psms_ctx *ctx, int field_old, int field_new
  *    range(P_b), P_b the projector onto the faces of black blocks that lie
  *    inside b; noise stream level 4; delta_out[b*n + i], b the lexicographic
  *    outer block index;
- *  - psms_logdet_ratio(level = PSMS_LEVEL_GLOBAL) uses the Schur complement
- *    of the outer decomposition;
+ *  - psms_logdet_ratio(level = PSMS_LEVEL_OUTER_GLOBAL) estimates the
+ *    global Schur complement of the outer decomposition (Eq. (ddfactor)
+ *    with the outer blocks as the blocks; noise stream and decision
+ *    counter of PSMS_LEVEL_GLOBAL), delta_out[i];
  *  - psms_filter_step with n_sub >= 1 runs the filter with one level of
  *    recursion (Eq. (4step)): after the block level, every outer block with
  *    an accepted block is accepted with min{1, exp(-Delta_b)},
  *    Delta_b = beta_sub sum dS_w (its accepted blocks) + the SUB estimate
  *    between U and the field after the block level (counter (step, 4, b);
- *    one decision on the sum for block extents <= 2); a rejected outer block
- *    restores all its blocks; the global level then uses the outer blocks.
+ *    one decision on the sum for block extents <= 2); an outer block none
+ *    of whose accepted blocks changed a link has Delta_b = 0 and is not
+ *    estimated (its det D-hat_b is unchanged, Eq. (ddrec)); a rejected
+ *    outer block restores all its blocks; the global level then uses the
+ *    outer blocks (PSMS_LEVEL_OUTER_GLOBAL).
  *    Not combined with the learned, HYP or gauge-fixing options
  *    (PSMS_EINVAL). */
 psms_status psms_set_outer_blocks(psms_ctx *ctx, const int *outer);

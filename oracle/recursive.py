@@ -197,7 +197,7 @@ class RecursiveParams:
     global_level: bool = True
 
 
-def filter_step(U, nest, prm, seed, step, proposal=None, translate=True):
+def filter_step(U, nest, prm, seed, step, proposal=None, translate=True, skip_unchanged=False):
     """One step of the filter with one level of recursion (Eq. (4step)).
     Returns (new field, record dict).
 
@@ -207,7 +207,8 @@ def filter_step(U, nest, prm, seed, step, proposal=None, translate=True):
         (counter (step, 1, b')), as in the filter without recursion:
         decisions per inner block when every inner extent is >= 3, else one
         decision on the sum (counter (step, 1, 0));
-     2) per outer block b whose links changed in stage 1:
+     2) per outer block b holding an accepted inner block whose links
+        changed in stage 1:
         Delta_b = beta_sub sum_{b' in b} dS_w,b' + stage-2 estimate between U
         and the field after stage 1 (counter (step, LEVEL_SUB, b)); outer
         blocks without a change keep Delta_b = 0 and are not drawn.  Per
@@ -216,7 +217,11 @@ def filter_step(U, nest, prm, seed, step, proposal=None, translate=True):
         gets all its old links back;
      3) Delta = beta_global dS_w + global Schur estimate with the outer
         blocks (counter (step, 2, 0)) between U and the field after stage 2;
-     4) translation by a random vector."""
+     4) translation by a random vector.
+
+    skip_unchanged: stage 1 estimates only the inner blocks whose links
+    changed and gives the others Delta = 0, the exact value of their
+    estimate (M = 1); for external proposals that move few blocks."""
     inner, outer = nest.inner, nest.outer
     active = inner.active_links()
     if proposal is None:
@@ -225,8 +230,19 @@ def filter_step(U, nest, prm, seed, step, proposal=None, translate=True):
         Unew, failed = np.array(proposal, copy=True), 0
     per_block = min(inner.block) >= 3
 
+    link_changed = np.any(U != Unew, axis=(-1, -2))            # [dims, 4]
+    block_moved = np.zeros(inner.n_blocks, dtype=bool)
+    np.logical_or.at(block_moved, inner.block_index.ravel(), link_changed.any(axis=-1).ravel())
+
     # stage 1: inner blocks
-    d_in = block_level(U, Unew, inner, prm.kappa, prm.n_block, seed, step, tol=prm.tol).sum(axis=1)
+    if skip_unchanged:
+        d_in = np.zeros(inner.n_blocks)
+        moved = [b for b in range(inner.n_blocks) if block_moved[b]]
+        if moved:
+            d_in[moved] = block_level(U, Unew, inner, prm.kappa, prm.n_block, seed, step, tol=prm.tol,
+                                      blocks=moved)[moved].sum(axis=1)
+    else:
+        d_in = block_level(U, Unew, inner, prm.kappa, prm.n_block, seed, step, tol=prm.tol).sum(axis=1)
     ds_in = per_block_action_change(U, Unew, inner) if (prm.beta_block or prm.beta_sub) else np.zeros(inner.n_blocks)
     d_in = d_in + prm.beta_block * ds_in
     if per_block:
@@ -235,10 +251,12 @@ def filter_step(U, nest, prm, seed, step, proposal=None, translate=True):
         acc_in = np.full(inner.n_blocks, accept(d_in.sum(), philox.accept_uniform(seed, step, 1, 0)))
     U1 = _merge(U, Unew, acc_in, inner, active)
 
-    # stage 2: Schur complements of the outer blocks
+    # stage 2: Schur complements of the outer blocks.  An outer block changes
+    # when one of its accepted inner blocks changed a link; det D-hat_b of
+    # the others is unchanged (it depends on the links inside b only).
     changed = np.zeros(outer.n_blocks, dtype=bool)
     for b in range(inner.n_blocks):
-        if acc_in[b]:
+        if acc_in[b] and block_moved[b]:
             changed[nest.outer_of_inner[b]] = True
     d_sub = np.zeros(outer.n_blocks)
     blocks = [b for b in range(outer.n_blocks) if changed[b]]

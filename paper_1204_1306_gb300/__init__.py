@@ -27,12 +27,15 @@ __all__ = [
     "psms_hyp_smear", "psms_hyp_block_action", "psms_block_action_change",
     "PREC_F64", "PREC_F32", "PREC_BF16", "OP_FULL", "OP_BLOCKS", "ACTIVE_BLOCKS", "ACTIVE_ALL",
     "LEVEL_BLOCK", "LEVEL_GLOBAL", "LEVEL_SUB", "EST_INTERP", "EST_INDEPENDENT", "psms_set_outer_blocks",
+    "LEVEL_OUTER_GLOBAL", "psms_filter_record", "psms_max_chunk", "REC_H", "REC_DELTA_HYP", "REC_ACCEPT_BLOCK",
+    "REC_DELTA_SUB", "REC_ACCEPT_SUB",
 ]
 
 PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
 OP_FULL, OP_BLOCKS = -1, -2
 ACTIVE_BLOCKS, ACTIVE_ALL = 0, 1
-LEVEL_BLOCK, LEVEL_GLOBAL, LEVEL_SUB = 1, 2, 4
+LEVEL_BLOCK, LEVEL_GLOBAL, LEVEL_SUB, LEVEL_OUTER_GLOBAL = 1, 2, 4, 6
+REC_H, REC_DELTA_HYP, REC_ACCEPT_BLOCK, REC_DELTA_SUB, REC_ACCEPT_SUB = 0, 1, 2, 3, 4
 EST_INTERP, EST_INDEPENDENT = 0, 1
 
 STATUS = {0: "PSMS_OK", 1: "PSMS_EINVAL", 2: "PSMS_ENOMEM", 3: "PSMS_ECUDA", 4: "PSMS_ENOCONV",
@@ -151,6 +154,8 @@ _SIGS = {
     "psms_set_outer_blocks": [_P, _P],
     "psms_hyp_block_action": [_P, _I, _P, _P],
     "psms_level_coefficients": [_I, _P, _P, _P, _P],
+    "psms_filter_record": [_P, _I, _P, _I, ctypes.POINTER(_I)],
+    "psms_max_chunk": [_P, _I],
 }
 
 _lib = None
@@ -316,6 +321,22 @@ def psms_logdet_ratio(ctx, level, field_old, field_new, n, mode, seed, counter, 
                                         int(counter), float(tol), inner_prec, out))
     a = np.frombuffer(out, dtype=np.float64).copy()
     return a.reshape(nb, n) if level in (LEVEL_BLOCK, LEVEL_SUB) else a
+
+
+def psms_filter_record(ctx, what):
+    """Per-block record `what` (REC_*) of the last psms_filter_step."""
+    n = ctypes.c_int()
+    nb = int(np.prod([d // b for d, b in zip(ctx.dims, ctx.block)]))
+    outer = getattr(ctx, "outer", None)
+    no = nb if outer is None else int(np.prod([d // b for d, b in zip(ctx.dims, outer)]))
+    out = np.zeros(max(nb, no), dtype=np.float64)
+    ctx.check(ctx.lib.psms_filter_record(ctx.handle, int(what), out.ctypes.data, len(out), ctypes.byref(n)))
+    return out[:n.value].copy()
+
+
+def psms_max_chunk(ctx, n):
+    """Cap on interpolation steps batched per estimator launch (0: automatic)."""
+    ctx.check(ctx.lib.psms_max_chunk(ctx.handle, int(n)))
 
 
 def psms_set_outer_blocks(ctx, outer):

@@ -652,7 +652,7 @@ psms_status psms_logdet_ratio(psms_ctx *ctx, int level, int field_old, int field
         double *d = (double *)scratch(ctx, "ld_delta", sizeof(double) * nb * n);
         block_level(ctx, ctx->U64[field_old], ctx->U64[field_new], n, mode, seed, counter, tol, inner_prec, d);
         cuda_check(cudaMemcpyAsync(delta_out, d, sizeof(double) * nb * n, cudaMemcpyDeviceToHost, ctx->stream), "out");
-    } else if (level == PSMS_LEVEL_GLOBAL && has_outer(ctx)) {
+    } else if (level == PSMS_LEVEL_OUTER_GLOBAL) {
         outer_global_level(ctx, ctx->U64[field_old], ctx->U64[field_new], n, mode, seed, counter, tol, inner_prec,
                            delta_out);
     } else if (level == PSMS_LEVEL_GLOBAL) {
@@ -662,7 +662,8 @@ psms_status psms_logdet_ratio(psms_ctx *ctx, int level, int field_old, int field
     } else if (level == PSMS_LEVEL_SUB) {
         sub_level(ctx, ctx->U64[field_old], ctx->U64[field_new], n, mode, seed, counter, tol, inner_prec, delta_out);
     } else {
-        fail(PSMS_EINVAL, "level must be PSMS_LEVEL_BLOCK, PSMS_LEVEL_GLOBAL or PSMS_LEVEL_SUB");
+        fail(PSMS_EINVAL, "level must be PSMS_LEVEL_BLOCK, PSMS_LEVEL_GLOBAL, PSMS_LEVEL_SUB or "
+                          "PSMS_LEVEL_OUTER_GLOBAL");
     }
     cuda_check(cudaStreamSynchronize(ctx->stream), "logdet sync");
     PSMS_CATCH(ctx)
@@ -743,6 +744,7 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
     const long long nel = 36 * g.V;
     const size_t fb = sizeof(double2) * nel;
     double2 *cur = ctx->U64[field];
+    for (auto *v : {&ctx->rec_h, &ctx->rec_dhyp, &ctx->rec_acc1, &ctx->rec_dsub, &ctx->rec_acc_sub}) v->clear();
     double2 *old = (double2 *)scratch(ctx, "fs_old", fb);
     double2 *prop = (double2 *)scratch(ctx, "fs_prop", fb);
     double2 *mid = (double2 *)scratch(ctx, "fs_mid", fb);
@@ -806,7 +808,11 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         int *d_acc5 = (int *)scratch(ctx, "fs_acc5", sizeof(int) * nb);
         decide(ctx, d_dl, nb, 1, per_block ? 1 : 0, prm->seed, prm->step, 5, 0.0, nullptr, 0.0, d_hs5, d_acc5);
         std::vector<int> h5(nb);
+        ctx->rec_dhyp.assign(nb, 0.0);
         cuda_check(cudaMemcpyAsync(h5.data(), d_acc5, sizeof(int) * nb, cudaMemcpyDeviceToHost, ctx->stream), "l5");
+        cuda_check(cudaMemcpyAsync(ctx->rec_dhyp.data(), d_dl, sizeof(double) * nb, cudaMemcpyDeviceToHost,
+                                   ctx->stream),
+                   "l5");
         cuda_check(cudaStreamSynchronize(ctx->stream), "l5");
         n_hyp = 0;
         for (int v : h5) n_hyp += v;
@@ -830,7 +836,10 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         double *d_hs = (double *)scratch(ctx, "fs_hsum", sizeof(double) * (nb + 1));
         decide(ctx, d_h, nb, 1, 1, prm->seed, prm->step, 3, 0.0, nullptr, 0.0, d_hs, d_acc3, d_mask);
         std::vector<int> h3(nb);
+        ctx->rec_h.assign(nb, 0.0);
         cuda_check(cudaMemcpyAsync(h3.data(), d_acc3, sizeof(int) * nb, cudaMemcpyDeviceToHost, ctx->stream), "l3");
+        cuda_check(cudaMemcpyAsync(ctx->rec_h.data(), d_h, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream),
+                   "l3");
         cuda_check(cudaStreamSynchronize(ctx->stream), "l3");
         n_learned = 0;
         for (int v : h3) n_learned += v;
@@ -894,6 +903,9 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         nacc += ha[b];
         dsum += hd[b];
     }
+    if (ctx->rec_h.empty()) ctx->rec_h.assign(nb, 0.0);
+    if (ctx->rec_dhyp.empty()) ctx->rec_dhyp.assign(nb, 0.0);
+    ctx->rec_acc1.assign(ha.begin(), ha.end());
     // stage 2 of the recursive decomposition (Eq. (4step)): the Schur
     // complements of the outer blocks that changed, between U and the field
     // after the block level
@@ -913,10 +925,17 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
             for (int m = 0; m < 4; ++m) o = o * (g.L[m] / ctx->outer[m]) + B[m] * g.l[m] / ctx->outer[m];
             oo[b] = o;
         }
+        // an outer block changes when one of its accepted blocks changed a
+        // link; the others keep det D-hat_b (Eq. (ddrec)) and Delta_b = 0
+        int *d_chg = (int *)scratch(ctx, "fs_chg", sizeof(int) * nb);
+        block_changed(ctx, old, prop, d_chg);
+        std::vector<int> chg(nb);
+        cuda_check(cudaMemcpyAsync(chg.data(), d_chg, sizeof(int) * nb, cudaMemcpyDeviceToHost, ctx->stream), "chg");
+        cuda_check(cudaStreamSynchronize(ctx->stream), "chg");
         std::vector<char> changed(no, 0);
         bool any = false;
         for (int b = 0; b < nb; ++b)
-            if (ha[b]) changed[oo[b]] = 1, any = true;
+            if (ha[b] && chg[b]) changed[oo[b]] = 1, any = true;
         std::vector<double> dsub(no, 0.0);
         if (any) {
             std::vector<double> hs((long long)no * prm->n_sub);
@@ -954,6 +973,8 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         }
         n_sub_acc = 0;
         for (int o = 0; o < no; ++o) n_sub_acc += changed[o] && acc_o[o];
+        ctx->rec_dsub.assign(dsub.begin(), dsub.end());
+        ctx->rec_acc_sub.assign(acc_o.begin(), acc_o.end());
         nacc = 0;
         for (int b = 0; b < nb; ++b) {
             ha[b] = ha[b] && acc_o[oo[b]];
@@ -1044,6 +1065,31 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         for (int b = 0; b < nb; ++b) delta_block_out[b] = hd[b];
     if (accept_block_out)
         for (int b = 0; b < nb; ++b) accept_block_out[b] = ha[b];
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_filter_record(psms_ctx *ctx, int what, double *out, int n, int *n_out) {
+    PSMS_TRY(ctx)
+    const std::vector<double> *v = nullptr;
+    switch (what) {
+        case PSMS_REC_H: v = &ctx->rec_h; break;
+        case PSMS_REC_DELTA_HYP: v = &ctx->rec_dhyp; break;
+        case PSMS_REC_ACCEPT_BLOCK: v = &ctx->rec_acc1; break;
+        case PSMS_REC_DELTA_SUB: v = &ctx->rec_dsub; break;
+        case PSMS_REC_ACCEPT_SUB: v = &ctx->rec_acc_sub; break;
+        default: fail(PSMS_EINVAL, "unknown filter record");
+    }
+    if (v->empty()) fail(PSMS_EINVAL, "no filter step has produced this record");
+    if (n_out) *n_out = (int)v->size();
+    if (!out || n < (int)v->size()) fail(PSMS_EINVAL, "record output too small");
+    for (size_t i = 0; i < v->size(); ++i) out[i] = (*v)[i];
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_max_chunk(psms_ctx *ctx, int n) {
+    PSMS_TRY(ctx)
+    if (n < 0) fail(PSMS_EINVAL, "the chunk cap must be >= 0");
+    ctx->max_chunk = n;
     PSMS_CATCH(ctx)
 }
 

@@ -68,6 +68,10 @@ struct psms_ctx {
     int full_solver = 1;          // inner Krylov method of whole-lattice solves: 0 CGNR, 1 BiCGStab
     int block_krylov = 0;         // inner Krylov method of block solves: 0 CGNR, 1 BiCGStab
     int outer[4] = {0, 0, 0, 0};  // outer blocks of the recursive decomposition (0: none)
+    int max_chunk = 0;            // cap on systems per estimator launch (0: from the memory estimate)
+    // per-block records of the last filter step (psms_filter_record); empty
+    // until a step has produced them
+    std::vector<double> rec_h, rec_dhyp, rec_acc1, rec_dsub, rec_acc_sub;
     // autotuned block-solver variant per (precision, block size, batched)
     std::map<long long, int> block_variant;
     int forced_block_variant = -1;

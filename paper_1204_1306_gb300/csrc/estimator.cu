@@ -143,13 +143,12 @@ __global__ void block_delta_kernel(const BlockInfo *binfo, const double *a, cons
     delta[(long long)binfo[r].lex * N + i0 + i] = a[t] - b[t];
 }
 
-// number of interpolation steps batched per launch, from a per-system
-// device-memory estimate (bytes per lattice site) and a 64 GB budget
-static int chunk_size(psms_ctx *c, int N, double bytes_per_site) {
+int chunk_size(psms_ctx *c, int N, double bytes_per_site) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     double budget = std::min(64e9, 0.45 * (double)tot);
     int k = (int)(budget / (bytes_per_site * (double)c->g.V));
+    if (c->max_chunk > 0) k = std::min(k, c->max_chunk);
     return std::max(1, std::min(N, k));
 }
 

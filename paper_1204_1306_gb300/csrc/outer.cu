@@ -120,6 +120,24 @@ __global__ void __launch_bounds__(kNormNT) rank_norm_kernel(Geom g, const double
     }
 }
 
+// flag[lex(r)] = 1 when any link starting in block r differs between U and Up
+constexpr int kChgNT = 128;
+__global__ void __launch_bounds__(kChgNT) block_changed_kernel(Geom g, const BlockInfo *binfo, const double2 *U,
+                                                               const double2 *Up, int *flag) {
+    const int r = blockIdx.x;
+    int diff = 0;
+    for (int t = threadIdx.x; t < 2 * g.Vbh && !diff; t += kChgNT) {
+        const int p = t >= g.Vbh ? 1 : 0;
+        const long long s = (long long)p * g.Vh + (long long)r * g.Vbh + (t - p * g.Vbh);
+        for (int e = 0; e < 36 && !diff; ++e) {
+            const double2 a = U[(long long)e * g.V + s], b = Up[(long long)e * g.V + s];
+            diff = (a.x != b.x) || (a.y != b.y);
+        }
+    }
+    diff = __syncthreads_or(diff);
+    if (threadIdx.x == 0) flag[binfo[r].lex] = diff ? 1 : 0;
+}
+
 constexpr int NT = 128;
 
 void mask_links(psms_ctx *c, double2 *U, long long bs, int n_fields, int kind) {
@@ -234,14 +252,6 @@ void hop_all(psms_ctx *c, const double2 *U64, long long bs, int n, const double2
     h.in = View<void>{(void *)in, V, 0, fs};
     h.out = View<void>{out, V, 0, fs};
     hop_launch(c, h);
-}
-
-int chunk_of(psms_ctx *c, int N, double bytes_per_site) {
-    size_t fr = 0, tot = 0;
-    cudaMemGetInfo(&fr, &tot);
-    const double budget = std::min(64e9, 0.45 * (double)tot);
-    const int k = (int)(budget / (bytes_per_site * (double)c->g.V));
-    return std::max(1, std::min(N, k));
 }
 
 // outer block (lexicographic over the outer blocks) of every inner rank
@@ -392,6 +402,11 @@ long long outer_global_chunk(psms_ctx *c, const double2 *U, const double2 *Up, i
 
 }  // namespace
 
+void block_changed(psms_ctx *c, const double2 *U, const double2 *Up, int *d_flag) {
+    block_changed_kernel<<<c->g.nblocks, kChgNT, 0, c->stream>>>(c->g, c->d_binfo, U, Up, d_flag);
+    PSMS_LAUNCH_CHECK("block_changed");
+}
+
 bool has_outer(const psms_ctx *c) { return c->outer[0] > 0; }
 
 int n_outer(const psms_ctx *c) {
@@ -418,7 +433,7 @@ void set_outer(psms_ctx *c, const int *B) {
 long long sub_level(psms_ctx *c, const double2 *U, const double2 *Up, int N, int mode, uint64_t seed,
                     uint64_t counter, double tol, int inner, double *h_delta) {
     if (!has_outer(c)) fail(PSMS_EINVAL, "no outer blocks set (psms_set_outer_blocks)");
-    const int ch = chunk_of(c, N, 2600.0);
+    const int ch = chunk_size(c, N, 2600.0);
     std::vector<double> h((long long)n_outer(c) * N, 0.0);
     long long tot = 0;
     for (int i0 = 0; i0 < N; i0 += ch)
@@ -430,7 +445,7 @@ long long sub_level(psms_ctx *c, const double2 *U, const double2 *Up, int N, int
 long long outer_global_level(psms_ctx *c, const double2 *U, const double2 *Up, int N, int mode, uint64_t seed,
                              uint64_t counter, double tol, int inner, double *h_delta) {
     if (!has_outer(c)) fail(PSMS_EINVAL, "no outer blocks set (psms_set_outer_blocks)");
-    const int ch = chunk_of(c, N, 4800.0);
+    const int ch = chunk_size(c, N, 4800.0);
     std::vector<double> h(N, 0.0);
     long long tot = 0;
     for (int i0 = 0; i0 < N; i0 += ch)

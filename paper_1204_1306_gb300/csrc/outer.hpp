@@ -7,6 +7,9 @@
 namespace psms {
 
 bool has_outer(const psms_ctx *c);
+// d_flag[b] (lexicographic block index) = 1 when a link starting in block b
+// differs between U and Up, else 0
+void block_changed(psms_ctx *c, const double2 *U, const double2 *Up, int *d_flag);
 int n_outer(const psms_ctx *c);
 // B = null or B[0] == 0 switches the outer level off
 void set_outer(psms_ctx *c, const int *B);

@@ -129,3 +129,31 @@ def test_unchanged_blocks_stay_unfixed():
     g1, g2, info = gaugefix.relative_gauge_fix(U, Up, geom)
     assert info["steps"][3] == 0 and np.all(np.delete(info["steps"], 3) > 0)
     assert np.array_equal(g1[keep], np.broadcast_to(np.eye(3), g1[keep].shape))
+
+
+def test_level2_endpoints_equal_fixing_the_merged_pair():
+    """The filter's level 2 interpolates between the gauge-fixed pair of
+    (U, U_mid), U_mid = U' on the accepted blocks and U elsewhere.  Blocks
+    decouple (every link touching an interior point lies in that point's
+    block), so that pair equals the level-1 endpoints merged on the accepted
+    blocks, which is how oracle.filter forms it: fixing (U, U_mid) directly
+    gives the same fields."""
+    from oracle.filter import _merge
+    geom = lattice.Geometry((8, 8, 8, 8), (4, 4, 4, 4))
+    U = gauge.generate_links(geom.dims, 0.4, 61)
+    Up, _, _ = gauge.domain_sweep(U, geom, 5.3, 1, 0, 62, 0)
+    acc = np.random.default_rng(63).random(geom.n_blocks) < 0.5
+    assert 0 < acc.sum() < geom.n_blocks
+    active = geom.active_links()
+    Umid = _merge(U, Up, acc, geom, active)
+    E0, EN, _ = gaugefix.fixed_pair(U, Up, geom, max_iter=200)
+    G0, GN = _merge(U, E0, acc, geom, active), _merge(U, EN, acc, geom, active)
+    F0, FN, info = gaugefix.fixed_pair(U, Umid, geom, max_iter=200)
+    assert np.abs(F0 - G0).max() < 1e-12
+    assert np.abs(FN - GN).max() < 1e-12
+    # the rejected blocks are not transformed, the accepted ones are
+    assert np.all(info["steps"][~acc] == 0)
+    assert np.all(info["steps"][acc] > 0)
+    # a mistake in the merge (accepted blocks taken from the unfixed U') fails
+    bad = _merge(U, Up, acc, geom, active)
+    assert np.abs(FN - bad).max() > 1e-3
