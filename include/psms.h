@@ -168,6 +168,16 @@ typedef struct {
        interpolation steps (0: off) and the coefficient of dS_w           */
     int n_sub;
     double beta_sub;
+    /* exact block level (Sec. 3: LU of the small blocks; Tables 1 and 2):
+       with exact_block = 1 the block level uses beta_block_det times the
+       exact change of S_b = -2 ln|det D_b| (psms_block_logdet) instead of
+       the stochastic estimate; beta_global_blockdet adds that action's
+       change on the accepted blocks to the global level (App. C allows
+       coefficients on exactly evaluated actions only).  Not combined with
+       the recursive decomposition. */
+    int exact_block;
+    double beta_block_det;
+    double beta_global_blockdet;
 } psms_filter_params;
 
 typedef struct {
@@ -498,6 +508,19 @@ psms_status psms_autotune(psms_ctx *ctx, int enable, int block_variant);
  * synchronises the context's stream. */
 psms_status psms_block_action_change(psms_ctx *ctx, int field_old, int field_new, double *ds_host);
 
+/* Exact ln|det D_b(U_field)| of every Dirichlet block (Sec. 3: the paper
+ * takes small-block determinants by LU), lexicographic block index, into
+ * out_host[n_blocks]: det D_b = A^{n_e} det(Dhat_b) with A = 4 + m0 and
+ * Dhat_b = A - D_oe D_eo / A the even-odd reduced block operator (n x n
+ * complex, n = 6 x block volume), factorised by batched FP64 LU with
+ * partial pivoting on the device.  Cost about (8/3) n^3 FP64 flop per block
+ * (1e10 for a 4^4 block); device memory n^2 x 16 B per block of a batch
+ * (batches sized from the free memory, psms_max_chunk caps them).
+ * PSMS_ESPECTRUM if a block operator is singular (non-finite result);
+ * PSMS_EINVAL for blocks of more than 1024 sites.  Synchronises the
+ * context's stream. */
+psms_status psms_block_logdet(psms_ctx *ctx, int field, double *out_host);
+
 /* ---- recursive domain decomposition (Eq. (ddrec), the 5-step filter) --------
  * psms_set_outer_blocks: outer blocks of extents outer[4] tiled by the
  * context's blocks (outer = NULL or outer[0] = 0: off).  Each outer extent
@@ -524,9 +547,11 @@ psms_status psms_block_action_change(psms_ctx *ctx, int field_old, int field_new
  *    of whose accepted blocks changed a link has Delta_b = 0 and is not
  *    estimated (its det D-hat_b is unchanged, Eq. (ddrec)); a rejected
  *    outer block restores all its blocks; the global level then uses the
- *    outer blocks (PSMS_LEVEL_OUTER_GLOBAL).
- *    Not combined with the learned, HYP or gauge-fixing options
- *    (PSMS_EINVAL). */
+ *    outer blocks (PSMS_LEVEL_OUTER_GLOBAL).  With the learned level the
+ *    inner blocks pass it first; with relative gauge fixing stage 2 and the
+ *    global level interpolate between the stage-1 endpoints merged on the
+ *    accepted inner blocks.  Not combined with the HYP options or the exact
+ *    block level (PSMS_EINVAL). */
 psms_status psms_set_outer_blocks(psms_ctx *ctx, const int *outer);
 
 /* ---- HYP-smeared links and the block HYP plaquette action (App. C, Sec. 5) ----
@@ -578,6 +603,10 @@ psms_status psms_hyp_block_action(psms_ctx *ctx, int field, const double *alpha,
 psms_status psms_level_covariance(const double *samples, long long n_samples, int n_actions, double *cov);
 psms_status psms_level_coefficients(int n_levels, const double *covs, const double *targets,
                                     const int *stochastic, double *beta);
+
+/* Device memory the context holds in scratch buffers (bytes, host output);
+ * it grows when a call needs more and is freed with the context. */
+psms_status psms_scratch_bytes(const psms_ctx *ctx, size_t *bytes);
 
 /* Number of CUDA kernels the library has launched in this process. */
 long long psms_kernel_launches(void);

@@ -50,6 +50,7 @@ class FilterParams:
     learned: object = None   # MLP parameter dict (oracle.mlp) or None
     gauge_fix: object = None  # relative gauge fixing (Sec. 4.2): dict of oracle.gaugefix parameters, or None
     exact_block: bool = False    # block level with exact determinants (Sec. 3, dense LU) instead of Eq. (staccN)
+    block_det_coef: float = 1.0  # coefficient of the exact block-determinant action at the block level (Table 1: 1.644)
     beta_global_blockdet: float = 0.0  # coefficient of the block-determinant action at the global level (App. C)
     hyp_level: object = None  # (beta_1^(0), beta_1^(1)) of the HYP plaquette level (App. C), or None
     beta_block_hyp: float = 0.0   # beta^(1) of the block level (HYP action)
@@ -98,8 +99,12 @@ def exact_block_change(U, Up, geom, kappa, blocks=None):
     U' for the listed blocks (others 0): the exact value of the stochastic
     block estimate, E[exp(-Delta_b)] = exp(-dS_b) (Sec. 4.1)."""
     out = np.zeros(geom.n_blocks)
+    # a block whose links did not change keeps its determinant: 0 exactly
+    moved = np.zeros(geom.n_blocks, dtype=bool)
+    np.logical_or.at(moved, geom.block_index.ravel(), np.any(U != Up, axis=(-1, -2, -3)).ravel())
     for b in (range(geom.n_blocks) if blocks is None else blocks):
-        out[b] = 2.0 * (block_logdet(U, geom, b, kappa) - block_logdet(Up, geom, b, kappa))
+        if moved[b]:
+            out[b] = 2.0 * (block_logdet(U, geom, b, kappa) - block_logdet(Up, geom, b, kappa))
     return out
 
 
@@ -138,11 +143,12 @@ def _merge(U, V, acc_b, geom, active):
 def filter_step(U, geom, prm, seed, step, h_override=None, gf_override=None, proposal=None, translate=True):
     """Returns (new field, record dict).
 
-    With prm.exact_block the block level uses the exact change of the
-    block-determinant action (dense LU, the paper's own method for blocks of
-    up to about 6^4 sites, Sec. 3) instead of the stochastic estimate; that
-    action may then also enter the global level with beta_global_blockdet
-    (Tables 1 and 2 carry such a coefficient; App. C allows it only for
+    With prm.exact_block the block level uses block_det_coef times the exact
+    change of the block-determinant action (dense LU, the paper's own method
+    for blocks of up to about 6^4 sites, Sec. 3) instead of the stochastic
+    estimate; that action may then also enter the global level with
+    beta_global_blockdet (Tables 1 and 2 carry coefficients at both levels,
+    summing to the action's target 1; App. C allows coefficients only on
     exactly evaluated actions).
 
     With prm.hyp_level = (b0, b1) a parametrised level precedes the others
@@ -218,7 +224,7 @@ def filter_step(U, geom, prm, seed, step, h_override=None, gf_override=None, pro
     if prm.exact_block or prm.beta_global_blockdet != 0.0:
         ds_det = exact_block_change(U, Unew, geom, prm.kappa)
     if blocks and prm.exact_block:
-        d_blk[blocks] = ds_det[blocks]
+        d_blk[blocks] = prm.block_det_coef * ds_det[blocks]
     elif blocks:
         d_all = block_level(E0, EN, geom, prm.kappa, prm.n_block, seed, step, tol=prm.tol, blocks=blocks)
         d_blk[blocks] = d_all[blocks].sum(axis=1)

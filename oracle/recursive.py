@@ -195,9 +195,12 @@ class RecursiveParams:
     beta_global: float = 0.0
     tol: float = 1e-13
     global_level: bool = True
+    learned: object = None    # MLP parameter dict (oracle.mlp) of the learned level before stage 1, or None
+    gauge_fix: object = None  # relative gauge fixing of the inner blocks (dict of oracle.gaugefix parameters), or None
 
 
-def filter_step(U, nest, prm, seed, step, proposal=None, translate=True, skip_unchanged=False):
+def filter_step(U, nest, prm, seed, step, proposal=None, translate=True, skip_unchanged=False, h_override=None,
+                gf_override=None):
     """One step of the filter with one level of recursion (Eq. (4step)).
     Returns (new field, record dict).
 
@@ -221,7 +224,18 @@ def filter_step(U, nest, prm, seed, step, proposal=None, translate=True, skip_un
 
     skip_unchanged: stage 1 estimates only the inner blocks whose links
     changed and gives the others Delta = 0, the exact value of their
-    estimate (M = 1); for external proposals that move few blocks."""
+    estimate (M = 1); for external proposals that move few blocks.
+
+    prm.learned (per-inner-block decisions only): the learned level of
+    oracle.filter precedes stage 1 -- h_b of the inner block (or
+    h_override), accepted with min{1, exp(-h_b)} (counter (step, 3, b));
+    stage 1 runs on the blocks that passed with Delta_b - h_b.
+    prm.gauge_fix (or gf_override = (g_1, g_2)): every interpolation runs
+    between relatively gauge-fixed endpoints (Sec. 4.2) of the inner
+    blocks' interiors: stage 1 between U^{g_1} and U'^{g_2}; stage 2 and
+    the global level between the fixed pair of (U, field after the stage
+    before), which (the inner blocks decouple) is the stage-1 pair merged
+    on the accepted inner blocks (U elsewhere)."""
     inner, outer = nest.inner, nest.outer
     active = inner.active_links()
     if proposal is None:
@@ -234,19 +248,36 @@ def filter_step(U, nest, prm, seed, step, proposal=None, translate=True, skip_un
     block_moved = np.zeros(inner.n_blocks, dtype=bool)
     np.logical_or.at(block_moved, inner.block_index.ravel(), link_changed.any(axis=-1).ravel())
 
+    # learned level (before stage 1)
+    passed = np.ones(inner.n_blocks, dtype=bool)
+    h = np.zeros(inner.n_blocks)
+    if prm.learned is not None:
+        from .mlp import antisym, pair_features
+        assert per_block
+        h = (antisym(prm.learned, pair_features(U, Unew, inner)) if h_override is None
+             else np.asarray(h_override, dtype=np.float64))
+        passed = np.array([accept(h[b], philox.accept_uniform(seed, step, 3, b)) for b in range(inner.n_blocks)])
+
+    # relatively gauge-fixed endpoints of the interpolations
+    E0, EN = U, Unew
+    if prm.gauge_fix is not None or gf_override is not None:
+        from .gaugefix import relative_gauge_fix, transform
+        g1, g2 = (relative_gauge_fix(U, Unew, inner, **prm.gauge_fix)[:2] if gf_override is None
+                  else gf_override)
+        E0, EN = transform(U, g1), transform(Unew, g2)
+    fixed = E0 is not U
+
     # stage 1: inner blocks
-    if skip_unchanged:
-        d_in = np.zeros(inner.n_blocks)
-        moved = [b for b in range(inner.n_blocks) if block_moved[b]]
-        if moved:
-            d_in[moved] = block_level(U, Unew, inner, prm.kappa, prm.n_block, seed, step, tol=prm.tol,
-                                      blocks=moved)[moved].sum(axis=1)
-    else:
-        d_in = block_level(U, Unew, inner, prm.kappa, prm.n_block, seed, step, tol=prm.tol).sum(axis=1)
+    todo = [b for b in range(inner.n_blocks) if passed[b] and (block_moved[b] or not skip_unchanged)]
+    d_in = np.zeros(inner.n_blocks)
+    if todo:
+        d_in[todo] = block_level(E0, EN, inner, prm.kappa, prm.n_block, seed, step, tol=prm.tol,
+                                 blocks=todo)[todo].sum(axis=1)
     ds_in = per_block_action_change(U, Unew, inner) if (prm.beta_block or prm.beta_sub) else np.zeros(inner.n_blocks)
-    d_in = d_in + prm.beta_block * ds_in
+    d_in = d_in + prm.beta_block * ds_in - h
     if per_block:
-        acc_in = np.array([accept(d_in[b], philox.accept_uniform(seed, step, 1, b)) for b in range(inner.n_blocks)])
+        acc_in = np.array([passed[b] and accept(d_in[b], philox.accept_uniform(seed, step, 1, b))
+                           for b in range(inner.n_blocks)])
     else:
         acc_in = np.full(inner.n_blocks, accept(d_in.sum(), philox.accept_uniform(seed, step, 1, 0)))
     U1 = _merge(U, Unew, acc_in, inner, active)
@@ -261,7 +292,10 @@ def filter_step(U, nest, prm, seed, step, proposal=None, translate=True, skip_un
     d_sub = np.zeros(outer.n_blocks)
     blocks = [b for b in range(outer.n_blocks) if changed[b]]
     if blocks:
-        d_all = sub_level(U, U1, nest, prm.kappa, prm.n_sub, seed, step, tol=prm.tol, blocks=blocks)
+        S0, S1 = U, U1
+        if fixed:
+            S0, S1 = _merge(U, E0, acc_in, inner, active), _merge(U, EN, acc_in, inner, active)
+        d_all = sub_level(S0, S1, nest, prm.kappa, prm.n_sub, seed, step, tol=prm.tol, blocks=blocks)
         d_sub[blocks] = d_all[blocks].sum(axis=1)
     if prm.beta_sub != 0.0:
         d_sub = d_sub + prm.beta_sub * np.bincount(nest.outer_of_inner, weights=ds_in * acc_in,
@@ -276,10 +310,14 @@ def filter_step(U, nest, prm, seed, step, proposal=None, translate=True, skip_un
     U2 = _merge(U, Unew, acc2, inner, active)
 
     rec = {"delta_block": d_in, "accept_block": acc_in, "delta_sub": d_sub, "accept_sub": acc_out,
-           "changed_sub": changed, "accept_after_sub": acc2, "hb_failed": failed}
+           "changed_sub": changed, "accept_after_sub": acc2, "hb_failed": failed, "h": h,
+           "passed_learned": passed}
     Ufin = U2
     if prm.global_level:
-        dg = global_level(U, U2, outer, prm.kappa, prm.n_global, seed, step, tol=prm.tol)
+        G0, G1 = U, U2
+        if fixed:
+            G0, G1 = _merge(U, E0, acc2, inner, active), _merge(U, EN, acc2, inner, active)
+        dg = global_level(G0, G1, outer, prm.kappa, prm.n_global, seed, step, tol=prm.tol)
         d = float(dg.sum())
         if prm.beta_global != 0.0:
             d += prm.beta_global * (wilson_action(U2) - wilson_action(U))

@@ -28,7 +28,7 @@ __all__ = [
     "PREC_F64", "PREC_F32", "PREC_BF16", "OP_FULL", "OP_BLOCKS", "ACTIVE_BLOCKS", "ACTIVE_ALL",
     "LEVEL_BLOCK", "LEVEL_GLOBAL", "LEVEL_SUB", "EST_INTERP", "EST_INDEPENDENT", "psms_set_outer_blocks",
     "LEVEL_OUTER_GLOBAL", "psms_filter_record", "psms_max_chunk", "REC_H", "REC_DELTA_HYP", "REC_ACCEPT_BLOCK",
-    "REC_DELTA_SUB", "REC_ACCEPT_SUB",
+    "REC_DELTA_SUB", "REC_ACCEPT_SUB", "psms_block_logdet", "psms_scratch_bytes",
 ]
 
 PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
@@ -78,7 +78,9 @@ class FilterParams(ctypes.Structure):
                 ("learned", ctypes.c_int), ("gauge_fix", ctypes.c_int), ("relgf", RelGFParams),
                 ("proposal_field", ctypes.c_int), ("translate", ctypes.c_int), ("hyp_level", ctypes.c_int),
                 ("hyp_beta", ctypes.c_double * 2), ("beta_block_hyp", ctypes.c_double),
-                ("beta_global_hyp", ctypes.c_double), ("n_sub", ctypes.c_int), ("beta_sub", ctypes.c_double)]
+                ("beta_global_hyp", ctypes.c_double), ("n_sub", ctypes.c_int), ("beta_sub", ctypes.c_double),
+                ("exact_block", ctypes.c_int), ("beta_block_det", ctypes.c_double),
+                ("beta_global_blockdet", ctypes.c_double)]
 
 
 class FilterResult(ctypes.Structure):
@@ -156,6 +158,8 @@ _SIGS = {
     "psms_level_coefficients": [_I, _P, _P, _P, _P],
     "psms_filter_record": [_P, _I, _P, _I, ctypes.POINTER(_I)],
     "psms_max_chunk": [_P, _I],
+    "psms_block_logdet": [_P, _I, _P],
+    "psms_scratch_bytes": [_P, ctypes.POINTER(ctypes.c_size_t)],
 }
 
 _lib = None
@@ -334,6 +338,21 @@ def psms_filter_record(ctx, what):
     return out[:n.value].copy()
 
 
+def psms_block_logdet(ctx, field):
+    """ln|det D_b| of every block (lexicographic block index), exact."""
+    nb = int(psms_geometry_info(ctx)[0])
+    out = np.empty(nb, dtype=np.float64)
+    ctx.check(ctx.lib.psms_block_logdet(ctx.handle, field, out.ctypes.data))
+    return out
+
+
+def psms_scratch_bytes(ctx):
+    """Bytes of device scratch the context holds."""
+    v = ctypes.c_size_t()
+    ctx.check(ctx.lib.psms_scratch_bytes(ctx.handle, ctypes.byref(v)))
+    return v.value
+
+
 def psms_max_chunk(ctx, n):
     """Cap on interpolation steps batched per estimator launch (0: automatic)."""
     ctx.check(ctx.lib.psms_max_chunk(ctx.handle, int(n)))
@@ -349,7 +368,8 @@ def psms_set_outer_blocks(ctx, outer):
 def psms_filter_step(ctx, field, *, beta0, n_iter=1, n_or=0, n_block=4, n_global=4, beta_block=0.0,
                      beta_global=0.0, global_level=True, tol=1e-10, inner_prec=PREC_F64, seed=0, step=0,
                      learned=False, gauge_fix=None, proposal_field=-1, translate=True, hyp_level=None,
-                     beta_block_hyp=0.0, beta_global_hyp=0.0, n_sub=0, beta_sub=0.0):
+                     beta_block_hyp=0.0, beta_global_hyp=0.0, n_sub=0, beta_sub=0.0, exact_block=False,
+                     beta_block_det=1.0, beta_global_blockdet=0.0):
     """gauge_fix: None (off) or a dict of relative gauge-fixing parameters
     (alpha0, alpha_min, dalpha, theta_tol, max_iter, prec; {} = defaults).
     proposal_field: -1 (domain sweep) or the slot of an external proposal.
@@ -359,7 +379,8 @@ def psms_filter_step(ctx, field, *, beta0, n_iter=1, n_or=0, n_block=4, n_global
                      float(beta_global), int(bool(global_level)), float(tol), int(inner_prec), int(seed), int(step),
                      int(bool(learned)), int(gauge_fix is not None), _relgf(**(gauge_fix or {})),
                      int(proposal_field), int(bool(translate)), int(hyp_level is not None), (_D * 2)(*hb),
-                     float(beta_block_hyp), float(beta_global_hyp), int(n_sub), float(beta_sub))
+                     float(beta_block_hyp), float(beta_global_hyp), int(n_sub), float(beta_sub),
+                     int(bool(exact_block)), float(beta_block_det), float(beta_global_blockdet))
     r = FilterResult()
     nb = int(np.prod([d // b for d, b in zip(ctx.dims, ctx.block)]))
     db = (_D * nb)()

@@ -18,6 +18,7 @@
 #include "gaugefix.hpp"
 #include "hyp.hpp"
 #include "block_action.hpp"
+#include "blockdet.hpp"
 #include "outer.hpp"
 #include "mlp.hpp"
 #include "solver.hpp"
@@ -444,6 +445,20 @@ psms_status psms_hyp_block_action(psms_ctx *ctx, int field, const double *alpha,
     PSMS_CATCH(ctx)
 }
 
+psms_status psms_block_logdet(psms_ctx *ctx, int field, double *out_host) {
+    PSMS_TRY(ctx)
+    check_field(ctx, field);
+    if (!out_host) fail(PSMS_EINVAL, "null output");
+    const int nb = ctx->g.nblocks;
+    double *d = (double *)scratch(ctx, "bd_out", sizeof(double) * nb);
+    block_logdet(ctx, ctx->U64[field], d);
+    cuda_check(cudaMemcpyAsync(out_host, d, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream), "logdet");
+    cuda_check(cudaStreamSynchronize(ctx->stream), "logdet");
+    for (int b = 0; b < nb; ++b)
+        if (!std::isfinite(out_host[b])) fail(PSMS_ESPECTRUM, "singular block operator (non-finite ln|det|)");
+    PSMS_CATCH(ctx)
+}
+
 psms_status psms_set_outer_blocks(psms_ctx *ctx, const int *outer) {
     PSMS_TRY(ctx)
     set_outer(ctx, outer);
@@ -777,10 +792,28 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
     const bool recursive = prm->n_sub > 0;
     if (recursive) {
         if (!has_outer(ctx)) fail(PSMS_EINVAL, "n_sub >= 1 needs outer blocks (psms_set_outer_blocks)");
-        if (prm->learned || prm->hyp_level || prm->gauge_fix || prm->beta_block_hyp != 0.0 ||
-            prm->beta_global_hyp != 0.0)
-            fail(PSMS_EINVAL, "the recursive filter does not combine with the learned, HYP or gauge-fixing options");
+        if (prm->hyp_level || prm->beta_block_hyp != 0.0 || prm->beta_global_hyp != 0.0)
+            fail(PSMS_EINVAL, "the recursive filter does not combine with the HYP options");
         if (!std::isfinite(prm->beta_sub)) fail(PSMS_EINVAL, "beta_sub must be finite");
+        if (prm->exact_block || prm->beta_global_blockdet != 0.0)
+            fail(PSMS_EINVAL, "the recursive filter does not combine with the exact block level");
+    }
+    if (!std::isfinite(prm->beta_block_det) || !std::isfinite(prm->beta_global_blockdet))
+        fail(PSMS_EINVAL, "filter coefficients must be finite");
+    // exact change of the block-determinant action S_b = -2 ln|det D_b|
+    double *d_dsb = nullptr;
+    if (prm->exact_block || prm->beta_global_blockdet != 0.0) {
+        double *d_l0 = (double *)scratch(ctx, "fs_ld0", sizeof(double) * nb);
+        double *d_l1 = (double *)scratch(ctx, "fs_ld1", sizeof(double) * nb);
+        d_dsb = (double *)scratch(ctx, "fs_dsb", sizeof(double) * nb);
+        block_logdet(ctx, old, d_l0);
+        block_logdet(ctx, prop, d_l1);
+        block_lincomb(ctx, 2.0, d_l0, -2.0, d_l1, 0.0, nullptr, d_dsb);
+        std::vector<double> chk(nb);
+        cuda_check(cudaMemcpyAsync(chk.data(), d_dsb, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream), "dsb");
+        cuda_check(cudaStreamSynchronize(ctx->stream), "dsb");
+        for (double v : chk)
+            if (!std::isfinite(v)) fail(PSMS_ESPECTRUM, "singular block operator (non-finite ln|det|)");
     }
     const bool need_dsw = prm->beta_block != 0.0 || prm->hyp_level || (recursive && prm->beta_sub != 0.0);
     const bool need_hyp = prm->hyp_level || prm->beta_block_hyp != 0.0 || prm->beta_global_hyp != 0.0;
@@ -869,11 +902,16 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
     double *d_db = (double *)scratch(ctx, "fs_dblk", sizeof(double) * nb * N1);
     long long iters = 0;
     const int n_pass = n_learned >= 0 ? n_learned : n_hyp;  // -1: every block
-    if (n_pass != 0)
+    int N1d = N1;  // Delta terms per block in d_db
+    if (prm->exact_block) {
+        N1d = 1;
+        block_lincomb(ctx, prm->beta_block_det, d_dsb, 0.0, nullptr, 0.0, nullptr, d_db);
+    } else if (n_pass != 0) {
         iters = block_level(ctx, e0, eN, N1, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol, prm->inner_prec,
                             d_db, d_mask);
-    else
+    } else {
         cuda_check(cudaMemsetAsync(d_db, 0, sizeof(double) * nb * N1, ctx->stream), "dblk");
+    }
     double *d_dsum = (double *)scratch(ctx, "fs_dsum", sizeof(double) * (nb + 1));
     int *d_acc = (int *)scratch(ctx, "fs_acc", sizeof(int) * nb);
     // per-block extra term: beta_block dS_w,b + beta_block_hyp dS_HYP,b
@@ -887,7 +925,7 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         d_extra = d_ex;
         coef = 1.0;
     }
-    decide(ctx, d_db, nb, N1, per_block ? 1 : 0, prm->seed, prm->step, PSMS_LEVEL_BLOCK, 0.0, d_extra, coef, d_dsum,
+    decide(ctx, d_db, nb, N1d, per_block ? 1 : 0, prm->seed, prm->step, PSMS_LEVEL_BLOCK, 0.0, d_extra, coef, d_dsum,
            d_acc, d_mask);
     if (!per_block && n_hyp == 0)  // one decision on the sum: a rejected HYP level rejects the step
         cuda_check(cudaMemsetAsync(d_acc, 0, sizeof(int) * nb, ctx->stream), "reject");
@@ -938,8 +976,18 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
             if (ha[b] && chg[b]) changed[oo[b]] = 1, any = true;
         std::vector<double> dsub(no, 0.0);
         if (any) {
+            // between U and the field after stage 1, or their relatively
+            // gauge-fixed pair: the stage-1 endpoints merged on the accepted
+            // inner blocks (the inner blocks decouple)
+            const double2 *s0 = old, *s1 = mid;
+            if (prm->gauge_fix) {
+                merge_blocks(ctx, old, e0, e0, d_acc);
+                merge_blocks(ctx, old, eN, eN, d_acc);
+                s0 = e0;
+                s1 = eN;
+            }
             std::vector<double> hs((long long)no * prm->n_sub);
-            iters += sub_level(ctx, old, mid, prm->n_sub, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol,
+            iters += sub_level(ctx, s0, s1, prm->n_sub, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol,
                                prm->inner_prec, hs.data());
             for (int o = 0; o < no; ++o)
                 if (changed[o])
@@ -999,8 +1047,8 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         }
         std::vector<double> hg(N2);
         if (recursive) {
-            iters += outer_global_level(ctx, old, mid, N2, PSMS_EST_INTERP, prm->seed, prm->step, prm->tol,
-                                        prm->inner_prec, hg.data());
+            iters += outer_global_level(ctx, e0, prm->gauge_fix ? eN : mid, N2, PSMS_EST_INTERP, prm->seed,
+                                        prm->step, prm->tol, prm->inner_prec, hg.data());
         } else {
             iters += global_level(ctx, e0, prm->gauge_fix ? eN : mid, N2, PSMS_EST_INTERP, prm->seed, prm->step,
                                   prm->tol, prm->inner_prec, d_dg);
@@ -1028,6 +1076,17 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
             for (int b = 0; b < nb; ++b)
                 if (ha[b]) sh += hh[b];
             dglob += prm->beta_global_hyp * sh;
+        }
+        if (prm->beta_global_blockdet != 0.0) {
+            // S_b changes on the accepted blocks only (the blocks decouple)
+            std::vector<double> hb(nb);
+            cuda_check(cudaMemcpyAsync(hb.data(), d_dsb, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream),
+                       "dS_b");
+            cuda_check(cudaStreamSynchronize(ctx->stream), "dS_b");
+            double sb = 0.0;
+            for (int b = 0; b < nb; ++b)
+                if (ha[b]) sb += hb[b];
+            dglob += prm->beta_global_blockdet * sb;
         }
         if (!std::isfinite(dglob)) fail(PSMS_ESPECTRUM, "non-finite global estimate");
         const double u = uniforms(prm->seed, TAG_ACCEPT, prm->step, PSMS_LEVEL_GLOBAL, 0, 0).u[0];
@@ -1084,6 +1143,14 @@ psms_status psms_filter_record(psms_ctx *ctx, int what, double *out, int n, int 
     if (!out || n < (int)v->size()) fail(PSMS_EINVAL, "record output too small");
     for (size_t i = 0; i < v->size(); ++i) out[i] = (*v)[i];
     PSMS_CATCH(ctx)
+}
+
+psms_status psms_scratch_bytes(const psms_ctx *cctx, size_t *bytes) {
+    if (!cctx || !bytes) return PSMS_EINVAL;
+    size_t t = 0;
+    for (const auto &kv : cctx->scratch) t += kv.second.bytes;
+    *bytes = t;
+    return PSMS_OK;
 }
 
 psms_status psms_max_chunk(psms_ctx *ctx, int n) {

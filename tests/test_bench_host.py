@@ -47,10 +47,38 @@ def test_clock_summary_reasons_and_median():
     assert s["reasons"] == ["hw_thermal_slowdown"]
 
 
-def test_step_model_covers_every_workload():
-    assert set(bench.STEP_MODEL) == set(bench.WORKLOADS)
-    for iters, acc in bench.STEP_MODEL.values():
-        assert iters > 0 and 0.0 <= acc <= 1.0
+def test_poisson_interval():
+    """Garwood interval: k = 0 gives [0, 3.689] (the 'rule of three' bound
+    -ln 0.025), k = 10 gives [4.795, 18.39] (tabulated exact values)."""
+    lo, hi = bench._poisson_interval(0)
+    assert lo == 0.0 and hi == pytest.approx(3.6889, abs=1e-3)
+    lo, hi = bench._poisson_interval(10)
+    assert lo == pytest.approx(4.7954, abs=1e-3) and hi == pytest.approx(18.390, abs=1e-2)
+
+
+def test_rao_blackwell_count():
+    import math
+
+    import numpy as np
+    recs = [{"n_accept_blocks": 2, "delta_global": -0.3},     # certain
+            {"n_accept_blocks": 1, "delta_global": 1.0},      # e^-1
+            {"n_accept_blocks": 0, "delta_global": 0.0}]      # nothing changed
+    assert bench._rb_accepted(recs) == pytest.approx(1.0 + math.exp(-1.0))
+    recs = [dict(r, accept_global=True, n_blocks=4, accept_block=np.ones(4, bool), delta_block=np.zeros(4),
+                 solver_iters=10) for r in recs]
+    s = bench._arm_summary(recs, 2000.0)
+    assert s["accepted_updates"] == 2 and s["s_per_step"] == pytest.approx(2.0 / 3)
+    assert s["accepted_updates_per_s"] == pytest.approx(1.0)
+    lo, hi = s["accepted_updates_per_s_95ci"]
+    assert lo < 1.0 < hi
+
+
+def test_oracle_step_model_arithmetic():
+    comp = {"sweep_s": 2.0, "level_overhead_s": 1.0, "block_solve_s": 0.1, "cgnr_iteration_s": 0.5}
+    wl = bench.WORKLOADS["16^4"]
+    nb = 256
+    ref = 2.0 + wl["n_block"] * (1.0 + nb * 0.1) + wl["n_global"] * (1.0 + nb * 0.1 + 300 * 0.5)
+    assert bench.oracle_step_seconds("16^4", comp, 300) == pytest.approx(ref)
 
 
 def test_delta_statistics_and_gaussian_prediction():

@@ -156,9 +156,9 @@ def test_filter_step_with_gauge_fixing_parity(prec):
         ps.psms_gauge_sweep(ctx, 1, ps.ACTIVE_BLOCKS, 1, 1, 5.3, SEED, step << 20)
         g1, g2, _ = _g(ctx, prec=prec)
         override = (g1, g2)
-    r = ps.psms_filter_step(ctx, 0, beta0=5.3, n_iter=1, n_or=1, n_block=8, n_global=2, tol=1e-13,
+    r = ps.psms_filter_step(ctx, 0, beta0=5.3, n_iter=1, n_or=1, n_block=3, n_global=1, tol=1e-13,
                             inner_prec=ps.PREC_F32, seed=SEED, step=step, gauge_fix=gf)
-    prm = ofilter.FilterParams(kappa=kappa, beta0=5.3, n_iter=1, n_or=1, n_block=8, n_global=2, tol=1e-13,
+    prm = ofilter.FilterParams(kappa=kappa, beta0=5.3, n_iter=1, n_or=1, n_block=3, n_global=1, tol=1e-13,
                                gauge_fix={} if override is None else None)
     U2, rec = ofilter.filter_step(U, geom, prm, SEED, step, gf_override=override)
     assert r["gf_steps"] > 0

@@ -1,6 +1,8 @@
 """GPU parity of the Krylov solves (whole lattice and Dirichlet blocks) with
 the oracle: the solution matches the oracle's CGNR solution and the true
 residual, recomputed with the oracle's D, meets the tolerance."""
+import functools
+
 import numpy as np
 import pytest
 import torch
@@ -115,23 +117,34 @@ def test_solver_reports_non_convergence():
     assert e.value.status == 4
 
 
+_VARIANT_CASE = dict(dims=(8, 8, 8, 16), block=(8, 8, 8, 8), kappa=0.156)
+
+
+@functools.lru_cache(maxsize=1)
+def _variant_reference():
+    """The oracle's solution on block 1 of the variant test (computed once)."""
+    c = _VARIANT_CASE
+    geom = lattice.Geometry(c["dims"], c["block"])
+    U = gauge.generate_links(c["dims"], 0.5, 15)
+    b = seeded.spinor(c["dims"], 16)
+    ref = estimator.solve_blocks(U, b, geom, c["kappa"], [1], 1e-14)
+    return geom, U, b, dirac.extract_block(ref, geom, 1)
+
+
 @pytest.mark.parametrize("variant", range(18))
 def test_block_solver_cluster_variants(variant):
     """Every (cluster size, register cap) variant of the block solver gives the
     oracle's solution (8^4 blocks: one block is shared by up to 8 CTAs of a
     thread-block cluster)."""
-    dims, block, kappa = (8, 8, 8, 16), (8, 8, 8, 8), 0.156
-    geom = lattice.Geometry(dims, block)
-    ctx = ps.psms_create(dims, block, kappa, 1)
+    c = _VARIANT_CASE
+    geom, U, b, ref1 = _variant_reference()
+    ctx = ps.psms_create(c["dims"], c["block"], c["kappa"], 1)
     ps.psms_gauge_init(ctx, 0, 0.5, 15)
     ps.psms_autotune(ctx, False, variant)
-    U = gauge.generate_links(dims, 0.5, 15)
-    b = seeded.spinor(dims, 16)
     for inner in (ps.PREC_F32, ps.PREC_F64):
         x = torch.zeros_like(native(ctx, b))
         ps.psms_solve(ctx, 0, ps.OP_BLOCKS, native(ctx, b), x, 1e-13, 20000, inner)
         got = canonical(ctx, x)
-        r = b - dirac.apply_D(U, got, kappa, geom, mode="block")
+        r = b - dirac.apply_D(U, got, c["kappa"], geom, mode="block")
         assert np.sqrt(linalg.norm2(r) / linalg.norm2(b)) <= 1e-13
-        ref = estimator.solve_blocks(U, b, geom, kappa, [1], 1e-14)
-        assert rel_err(dirac.extract_block(got, geom, 1), dirac.extract_block(ref, geom, 1)) < 1e-11
+        assert rel_err(dirac.extract_block(got, geom, 1), ref1) < 1e-11

@@ -334,3 +334,32 @@ def test_filter_step_bookkeeping():
         assert np.abs(rec["delta_sub"][check] - ref).max() < 1e-8
         keep = acc2[nest.inner.block_index][..., None] & act
         assert np.array_equal(Unew, np.where(keep[..., None, None], Up, U))
+
+
+def test_filter_with_learned_level_and_gauge_fixing_reduces_to_one_level():
+    """The same reduction with the learned level and relative gauge fixing
+    switched on (3^4 blocks: per-block decisions and one interior point per
+    block): decisions, h, estimates and the final field equal those of the
+    filter without recursion."""
+    from oracle import mlp
+    dims, B = (6, 6, 6, 6), (3, 3, 3, 3)
+    nest = recursive.Nested(dims, B, B)
+    U = gauge.generate_links(dims, 0.5, 83)
+    p = mlp.init_params(5)
+    p["ys"] = 3.0
+    gf = dict(max_iter=50)
+    prm = dict(kappa=K, beta0=5.3, n_iter=1, n_or=1, n_block=2, n_global=2, tol=1e-12, learned=p, gauge_fix=gf)
+    seen_h = False
+    for step in range(2):
+        U5, r5 = recursive.filter_step(U, nest, recursive.RecursiveParams(n_sub=2, **prm), 9, step)
+        U4, r4 = ofilter.filter_step(U, lattice.Geometry(dims, B), ofilter.FilterParams(**prm), 9, step)
+        assert np.array_equal(r5["passed_learned"], r4["passed_learned"])
+        assert np.abs(r5["h"] - r4["h"]).max() < 1e-12
+        seen_h |= bool(np.any(r5["h"] != 0))
+        assert np.array_equal(r5["accept_block"], r4["accept_block"])
+        assert np.abs(r5["delta_block"] - r4["delta_block"]).max() < 1e-12
+        assert r5["accept_global"] == r4["accept_global"]
+        assert abs(r5["delta_global"] - r4["delta_global"]) < 1e-12
+        assert np.array_equal(U5, U4)
+        U = U5
+    assert seen_h

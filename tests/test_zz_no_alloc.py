@@ -39,6 +39,7 @@ def test_noalloc_block_solve_matches_block_solve_twice():
     torch.cuda.synchronize()
 
     x = torch.zeros_like(b1)
+    held = ps.psms_scratch_bytes(ctx)
     info1 = ps.psms_block_solve_noalloc(ctx, 0, ps.OP_BLOCKS, b1, x, TOL, 20000)
     assert rel_err(canonical(ctx, x), ref1) < PARITY
     assert info1["true_residual"] <= TOL
@@ -49,6 +50,10 @@ def test_noalloc_block_solve_matches_block_solve_twice():
     assert info2["true_residual"] <= TOL
     ps.psms_block_solve_noalloc(ctx, 0, 5, b2, x, TOL, 20000)
     assert rel_err(canonical(ctx, x), ref_one) < PARITY
+    # the context's scratch registry did not grow (the calls allocated
+    # nothing of their own); the device-wide free memory is a secondary
+    # check that other processes could disturb
+    assert ps.psms_scratch_bytes(ctx) == held
     assert torch.cuda.mem_get_info()[0] >= free_after_first
 
 
