@@ -89,3 +89,81 @@ def test_filter_chain_detailed_balance():
           f"batch-means s.e. {np.round(se, 4)}; z {np.round(z, 2)}")
     assert acc > 0.15
     assert np.all(np.abs(z) < 4.0), z
+
+
+def test_block_chain_detailed_balance_learned_gauge_fixed():
+    """App. A for the block part of the benchmarked hierarchy: the learned
+    level (a fixed random antisymmetric network, App. C's auxiliary action)
+    and then the stochastic block level with Delta_b - h_b between
+    relatively gauge-fixed endpoints (Sec. 4.2), per-block decisions (4^4
+    blocks), no global level.  Two blocks of an 8^4 lattice have three
+    states each, differing on their active links; the symmetric proposal
+    moves each of them to one of its two other states; no other link ever
+    changes.  The blocks are independent chains whose stationary
+    distributions must be |det D_b(U_k)|^2 / sum_j |det D_b(U_j)|^2, with
+    the determinants from the oracle's dense LU of the block operator."""
+    from oracle import mlp
+    dims, block, kappa = (8, 8, 8, 8), (4, 4, 4, 4), 0.156
+    geom = lattice.Geometry(dims, block)
+    act = geom.active_links()
+    varying, k_states, n_steps, n_batches = (5, 10), 3, 3000, 20
+    U0 = gauge.generate_links(dims, 0.3, 21)
+    g = np.random.default_rng(22)
+    sel = {b: (geom.block_index == b)[..., None] & act for b in varying}
+    states = {}
+    for b in varying:
+        states[b] = []
+        for _ in range(k_states):
+            om = g.standard_normal(U0.shape[:5] + (8,))
+            R = gauge.expm_i_hermitian(gauge.hermitian_generators(om), 0.15)
+            states[b].append(np.where(sel[b][..., None, None], U0 @ R, U0))
+
+    def field(s):
+        F = U0.copy()
+        for b in varying:
+            F[sel[b]] = states[b][s[b]][sel[b]]
+        return F
+
+    pis = {}
+    for b in varying:
+        logw = np.array([2.0 * ofilter.block_logdet(states[b][k], geom, b, kappa) for k in range(k_states)])
+        p = np.exp(logw - logw.max())
+        pis[b] = p / p.sum()
+    ctx = ps.psms_create(dims, block, kappa, 2)
+    q = mlp.init_params(17)
+    q["ys"] = 1.0
+    flat = np.concatenate([q["W1"].ravel(), q["b1"], q["W2"].ravel(), q["b2"], q["w3"], [q["b3"]], q["mu"],
+                           q["sigma"], [q["ys"]]]).astype(np.float32)
+    ps.psms_mlp_params(ctx, flat)
+    s = {b: 0 for b in varying}
+    set_links(ctx, 0, field(s))
+    rng = np.random.default_rng(23)
+    visits, moves, h_seen = [], 0, 0.0
+    for step in range(n_steps):
+        t = {b: (s[b] + 1 + int(rng.integers(k_states - 1))) % k_states for b in varying}
+        set_links(ctx, 1, field(t))
+        r = ps.psms_filter_step(ctx, 0, beta0=5.3, n_block=16, n_global=1, global_level=False, tol=1e-10,
+                                inner_prec=ps.PREC_F32, seed=SEED, step=step, proposal_field=1, translate=False,
+                                learned=True, gauge_fix={"prec": ps.PREC_F32})
+        if step < 50:
+            h_seen = max(h_seen, float(np.abs(ps.psms_filter_record(ctx, ps.REC_H)[list(varying)]).max()))
+        for b in varying:
+            if r["accept_block"][b]:
+                s[b] = t[b]
+                moves += 1
+        visits.append([s[b] for b in varying])
+        if step % 1000 == 999:
+            assert np.array_equal(get_links(ctx, 0), field(s))
+    visits = np.array(visits)
+    acc = moves / (n_steps * len(varying))
+    assert acc > 0.15
+    assert h_seen > 0.05          # the learned level is not idle
+    for col, b in enumerate(varying):
+        v = visits[:, col]
+        freq = np.array([(v == k).mean() for k in range(k_states)])
+        bf = np.array([[(w == k).mean() for k in range(k_states)] for w in v.reshape(n_batches, -1)])
+        se = bf.std(axis=0, ddof=1) / np.sqrt(n_batches)
+        z = (freq - pis[b]) / np.maximum(se, 1e-3)
+        print(f"block {b}: acceptance {acc:.3f}; exact pi {np.round(pis[b], 4)}; chain {np.round(freq, 4)}; "
+              f"z {np.round(z, 2)}")
+        assert np.all(np.abs(z) < 4.0), z
