@@ -38,14 +38,18 @@ UNIT = "accepted updates/s"
 SEED = 0x50534D53
 
 WORKLOADS = {
-    # name: dims (L0..L3), block, kappa, eps, beta, n_block, n_global, therm iterations
-    "32^3x64": dict(dims=(64, 32, 32, 32), block=(8, 8, 8, 8), kappa=0.157, eps=0.5, beta=5.3, n_block=4,
-                    n_global=24, therm=4, n_iter=1, n_or=2, tol=1e-10, train_props=8),
-    "16^4": dict(dims=(16, 16, 16, 16), block=(4, 4, 4, 4), kappa=0.156, eps=0.5, beta=5.3, n_block=48,
-                 n_global=12, therm=4, n_iter=1, n_or=1, tol=1e-13, train_props=48),
-    "4^4": dict(dims=(4, 4, 4, 4), block=(2, 2, 2, 2), kappa=0.15, eps=0.3, beta=5.3, n_block=4, n_global=4,
-                therm=0, n_iter=1, n_or=0, tol=1e-10, train_props=8),
+    # name: dims (L0..L3), block (the smallest Dirichlet blocks), outer blocks of the recursive
+    # decomposition (None: one level), kappa, eps, beta, interpolation steps per level,
+    # thermalisation iterations, proposal sweeps, tolerance, proposals for the learned level's labels
+    "32^3x64": dict(dims=(64, 32, 32, 32), block=(4, 4, 4, 4), outer=(8, 8, 8, 8), kappa=0.157, eps=0.5,
+                    beta=5.3, n_block=12, n_sub=12, n_global=24, therm=4, n_iter=1, n_or=2, tol=1e-10,
+                    train_props=8),
+    "16^4": dict(dims=(16, 16, 16, 16), block=(4, 4, 4, 4), outer=None, kappa=0.156, eps=0.5, beta=5.3, n_block=48,
+                 n_sub=0, n_global=12, therm=4, n_iter=1, n_or=1, tol=1e-13, train_props=48),
+    "4^4": dict(dims=(4, 4, 4, 4), block=(2, 2, 2, 2), outer=None, kappa=0.15, eps=0.3, beta=5.3, n_block=4,
+                n_sub=0, n_global=4, therm=0, n_iter=1, n_or=0, tol=1e-10, train_props=8),
 }
+HEADLINE = "32^3x64"
 DW_FLOP_PER_SITE = 1320.0
 DW_BYTES_PER_SITE = {"bf16": 384.0, "f32": 480.0, "f64": 960.0}
 
@@ -529,6 +533,51 @@ def levels_only(args):
     print(json.dumps(out), flush=True)
 
 
+def block_only(args):
+    """The block level alone on the 16^4 workload (4^4 blocks): all blocks x
+    n interpolation steps (--block-n, default 12) between the gauge-fixed
+    endpoints of one domain-sweep proposal, FP32 inner iterations to the
+    workload tolerance, one persistent launch of the block solver per call.
+    The first call autotunes the solver variant; --steps calls are timed
+    with CUDA events.  The small case for Nsight Compute captures of
+    block_solve_cluster_kernel (about 1 GB on the device at n = 12)."""
+    import torch
+
+    import paper_1204_1306_gb300 as ps
+    from paper_1204_1306_gb300 import build as _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    wl = WORKLOADS["16^4"]
+    seed = SEED + 5
+    ctx = _new_chain(ps, torch, wl, seed)
+    ps.psms_gauge_copy(ctx, 1, 0)
+    ps.psms_gauge_sweep(ctx, 1, ps.ACTIVE_BLOCKS, wl["n_iter"], wl["n_or"], wl["beta"], seed, 9 << 20)
+    ps.psms_relative_gauge_fix(ctx, 0, 1, 2, 3, prec=ps.PREC_F32)
+    n = args.block_n
+    for r in range(args.warmup):
+        ps.psms_logdet_ratio(ctx, ps.LEVEL_BLOCK, 2, 3, n, ps.EST_INTERP, seed, r, wl["tol"], ps.PREC_F32)
+    ps.psms_profile_enable(ctx, 1)
+    ms = []
+    for r in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        ps.psms_logdet_ratio(ctx, ps.LEVEL_BLOCK, 2, 3, n, ps.EST_INTERP, seed, 100 + r, wl["tol"], ps.PREC_F32)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    nl, bms, bbytes = ps.psms_profile_read_block(ctx)
+    peak, kind = peaks()
+    nb = ps.psms_geometry_info(ctx)[0]
+    print(json.dumps({"workload": "16^4 block level", "n": n, "blocks": nb, "ms_per_call": statistics.median(ms),
+                      "estimates_per_s": nb * n / (statistics.median(ms) * 1e-3),
+                      "block_solver": {"launches": nl, "ms": round(bms, 3), "algorithmic_GB/s": round(
+                          bbytes / (bms * 1e-3) / 1e9, 1) if bms > 0 else None, "peak_gbs": peak, "peak_kind": kind}}),
+          flush=True)
+    ctx.close()
+
+
 def measure_estimators(ps, torch, wl, seed, n=12, reps=3):
     """Det-ratio estimates per second on the workload lattice: the block
     level (all blocks x n interpolation steps) and the global level (n
@@ -566,12 +615,20 @@ ARMS = (
 
 def _filter_prm(ps, wl, seed):
     return dict(beta0=wl["beta"], n_iter=wl["n_iter"], n_or=wl["n_or"], n_block=wl["n_block"],
-                n_global=wl["n_global"], tol=wl["tol"], seed=seed, gauge_fix={"prec": ps.PREC_F32})
+                n_global=wl["n_global"], tol=wl["tol"], seed=seed, gauge_fix={"prec": ps.PREC_F32},
+                n_sub=wl["n_sub"] if wl.get("outer") else 0)
+
+
+def _ctx(ps, torch, wl):
+    ctx = ps.psms_create(wl["dims"], wl["block"], wl["kappa"], 4)
+    ps.psms_set_stream(ctx, torch.cuda.current_stream())
+    if wl.get("outer"):
+        ps.psms_set_outer_blocks(ctx, wl["outer"])
+    return ctx
 
 
 def _new_chain(ps, torch, wl, seed):
-    ctx = ps.psms_create(wl["dims"], wl["block"], wl["kappa"], 4)
-    ps.psms_set_stream(ctx, torch.cuda.current_stream())
+    ctx = _ctx(ps, torch, wl)
     ps.psms_gauge_init(ctx, 0, wl["eps"], seed)
     if wl["therm"]:
         ps.psms_gauge_sweep(ctx, 0, ps.ACTIVE_ALL, wl["therm"], 2, wl["beta"], seed, 1 << 40)
@@ -620,25 +677,13 @@ def _accepted(recs):
     return sum(1 for r in recs if r["accept_global"] and r["n_accept_blocks"] > 0)
 
 
-def large_workload(ps, torch, steps=2):
-    """32^3 x 64, 8^4 domains, kappa 0.157, 24 interpolation steps at the
-    global level: stand-alone D_w per precision, the domain heatbath, and
-    filter steps (FP32 inner, relative gauge fixing)."""
-    wl = WORKLOADS["32^3x64"]
+def dw_and_heatbath(ps, torch, wl_name):
+    """Stand-alone D_w per precision and the domain heatbath on the workload
+    lattice (thermalised field)."""
+    wl = WORKLOADS[wl_name]
     ctx = _new_chain(ps, torch, wl, SEED + 4)
-    dw = measure_dw(ps, ctx, torch)
-    hb = measure_heatbath(ps, ctx, torch, wl)
-    prm = _filter_prm(ps, wl, SEED + 4)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    ps.psms_filter_step(ctx, 0, step=10_000, inner_prec=ps.PREC_F32, **prm)
-    recs, ms = _timed_steps(ps, torch, ctx, prm, ps.PREC_F32, False, steps, flush)
-    out = {"dims": list(wl["dims"]), "block": list(wl["block"]), "kappa": wl["kappa"], "n_block": wl["n_block"],
-           "n_global": wl["n_global"], "tol": wl["tol"], "ms_per_step": round(ms / steps, 2),
-           "accepted_updates_per_s": _accepted(recs) / (ms * 1e-3),
-           "block_acceptance": sum(r["n_accept_blocks"] for r in recs) / sum(r["n_blocks"] for r in recs),
-           "delta_block_mean": float(np.mean([r["delta_block"].mean() for r in recs])),
-           "gauge_fix_steps_per_step": sum(r["gf_steps"] for r in recs) / steps,
-           "dw": dw, "heatbath": hb}
+    out = {"workload": wl_name, "dims": list(wl["dims"]), "block": list(wl["block"]),
+           "dw": measure_dw(ps, ctx, torch), "heatbath": measure_heatbath(ps, ctx, torch, wl)}
     ctx.close()
     return out
 
@@ -681,23 +726,24 @@ def _arm_summary(recs, ms, **extra):
     return out
 
 
-def our_arm(args):
-    import torch
-
-    import paper_1204_1306_gb300 as ps
-    from paper_1204_1306_gb300 import build as _build
-
-    ws, rank, local = dist_setup()
-    _build.build()
-    wl = WORKLOADS[args.workload]
+def run_workload(ps, torch, wl_name, steps, warmup, ws, rank, compare=True, fp64_steps=2, profile=True,
+                 e2e=True):
+    """All arms of one workload from one checkpoint (the thermalised field and
+    the learned level trained on estimates the method generates from it):
+    learned + mixed (the headline hierarchy), mixed without the learned
+    level, and plain FP64.  The first two run `steps` timed steps with step
+    counters 0..steps-1 after warm-up steps on a copy of the field.  Plain
+    FP64 runs the same chain as mixed (same proposals, noise and decisions:
+    its estimates agree to the refinement tolerance); it times
+    min(steps, fp64_steps) steps, its decisions are checked against mixed's
+    on those steps, and its accepted count over `steps` is therefore mixed's
+    (reported as such)."""
+    wl = WORKLOADS[wl_name]
     seed = SEED + 1 + 1000 * rank
     prec = {"f32": ps.PREC_F32, "f64": ps.PREC_F64}
     prm = _filter_prm(ps, wl, seed)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-
-    # the start of every arm: the thermalised field and the learned level
-    # trained on estimates the method generates from it, in one checkpoint
-    ckpt = os.path.join(tempfile.mkdtemp(), f"start_{rank}.psms")
+    ckpt = os.path.join(tempfile.mkdtemp(), f"start_{wl_name.replace('^', '')}_{rank}.psms")
     ctx = _new_chain(ps, torch, wl, seed)
     plaq0, _ = ps.psms_plaquette(ctx, 0)
     t0 = time.perf_counter()
@@ -708,71 +754,142 @@ def our_arm(args):
     ctx.close()
 
     def arm_ctx():
-        c = ps.psms_create(wl["dims"], wl["block"], wl["kappa"], 4)
-        ps.psms_set_stream(c, torch.cuda.current_stream())
+        c = _ctx(ps, torch, wl)
         ps.psms_checkpoint_load(c, 0, ckpt)
         return c
 
-    def warm(c, inner, learned):
+    def warm(c, inner, learned, n):
         # warm-up steps on a copy (slot 3): the timed steps start from the
         # checkpointed field with step counters 0, 1, ...
         ps.psms_gauge_copy(c, 3, 0)
-        for i in range(args.warmup):
+        for i in range(n):
             ps.psms_filter_step(c, 3, step=100_000 + i, inner_prec=inner, learned=learned, **prm)
         torch.cuda.synchronize()
 
+    out = {"workload": wl_name, "plaquette_start": plaq0, "train_s": round(train_s, 2),
+           "train_loss_first_last": [losses[0], losses[-1]]}
     # the headline arm: learned level + FP32 inner iterations + batched solves
     ctx = arm_ctx()
-    warm(ctx, ps.PREC_F32, True)
+    warm(ctx, ps.PREC_F32, True, warmup)
     barrier(ws)
-    n_launch0 = ps.load_library().psms_kernel_launches()
-    ps.psms_profile_enable(ctx, 10 + ps.PREC_F32)
+    lib = ps.load_library()
+    n_launch0 = lib.psms_kernel_launches()
+    if profile:
+        ps.psms_profile_enable(ctx, 10 + ps.PREC_F32)
     with ClockSampler(torch.cuda.current_device()) as clk:
         torch.cuda.synchronize()
         tw = time.perf_counter()
         torch.cuda.nvtx.range_push("timed_steps")
-        recs, ms = _timed_steps(ps, torch, ctx, prm, ps.PREC_F32, True, args.steps, flush)
+        recs, ms = _timed_steps(ps, torch, ctx, prm, ps.PREC_F32, True, steps, flush)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-        wall = time.perf_counter() - tw
+        out["wall_s_timed"] = time.perf_counter() - tw
     barrier(ws)
-    n_launch = ps.load_library().psms_kernel_launches() - n_launch0
-    hop_n, hop_ms, hop_bytes = ps.psms_profile_read(ctx)
-    blk_n, blk_ms, blk_bytes = ps.psms_profile_read_block(ctx)
-    blk_first = ps.psms_profile_block_launches(ctx, 4)
-    ps.psms_profile_enable(ctx, 0)
+    out["clocks"] = clk.summary()
+    out["gpu_launches"] = lib.psms_kernel_launches() - n_launch0
+    if profile:
+        out["hop_profile"] = ps.psms_profile_read(ctx)
+        out["block_profile"] = ps.psms_profile_read_block(ctx)
+        out["block_first"] = ps.psms_profile_block_launches(ctx, 4)
+        ps.psms_profile_enable(ctx, 0)
+    out["recs"], out["ms"] = recs, ms
+    if e2e:
+        # end to end through the C ABI with host buffers: the same chain from
+        # the same start field, the field living in pinned host memory --
+        # every step copies it to the device, runs the filter step and copies
+        # the updated field back (identical steps, so identical decisions)
+        V = ctx.V
+        host_links = torch.empty(V * 4 * 9 * 2, dtype=torch.float64).pin_memory()
+        dev_links = torch.empty(V * 4 * 9 * 2, dtype=torch.float64, device="cuda")
+        ps.psms_checkpoint_load(ctx, 0, ckpt)
+        ps.psms_gauge_get(ctx, 0, dev_links)
+        host_links.copy_(dev_links)
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        e2e_recs = []
+        for i in range(steps):
+            dev_links.copy_(host_links, non_blocking=True)
+            ps.psms_gauge_set(ctx, 0, dev_links)
+            e2e_recs.append(ps.psms_filter_step(ctx, 0, step=i, inner_prec=ps.PREC_F32, learned=True, **prm))
+            ps.psms_gauge_get(ctx, 0, dev_links)
+            host_links.copy_(dev_links, non_blocking=True)
+            torch.cuda.synchronize()
+        out["e2e_s"] = allmax(ws, time.perf_counter() - t0)
+        out["e2e_accepted"] = _accepted(e2e_recs)
+        out["e2e_same"] = all(a["accept_global"] == b["accept_global"] and a["n_accept_blocks"] == b["n_accept_blocks"]
+                              for a, b in zip(recs, e2e_recs))
+        out["link_bytes"] = V * 4 * 9 * 16
+    ctx.close()
+    arms = {"learned_mixed": _arm_summary(recs, ms, learned_pass=sum(r["n_accept_learned"] for r in recs) /
+                                          sum(r["n_blocks"] for r in recs))}
+    if compare and rank == 0:
+        runs = {}
+        for name, inner, learned in ARMS[1:]:
+            n = steps if name == "mixed" else min(steps, fp64_steps)
+            c = arm_ctx()
+            warm(c, prec[inner], False, 1)
+            rr, mm = _timed_steps(ps, torch, c, prm, prec[inner], False, n, flush)
+            arms[name] = _arm_summary(rr, mm)
+            runs[name] = rr
+            c.close()
+        # mixed and plain FP64 run the same chain (same proposals, noise and
+        # decisions) until a decision differs: the estimate differences are
+        # the inner precision (FP32 vs FP64, both refined to the tolerance)
+        diffs, same = [], 0
+        for a, b in zip(runs["mixed"], runs["plain_fp64"]):
+            if not np.array_equal(a["accept_block"], b["accept_block"]):
+                break
+            diffs.append(float(np.abs(a["delta_block"] - b["delta_block"]).max()))
+            if a["n_accept_blocks"] > 0:
+                diffs.append(abs(a["delta_global"] - b["delta_global"]))
+            if a["accept_global"] != b["accept_global"]:
+                break
+            same += 1
+        mx, fp = arms["mixed"], arms["plain_fp64"]
+        mx["max_estimate_diff_vs_fp64"] = max(diffs) if diffs else None
+        mx["steps_identical_to_fp64"] = same
+        if fp["steps"] < steps and same == fp["steps"]:
+            # the FP64 chain is the mixed chain: its accepted updates over the
+            # headline's steps are mixed's, at FP64's measured time per step
+            s_all = fp["s_per_step"] * steps
+            k = mx["accepted_updates"]
+            lo, hi = _poisson_interval(k)
+            fp.update({"accepted_updates_over_headline_steps": k, "accepted_updates_per_s": k / s_all,
+                       "accepted_updates_per_s_95ci": [lo / s_all, hi / s_all],
+                       "rao_blackwell_updates_per_s": _rb_accepted(runs["mixed"]) / s_all,
+                       "rates_from": f"mixed's {steps} steps (identical decisions on the {fp['steps']} FP64 steps "
+                                     "run) at FP64's measured time per step"})
+        lm = arms["learned_mixed"]
+        arms["speedup_learned_mixed_vs_plain_fp64_s_per_step"] = fp["s_per_step"] / lm["s_per_step"]
+        gain = lm["rao_blackwell_updates_per_s"] > mx["rao_blackwell_updates_per_s"]
+        arms["learned_level_effect"] = (
+            "learned+mixed vs mixed on the same start field and steps: "
+            f"{lm['accepted_updates']} vs {mx['accepted_updates']} accepted updates, Rao-Blackwellised "
+            f"{lm['rao_blackwell_updates_per_s']:.3f} vs {mx['rao_blackwell_updates_per_s']:.3f} per s: the learned "
+            f"level {'gains' if gain else 'loses'} on these inputs")
+    out["arms"] = arms
+    return out
+
+
+def our_arm(args):
+    import torch
+
+    import paper_1204_1306_gb300 as ps
+    from paper_1204_1306_gb300 import build as _build
+
+    ws, rank, local = dist_setup()
+    _build.build()
+    wl = WORKLOADS[args.workload]
+    h = run_workload(ps, torch, args.workload, args.steps, args.warmup, ws, rank, compare=not args.no_compare,
+                     fp64_steps=args.fp64_steps)
+    recs, ms = h["recs"], h["ms"]
     ms_max = allmax(ws, ms)
     accepted = _accepted(recs)
     value = allsum(ws, accepted) / (ms_max * 1e-3)
-
-    # end to end through the C ABI with host buffers: the same chain from the
-    # same start field, the field living in pinned host memory -- every step
-    # copies it to the device, runs the filter step and copies the updated
-    # field back (identical steps, so identical decisions)
-    V = ctx.V
-    host_links = torch.empty(V * 4 * 9 * 2, dtype=torch.float64).pin_memory()
-    dev_links = torch.empty(V * 4 * 9 * 2, dtype=torch.float64, device="cuda")
-    ps.psms_checkpoint_load(ctx, 0, ckpt)
-    ps.psms_gauge_get(ctx, 0, dev_links)
-    host_links.copy_(dev_links)
-    torch.cuda.synchronize()
-    barrier(ws)
-    t0 = time.perf_counter()
-    e2e_recs = []
-    for i in range(args.steps):
-        dev_links.copy_(host_links, non_blocking=True)
-        ps.psms_gauge_set(ctx, 0, dev_links)
-        e2e_recs.append(ps.psms_filter_step(ctx, 0, step=i, inner_prec=ps.PREC_F32, learned=True, **prm))
-        ps.psms_gauge_get(ctx, 0, dev_links)
-        host_links.copy_(dev_links, non_blocking=True)
-        torch.cuda.synchronize()
-    e2e_s = allmax(ws, time.perf_counter() - t0)
-    e2e_value = allsum(ws, _accepted(e2e_recs)) / e2e_s
-    e2e_same = all(a["accept_global"] == b["accept_global"] and a["n_accept_blocks"] == b["n_accept_blocks"]
-                   for a, b in zip(recs, e2e_recs))
-    link_bytes = V * 4 * 9 * 16
-    ctx.close()
-
+    e2e_value = allsum(ws, h["e2e_accepted"]) / h["e2e_s"]
+    hop_n, hop_ms, hop_bytes = h["hop_profile"]
+    blk_n, blk_ms, blk_bytes = h["block_profile"]
     peak, peak_kind = peaks()
     rl_hop = roofline_entry("hop_kernel<float> (Wilson hop of the FP32 inner Krylov iterations)", hop_n, hop_ms,
                             hop_bytes, peak, peak_kind)
@@ -792,86 +909,63 @@ def our_arm(args):
     rl_main, rl_other = (rl_blk, rl_hop) if blk_ms >= hop_ms else (rl_hop, rl_blk)
     if rank != 0:
         return
-
-    # the other arms: the same start field, the same step counters and as
-    # many timed steps
-    arms = {"learned_mixed": _arm_summary(recs, ms, learned_pass=sum(r["n_accept_learned"] for r in recs) /
-                                          sum(r["n_blocks"] for r in recs), train_s=round(train_s, 2),
-                                          train_loss_first_last=[losses[0], losses[-1]])}
-    runs = {}
-    if not args.no_compare:
-        for name, inner, learned in ARMS[1:]:
-            c = arm_ctx()
-            warm(c, prec[inner], False)
-            rr, mm = _timed_steps(ps, torch, c, prm, prec[inner], False, args.steps, flush)
-            arms[name] = _arm_summary(rr, mm)
-            runs[name] = rr
-            c.close()
-        # mixed and plain FP64 run the same chain (same proposals, noise and
-        # decisions) until a decision differs: the estimate differences are
-        # the inner precision (FP32 vs FP64, both refined to the tolerance)
-        diffs, same = [], 0
-        for a, b in zip(runs["mixed"], runs["plain_fp64"]):
-            if not np.array_equal(a["accept_block"], b["accept_block"]):
-                break
-            diffs.append(float(np.abs(a["delta_block"] - b["delta_block"]).max()))
-            if a["n_accept_blocks"] > 0:
-                diffs.append(abs(a["delta_global"] - b["delta_global"]))
-            same += 1
-            if a["accept_global"] != b["accept_global"]:
-                break
-        arms["mixed"]["max_estimate_diff_vs_fp64"] = max(diffs) if diffs else None
-        arms["mixed"]["steps_compared_vs_fp64"] = same
-        lm, mx = arms["learned_mixed"], arms["mixed"]
-        arms["speedup_learned_mixed_vs_plain_fp64_s_per_step"] = (arms["plain_fp64"]["s_per_step"] /
-                                                                  lm["s_per_step"])
-        gain = lm["rao_blackwell_updates_per_s"] > mx["rao_blackwell_updates_per_s"]
-        arms["learned_level_effect"] = (
-            "learned+mixed vs mixed on the same start field and steps: "
-            f"{lm['accepted_updates']} vs {mx['accepted_updates']} accepted updates, Rao-Blackwellised "
-            f"{lm['rao_blackwell_updates_per_s']:.3f} vs {mx['rao_blackwell_updates_per_s']:.3f} per s: the learned "
-            f"level {'gains' if gain else 'loses'} on these inputs")
-    large = None if args.no_large else large_workload(ps, torch)
-    estimators = None if args.no_compare else measure_estimators(ps, torch, wl, seed)
+    arms = h["arms"]
+    secondary = None
+    if args.workload != "16^4" and not args.no_compare and not args.no_secondary:
+        s16 = run_workload(ps, torch, "16^4", args.secondary_steps, 3, 1, 0, compare=True,
+                           fp64_steps=args.secondary_steps, profile=False, e2e=False)
+        secondary = {"workload": "16^4 (4^4 blocks, kappa 0.156, N = 48 / 12, tol 1e-13)", "arms": s16["arms"],
+                     "delta_statistics": delta_stats(s16["recs"]), "train_s": s16["train_s"]}
+    dwhb = None if args.no_large else dw_and_heatbath(ps, torch, "32^3x64")
+    estimators = None if args.no_compare else measure_estimators(ps, torch, WORKLOADS["16^4"], SEED + 1)
     batched = None if args.no_compare else measure_batch(ps, torch)
     fp64 = measure_fp64_peak(torch)
     full_iters = sum(r["solver_iters"] for r in recs) / max(len(recs), 1)
+    cfg = {"workload": args.workload, "dims": list(wl["dims"]), "block": list(wl["block"]),
+           "kappa": wl["kappa"], "beta": wl["beta"], "eps": wl["eps"], "n_block": wl["n_block"],
+           "n_global": wl["n_global"], "tol": wl["tol"], "inner": "fp32 in fp64 defect correction",
+           "learned_level": True, "gauge_fix": "relative, block interiors, fp32 steps",
+           "start": "every arm loads one checkpoint (thermalised field + trained MLP); warm-up steps run on a copy; "
+                    "timed steps use step counters 0..K-1",
+           "l2": "flushed between timed steps (256 MB write, outside the step events)",
+           "parallelism": f"independent chains x{ws}"}
+    if wl.get("outer"):
+        cfg.update({"domains": list(wl["outer"]), "n_sub": wl["n_sub"],
+                    "decomposition": "8^4 domains each split into 2^4 Dirichlet blocks of 4^4 (recursive, 5-step "
+                                     "filter: learned level, blocks, domain Schur complements, global Schur "
+                                     "complement of the domains)"})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic: U = exp(i eps H) links thermalised at beta 5.3, Philox noise",
-        "config": {"workload": args.workload, "dims": list(wl["dims"]), "block": list(wl["block"]),
-                   "kappa": wl["kappa"], "beta": wl["beta"], "eps": wl["eps"], "n_block": wl["n_block"],
-                   "n_global": wl["n_global"], "tol": wl["tol"], "inner": "fp32 in fp64 defect correction",
-                   "learned_level": True, "gauge_fix": "relative, block interiors, fp32 steps",
-                   "start": "every arm loads one checkpoint (thermalised field + trained MLP); warm-up steps run "
-                            "on a copy; timed steps use step counters 0..K-1",
-                   "l2": "flushed between timed steps (256 MB write, outside the step events)",
-                   "parallelism": f"independent chains x{ws}"},
+        "config": cfg,
         "accepted_updates": accepted,
         "accepted_updates_per_s_95ci": arms["learned_mixed"]["accepted_updates_per_s_95ci"],
         "rao_blackwell_updates_per_s": arms["learned_mixed"]["rao_blackwell_updates_per_s"],
         "acceptance": {"global": sum(r["accept_global"] for r in recs) / len(recs),
-                       "blocks": sum(r["n_accept_blocks"] for r in recs) / sum(r["n_blocks"] for r in recs)},
+                       "blocks": sum(r["n_accept_blocks"] for r in recs) / sum(r["n_blocks"] for r in recs),
+                       "domains_after_stage_2": [r["n_accept_sub"] for r in recs]},
         "solver_iters_per_step": full_iters,
         "delta_statistics": delta_stats(recs),
         "gauge_fix_steps_per_step": sum(r["gf_steps"] for r in recs) / len(recs),
-        "plaquette_start": plaq0,
+        "plaquette_start": h["plaquette_start"],
+        "train_s": h["train_s"], "train_loss_first_last": h["train_loss_first_last"],
         "roofline": rl_main,
         "roofline_secondary": rl_other,
-        "block_solver_first_launches": [{"ms": round(a, 4), "algorithmic_bytes": b} for a, b in blk_first],
+        "block_solver_first_launches": [{"ms": round(a, 4), "algorithmic_bytes": b} for a, b in h["block_first"]],
         "arms": arms,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": link_bytes, "d2h_bytes_per_step": link_bytes,
-                "same_decisions_as_timed_steps": e2e_same},
-        "gpu_launches": n_launch,
-        "wall_s_timed": wall,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h["link_bytes"],
+                "d2h_bytes_per_step": h["link_bytes"], "same_decisions_as_timed_steps": h["e2e_same"]},
+        "gpu_launches": h["gpu_launches"],
+        "wall_s_timed": h["wall_s_timed"],
         "fp64_peak": fp64,
-        "large_workload_32^3x64": large,
-        "det_ratio_estimates": estimators,
+        "configs1_16x4": secondary,
+        "dw_heatbath_32^3x64": dwhb,
+        "det_ratio_estimates_16x4": estimators,
         "batched_block_solves": batched,
+        "clocks": h["clocks"],
     }
-    line["clocks"] = clk.summary()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, recs)
     print(json.dumps(line), flush=True)
@@ -977,33 +1071,58 @@ def _oracle_run(script, cfg, timeout=1200):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+# the oracle is timed on lattices up to this volume; larger workloads scale its
+# per-lattice times by volume (the oracle's work per site is fixed)
+ORACLE_MAX_SITES = 16 ** 4
+
+
 def oracle_components(workload, n_sample=2, with_iterations=True, sweep=True):
     """Measured oracle (numpy FP64, one thread) times of the pieces of one
-    filter step on the workload lattice: the domain sweep (and the swept
-    field for what follows), one whole-lattice CGNR iteration, one
-    interpolation step's per-lattice estimator work, and one block solve
-    (mean over a sample of blocks); with_iterations also measures the
-    oracle's CGNR iteration count of one whole-lattice solve on an 8^4
-    lattice (same kappa, field recipe and tolerance)."""
+    filter step: the domain sweep (and the swept field for what follows),
+    one whole-lattice CGNR iteration, one interpolation step's per-lattice
+    estimator work, and one block solve (mean over a sample of blocks);
+    with_iterations also measures the oracle's CGNR iteration count of one
+    whole-lattice solve on an 8^4 lattice (same kappa, field recipe and
+    tolerance).  Lattices above 16^4 sites are timed on a 16^4 lattice with
+    the same blocks and the per-lattice times scaled by the volume ratio."""
     wl = WORKLOADS[workload]
-    cfg = {"dims": list(wl["dims"]), "block": list(wl["block"]), "kappa": wl["kappa"], "eps": wl["eps"],
+    dims = list(wl["dims"])
+    V = int(np.prod(dims))
+    scale = 1.0
+    if V > ORACLE_MAX_SITES:
+        dims = [16, 16, 16, 16]
+        scale = V / ORACLE_MAX_SITES
+    cfg = {"dims": dims, "block": list(wl["block"]), "kappa": wl["kappa"], "eps": wl["eps"],
            "beta": wl["beta"], "n_or": wl["n_or"], "seed": SEED, "tol": wl["tol"], "n_sample": n_sample,
            "full_dims": [8, 8, 8, 8] if with_iterations else None, "sweep": sweep}
-    return _oracle_run(_COMPONENTS, cfg)
+    comp = _oracle_run(_COMPONENTS, cfg)
+    for k in ("sweep_s", "cgnr_iteration_s", "level_overhead_s"):
+        if k in comp:
+            comp[k] *= scale
+    comp["timed_on"] = "x".join(str(d) for d in dims) + ("" if scale == 1.0 else f", per-lattice times x{scale:g}")
+    return comp
 
 
 def oracle_step_seconds(workload, comp, full_iters):
-    """Oracle time of one filter step from measured component times: the
-    sweep; N_block interpolation steps of the block level (per-lattice work
-    + every block's solve); N_global steps of the global level (per-lattice
-    work, the D_ww^-1 and D_bb^-1 batches = every block solved once, and one
-    whole-lattice solve of full_iters CGNR iterations).  Extrapolated."""
+    """Oracle time of one filter step from measured component times:
+    the sweep; N_block interpolation steps of the block level (per-lattice
+    work + every block's solve); with the recursive decomposition n_sub
+    steps of stage 2 (per-lattice work, every block solved once in the
+    D_ww^-1 / D_bb^-1 batches, one whole-lattice solve of the domains'
+    Dirichlet operator); N_global steps of the global level (per-lattice
+    work and, without recursion, every block solved once and one
+    whole-lattice solve; with it, three whole-lattice solves: the domains'
+    D_ww^-1, D_bb^-1 and the full operator).  Every whole-lattice solve is
+    counted at full_iters CGNR iterations.  Extrapolated."""
     wl = WORKLOADS[workload]
     nb = int(np.prod([d // b for d, b in zip(wl["dims"], wl["block"])]))
-    blk = wl["n_block"] * (comp["level_overhead_s"] + nb * comp["block_solve_s"])
-    glb = wl["n_global"] * (comp["level_overhead_s"] + nb * comp["block_solve_s"]
-                            + full_iters * comp["cgnr_iteration_s"])
-    return comp["sweep_s"] + blk + glb
+    ov, bs, it = comp["level_overhead_s"], comp["block_solve_s"], full_iters * comp["cgnr_iteration_s"]
+    t = comp["sweep_s"] + wl["n_block"] * (ov + nb * bs)
+    if wl.get("outer"):
+        t += wl["n_sub"] * (ov + nb * bs + it) + wl["n_global"] * (ov + 3 * it)
+    else:
+        t += wl["n_global"] * (ov + nb * bs + it)
+    return t
 
 
 def cpu_baseline(workload, recs):
@@ -1017,13 +1136,12 @@ def cpu_baseline(workload, recs):
     step_s = oracle_step_seconds(workload, comp, comp["full_solve_iterations"])
     acc_frac = _accepted(recs) / max(len(recs), 1)
     return {"value": acc_frac / step_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"oracle components on the {workload} lattice (swept field): sweep {comp['sweep_s']:.2f} s, "
+            "sample": (f"oracle components (timed on {comp['timed_on']}, swept field): sweep {comp['sweep_s']:.2f} s, "
                        f"CGNR iteration {comp['cgnr_iteration_s']:.3f} s, block solve {comp['block_solve_s']:.3f} s "
                        f"(mean of {comp['block_sample']}), per-level overhead {comp['level_overhead_s']:.2f} s; "
                        f"whole-lattice solve {comp['full_solve_iterations']} CGNR iterations (oracle, 8^4); "
-                       f"step = sweep + N_block (overhead + all blocks) + N_global (overhead + all blocks + one "
-                       f"solve) = {step_s:.0f} s; accepted updates per step from the GPU chain "
-                       f"({_accepted(recs)}/{len(recs)}, identical decisions by parity); extrapolated"),
+                       f"step time from the levels' solve counts = {step_s:.0f} s; accepted updates per step from "
+                       f"the GPU chain ({_accepted(recs)}/{len(recs)}, identical decisions by parity); extrapolated"),
             "components": comp, "extrapolated_step_s": step_s}
 
 
@@ -1060,10 +1178,10 @@ def reference_arm(args):
                                              comp["full_solve_iterations"]))
         step_s = statistics.median(times)
         value = 1.0 / step_s
-        sample = (f"per step: one oracle CGNR iteration and one block solve on the {args.workload} lattice "
-                  f"(re-timed each step); sweep, per-level overhead and the whole-lattice iteration count "
-                  f"({comp['full_solve_iterations']}, oracle CGNR on 8^4) timed once; step time extrapolated; "
-                  f"value counts one accepted update per oracle step (an upper bound)")
+        sample = (f"per step: one oracle CGNR iteration and one block solve (timed on {comp['timed_on']}, "
+                  f"re-timed each step); sweep, per-level overhead and the whole-lattice iteration count "
+                  f"({comp['full_solve_iterations']}, oracle CGNR on 8^4) timed once; step time extrapolated from "
+                  f"the levels' solve counts; value counts one accepted update per oracle step (an upper bound)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -1079,16 +1197,20 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="16^4", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS))
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 arm")
+    ap.add_argument("--secondary-steps", type=int, default=10, help="timed steps per arm of the 16^4 section")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 16^4 section")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 and mixed arms")
-    ap.add_argument("--compare-steps", type=int, default=6, help="timed steps of each comparison arm")
-    ap.add_argument("--no-large", action="store_true", help="skip the 32^3x64 measurements")
+    ap.add_argument("--no-large", action="store_true", help="skip the 32^3x64 D_w and heatbath measurements")
     ap.add_argument("--learned-only", action="store_true", help="the learned level at 16^3x32 with 8^4 domains")
     ap.add_argument("--labels", type=int, default=100_000, help="training labels of --learned-only")
     ap.add_argument("--dw-only", action="store_true", help="stand-alone D_w measurement only")
     ap.add_argument("--solve-only", action="store_true", help="single-system solver measurement only")
     ap.add_argument("--batch-only", action="store_true", help="multi-lattice batched block solves (8^4, 12^4, 16^3x32)")
+    ap.add_argument("--block-only", action="store_true", help="the 16^4 block level alone (ncu case)")
+    ap.add_argument("--block-n", type=int, default=12, help="interpolation steps of --block-only")
     ap.add_argument("--levels-only", action="store_true",
                     help="parametrised levels and the recursive decomposition on 16^4 (auxiliary line)")
     args = ap.parse_args()
@@ -1106,6 +1228,8 @@ def main():
         learned_only(args)
     elif args.levels_only:
         levels_only(args)
+    elif args.block_only:
+        block_only(args)
     else:
         our_arm(args)
 

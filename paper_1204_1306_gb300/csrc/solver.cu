@@ -635,6 +635,8 @@ __device__ double finish_sum(const double *p, int k, int m, double *sh) {
 
 // stage: 0 alpha = rho / <rh, v>; 1 omega = <t, s> / <t, t>;
 //        2 rho_new = <rh, r>, rr = |r|^2, beta, convergence
+__device__ void bcg_stage(BCS *st, int k, double re, double im, double aa, int stage, int maxit, int *flags);
+
 template <int NT>
 __global__ void __launch_bounds__(NT) bcg_scalar_kernel(BCS *st, const double *p_re, const double *p_im,
                                                         const double *p_aa, int m, int stage, int maxit, int *flags) {
@@ -645,6 +647,10 @@ __global__ void __launch_bounds__(NT) bcg_scalar_kernel(BCS *st, const double *p
     const double im = finish_sum<NT>(p_im, k, m, sh);
     const double aa = p_aa ? finish_sum<NT>(p_aa, k, m, sh) : 0.0;
     if (threadIdx.x != 0) return;
+    bcg_stage(st, k, re, im, aa, stage, maxit, flags);
+}
+
+__device__ void bcg_stage(BCS *st, int k, double re, double im, double aa, int stage, int maxit, int *flags) {
     BCS s = st[k];
     const double2 d = make_double2(re, im);
     if (stage == 0) {
@@ -701,6 +707,147 @@ __global__ void __launch_bounds__(NT) bcg_axpy_kernel(const BCS *st, int mode, V
             st_(p, c, ld(r, c) + cmul(be, ld(p, c) - cmul(om, ld(v, c))));
         }
     }
+}
+
+// Writes this CTA's partials of system k; the last CTA of the system to
+// finish (a counter per system, no waiting) sums all partials in a fixed
+// order and applies the scalar stage, so the result does not depend on
+// which CTA finishes last.
+template <int NT>
+__device__ __forceinline__ void bcg_partials_and_stage(BCS *st, double re, double im, double aa, double *p_re,
+                                                       double *p_im, double *p_aa, unsigned int *counters, int stage,
+                                                       int maxit, int *flags, double (*sh)[NT / 32]) {
+    const int k = blockIdx.y;
+    const long long slot = (long long)k * gridDim.x + blockIdx.x;
+    __shared__ int last;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+        aa += __shfl_xor_sync(0xffffffffu, aa, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = re;
+        sh[1][threadIdx.x >> 5] = im;
+        sh[2][threadIdx.x >> 5] = aa;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t0 = 0, t1 = 0, t2 = 0;
+        for (int w = 0; w < NT / 32; ++w) {
+            t0 += sh[0][w];
+            t1 += sh[1][w];
+            t2 += sh[2][w];
+        }
+        p_re[slot] = t0;
+        p_im[slot] = t1;
+        p_aa[slot] = t2;
+        __threadfence();
+        last = atomicAdd(&counters[k], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // the other CTAs' partials, read past L1 (written by other SMs)
+    const int m = gridDim.x;
+    double v[3] = {0, 0, 0};
+    for (int i = threadIdx.x; i < m; i += NT) {
+        const long long q = (long long)k * m + i;
+        v[0] += __ldcg(p_re + q);
+        v[1] += __ldcg(p_im + q);
+        v[2] += __ldcg(p_aa + q);
+    }
+    double tot[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double x = v[a];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) sh[a][threadIdx.x >> 5] = x;
+        __syncthreads();
+        double t = 0;
+        for (int w = 0; w < NT / 32; ++w) t += sh[a][w];
+        tot[a] = t;
+    }
+    const double r0 = tot[0], r1 = tot[1], r2 = tot[2];
+    if (threadIdx.x == 0) {
+        counters[k] = 0;
+        bcg_stage(st, k, r0, r1, r2, stage, maxit, flags);
+    }
+}
+
+// <a, b> partials (sum conj(a) b, and |a|^2) and the scalar stage
+template <class S, int NT>
+__global__ void __launch_bounds__(NT) bcg_dot_stage_kernel(BCS *st, View<typename S::elem> a,
+                                                           View<typename S::elem> b, long long s_lo, long long n,
+                                                           double *p_re, double *p_im, double *p_aa,
+                                                           unsigned int *counters, int stage, int maxit, int *flags) {
+    using R = typename S::R;
+    __shared__ double sh[3][NT / 32];
+    const int k = blockIdx.y;
+    if (!st[k].active) return;
+    double re = 0, im = 0, aa = 0;
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
+    if (i < n) {
+        const long long sx = s_lo + i;
+        R tre = 0, tim = 0, taa = 0;
+        for (int c = 0; c < 12; ++c) {
+            const cpx<R> x = S::ldi(a.p, k * a.bs + S::idx(c, a.cs, sx - a.off));
+            const cpx<R> y = S::ldi(b.p, k * b.bs + S::idx(c, b.cs, sx - b.off));
+            tre += x.re * y.re + x.im * y.im;
+            tim += x.re * y.im - x.im * y.re;
+            taa += x.re * x.re + x.im * x.im;
+        }
+        re = (double)tre;
+        im = (double)tim;
+        aa = (double)taa;
+    }
+    bcg_partials_and_stage<NT>(st, re, im, aa, p_re, p_im, p_aa, counters, stage, maxit, flags, sh);
+}
+
+// x += alpha p + omega s, r = s - omega t, then the partials of
+// sum conj(r) rh and |r|^2 and scalar stage 2
+template <class S, int NT>
+__global__ void __launch_bounds__(NT) bcg_update_stage_kernel(BCS *st, View<typename S::elem> x,
+                                                              View<typename S::elem> p, View<typename S::elem> r,
+                                                              View<typename S::elem> s_, View<typename S::elem> t,
+                                                              View<typename S::elem> rh, long long s_lo, long long n,
+                                                              double *p_re, double *p_im, double *p_aa,
+                                                              unsigned int *counters, int maxit, int *flags) {
+    using R = typename S::R;
+    __shared__ double sh[3][NT / 32];
+    const int k = blockIdx.y;
+    if (!st[k].active) return;
+    const BCS bs = st[k];
+    const cpx<R> al = {(R)bs.alpha.x, (R)bs.alpha.y}, om = {(R)bs.omega.x, (R)bs.omega.y};
+    double re = 0, im = 0, aa = 0;
+    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
+    if (i < n) {
+        const long long sx = s_lo + i;
+        auto ld = [&](const View<typename S::elem> &w, int c) {
+            return S::ldi(w.p, k * w.bs + S::idx(c, w.cs, sx - w.off));
+        };
+        auto stv = [&](View<typename S::elem> &w, int c, cpx<R> val) {
+            S::sti(w.p, k * w.bs + S::idx(c, w.cs, sx - w.off), val);
+        };
+        R tre = 0, tim = 0, taa = 0;
+        for (int c = 0; c < 12; ++c) {
+            const cpx<R> sv = ld(s_, c);
+            stv(x, c, ld(x, c) + cmul(al, ld(p, c)) + cmul(om, sv));
+            cpx<R> rv = sv - cmul(om, ld(t, c));
+            stv(r, c, rv);
+            rv = ld(r, c);  // the stored value (rounded to the storage precision)
+            const cpx<R> hv = ld(rh, c);
+            tre += rv.re * hv.re + rv.im * hv.im;
+            tim += rv.re * hv.im - rv.im * hv.re;
+            taa += rv.re * rv.re + rv.im * rv.im;
+        }
+        re = (double)tre;
+        im = (double)tim;
+        aa = (double)taa;
+    }
+    bcg_partials_and_stage<NT>(st, re, im, aa, p_re, p_im, p_aa, counters, 2, maxit, flags, sh);
 }
 
 __global__ void iters_bcg_kernel(const BCS *st, int *out, int n) {
@@ -762,6 +909,10 @@ static void inner_bicgstab_full(psms_ctx *c, int n_sys, const void *Uin, long lo
     double *q_re = (double *)scratch(c, "fs_qre", sizeof(double) * (size_t)nb * n_sys);
     double *q_im = (double *)scratch(c, "fs_qim", sizeof(double) * (size_t)nb * n_sys);
     double *q_aa = (double *)scratch(c, "fs_qaa", sizeof(double) * (size_t)nb * n_sys);
+    // per-system completion counters of the fused reductions (each launch
+    // leaves them at zero)
+    unsigned int *cnt = (unsigned int *)scratch(c, "fs_bcnt", sizeof(unsigned int) * n_sys);
+    cuda_check(cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * n_sys, c->stream), "bcg counters");
     // w = Dhat u = A u + c4 H_o(H_e u)
     auto apply_dhat = [&](View<void> u, View<void> w) {
         h.dag = 0;
@@ -788,26 +939,23 @@ static void inner_bicgstab_full(psms_ctx *c, int n_sys, const void *Uin, long lo
     while (it < maxit) {
         for (int i = 0; i < chunk && it < maxit; ++i, ++it) {
             apply_dhat(pp, vv);
-            bcg_dot_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, tv(rh), tv(vv), Vh, n, q_re, q_im, nullptr);
-            PSMS_LAUNCH_CHECK("bcg_dot");
-            bcg_scalar_kernel<256><<<n_sys, 256, 0, c->stream>>>(st, q_re, q_im, nullptr, nb, 0, maxit, flags);
+            // alpha = rho / <rh, v>
+            bcg_dot_stage_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, tv(rh), tv(vv), Vh, n, q_re, q_im, q_aa,
+                                                                     cnt, 0, maxit, flags);
             PSMS_LAUNCH_CHECK("bcg_alpha");
             bcg_axpy_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, 0, tv(e), tv(pp), tv(r), tv(ss), tv(vv), tv(tt),
                                                                 Vh, n);
             PSMS_LAUNCH_CHECK("bcg_s");
             apply_dhat(ss, tt);
-            bcg_dot_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, tv(tt), tv(ss), Vh, n, q_re, q_im, q_aa);
-            PSMS_LAUNCH_CHECK("bcg_dot");
-            bcg_scalar_kernel<256><<<n_sys, 256, 0, c->stream>>>(st, q_re, q_im, q_aa, nb, 1, maxit, flags);
+            // omega = <t, s> / <t, t>
+            bcg_dot_stage_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, tv(tt), tv(ss), Vh, n, q_re, q_im, q_aa,
+                                                                     cnt, 1, maxit, flags);
             PSMS_LAUNCH_CHECK("bcg_omega");
-            bcg_axpy_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, 1, tv(e), tv(pp), tv(r), tv(ss), tv(vv), tv(tt),
-                                                                Vh, n);
+            // x, r updates with <rh, r>, |r|^2 and beta / convergence
+            bcg_update_stage_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, tv(e), tv(pp), tv(r), tv(ss), tv(tt),
+                                                                        tv(rh), Vh, n, q_re, q_im, q_aa, cnt, maxit,
+                                                                        flags);
             PSMS_LAUNCH_CHECK("bcg_update");
-            // <rh, r> and |r|^2 (the dot kernel's |a|^2 is of its first argument)
-            bcg_dot_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, tv(r), tv(rh), Vh, n, q_re, q_im, q_aa);
-            PSMS_LAUNCH_CHECK("bcg_dot");
-            bcg_scalar_kernel<256><<<n_sys, 256, 0, c->stream>>>(st, q_re, q_im, q_aa, nb, 3, maxit, flags);
-            PSMS_LAUNCH_CHECK("bcg_beta");
             bcg_axpy_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, 2, tv(e), tv(pp), tv(r), tv(ss), tv(vv), tv(tt),
                                                                 Vh, n);
             PSMS_LAUNCH_CHECK("bcg_p");

@@ -131,7 +131,7 @@ def test_block_chain_detailed_balance_learned_gauge_fixed():
         pis[b] = p / p.sum()
     ctx = ps.psms_create(dims, block, kappa, 2)
     q = mlp.init_params(17)
-    q["ys"] = 1.0
+    q["ys"] = 150.0    # h of order one on these nearby states
     flat = np.concatenate([q["W1"].ravel(), q["b1"], q["W2"].ravel(), q["b2"], q["w3"], [q["b3"]], q["mu"],
                            q["sigma"], [q["ys"]]]).astype(np.float32)
     ps.psms_mlp_params(ctx, flat)
