@@ -42,7 +42,7 @@ WORKLOADS = {
     # decomposition (None: one level), kappa, eps, beta, interpolation steps per level,
     # thermalisation iterations, proposal sweeps, tolerance, proposals for the learned level's labels
     "32^3x64": dict(dims=(64, 32, 32, 32), block=(4, 4, 4, 4), outer=(8, 8, 8, 8), kappa=0.157, eps=0.5,
-                    beta=5.3, n_block=12, n_sub=12, n_global=24, therm=4, n_iter=1, n_or=2, tol=1e-10,
+                    beta=5.3, n_block=12, n_sub=12, n_global=24, therm=4, n_iter=1, n_or=2, tol=1e-12,
                     train_props=8),
     "16^4": dict(dims=(16, 16, 16, 16), block=(4, 4, 4, 4), outer=None, kappa=0.156, eps=0.5, beta=5.3, n_block=48,
                  n_sub=0, n_global=12, therm=4, n_iter=1, n_or=1, tol=1e-13, train_props=48),

@@ -493,8 +493,11 @@ psms_status psms_checkpoint_load(psms_ctx *ctx, int field, const char *path, uin
  * 10..13, (1,4) with the branch-free hop out of line for 14, and with
  * BiCGStab on Dhat instead of CGNR: (1,4) branch-free for 15, (1,4) out of
  * line for 16, (8,4) branch-free for 17 (falling back to 0 when the block is
- * too small for the cluster); -1 restores the tuned choice.  Clears the
- * tuning cache.  PSMS_EINVAL outside -1..17.  Variants of one Krylov method
+ * too small for the cluster), and with the block's FP32 links staged once
+ * into shared memory (FP32 inner iterations, blocks whose links take at
+ * most 100 KB, e.g. 4^4): (1,3) inlined for 18, branch-free for 19, out of
+ * line for 20 (falling back to 0 otherwise); -1 restores the tuned choice.
+ * Clears the tuning cache.  PSMS_EINVAL outside -1..20.  Variants of one Krylov method
  * give identical results; the two methods agree to the solve tolerance. */
 psms_status psms_autotune(psms_ctx *ctx, int enable, int block_variant);
 

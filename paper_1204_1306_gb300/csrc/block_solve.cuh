@@ -10,6 +10,7 @@
 #include "solver.hpp"
 
 #include <cooperative_groups.h>
+#include <type_traits>
 
 namespace psms {
 
@@ -72,7 +73,54 @@ __device__ __forceinline__ void bar() {
 // a direction that leaves the block contributes an exact zero, so the eight
 // hops run as one straight sequence whose loads the compiler can issue early;
 // the result equals the branching form bit for bit.
-template <class S, class SL, class SY, int BF = 0>
+// Link of direction mu at the site with internal index s of parity q, from
+// global memory (LSM = 0) or from the block's copy in shared memory
+// (LSM = 1: layout of the global FP32 field with V -> 2 Vbh and the site at
+// q Vbh + its index in the block's parity half; plain loads).
+template <class SL, int LSM>
+__device__ __forceinline__ SU3<typename SL::R> blk_link(const Geom &g, const typename SL::elem *U, int r, int q,
+                                                        int mu, long long s) {
+    if constexpr (LSM) {
+        const long long l = (long long)q * g.Vbh + (s - (long long)q * g.Vh - (long long)r * g.Vbh);
+        const long long Vl = 2LL * g.Vbh;
+        SU3<typename SL::R> u;
+        const float2 *base = reinterpret_cast<const float2 *>(U) + (long long)mu * 9 * Vl;
+        const float4 *q4 = reinterpret_cast<const float4 *>(base);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 w = q4[k * Vl + l];
+            u.e[(2 * k) / 3][(2 * k) % 3] = {w.x, w.y};
+            u.e[(2 * k + 1) / 3][(2 * k + 1) % 3] = {w.z, w.w};
+        }
+        const float2 w = base[8 * Vl + l];
+        u.e[2][2] = {w.x, w.y};
+        return u;
+    } else {
+        return load_link<SL>(U, g.V, mu, s);
+    }
+}
+
+// Copy the FP32 links of every site of block r into shared memory (the
+// layout blk_link<SL, 1> reads).
+template <int NT>
+__device__ __forceinline__ void stage_block_links(const Geom &g, const float2 *U, int r, float2 *sm) {
+    const long long Vl = 2LL * g.Vbh;
+    for (long long t = threadIdx.x; t < 4 * Vl; t += NT) {
+        const int mu = (int)(t / Vl);
+        const long long l = t - (long long)mu * Vl;
+        const int q = l >= g.Vbh ? 1 : 0;
+        const long long s = (long long)q * g.Vh + (long long)r * g.Vbh + (l - (long long)q * g.Vbh);
+        const float2 *gb = U + (long long)mu * 9 * g.V;
+        float2 *sb = sm + (long long)mu * 9 * Vl;
+        const float4 *g4 = reinterpret_cast<const float4 *>(gb);
+        float4 *s4 = reinterpret_cast<float4 *>(sb);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s4[k * Vl + l] = __ldg(g4 + k * g.V + s);
+        sb[8 * Vl + l] = __ldg(gb + 8 * g.V + s);
+    }
+}
+
+template <class S, class SL, class SY, int BF = 0, int LSM = 0>
 __device__ __forceinline__ double block_hop(const Geom &g, const BlockInfo &bi, int r, int p, int dag,
                                             const typename S::elem *in, long long in_cs, long long in_off,
                                             typename S::elem *out, long long out_cs, long long out_off,
@@ -110,7 +158,7 @@ __device__ __forceinline__ double block_hop(const Geom &g, const BlockInfo &bi, 
                 for (int q = 0; q < 2; ++q)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) h.c[q][c] = keep[d] * h.c[q][c];
-                SU3<R> u = load_link<SL>(U, g.V, mu, fwd ? s : snb[d]);
+                SU3<R> u = blk_link<SL, LSM>(g, U, r, fwd ? p : 1 - p, mu, fwd ? s : snb[d]);
                 reconstruct_add(mu, tt, fwd ? su3_mul(u, h) : su3_dag_mul(u, h), acc);
             }
         } else {
@@ -122,14 +170,14 @@ __device__ __forceinline__ double block_hop(const Geom &g, const BlockInfo &bi, 
                 Spinor<R> v = load_spinor<S>(in, in_cs, sn - in_off);
                 const R tf = -sg;
                 Half<R> h = project(mu, tf, v);
-                SU3<R> u = load_link<SL>(U, g.V, mu, s);
+                SU3<R> u = blk_link<SL, LSM>(g, U, r, p, mu, s);
                 reconstruct_add(mu, tf, su3_mul(u, h), acc);
             }
             if (neighbour(g, bi, r, p, yy, ll, mu, -1, HOP_INTRA, sn, bs)) {
                 Spinor<R> v = load_spinor<S>(in, in_cs, sn - in_off);
                 const R tb = sg;
                 Half<R> h = project(mu, tb, v);
-                SU3<R> u = load_link<SL>(U, g.V, mu, sn);
+                SU3<R> u = blk_link<SL, LSM>(g, U, r, 1 - p, mu, sn);
                 reconstruct_add(mu, tb, su3_dag_mul(u, h), acc);
             }
         }
@@ -164,17 +212,18 @@ __device__ __forceinline__ double block_hop(const Geom &g, const BlockInfo &bi, 
 // The same hop as an out-of-line function: one copy of its code serves every
 // call site of the block CG (instruction-cache footprint), at the price of a
 // call and of no specialisation on constant arguments.
-template <class S, class SL, class SY, int BF>
+template <class S, class SL, class SY, int BF, int LSM>
 __device__ __noinline__ double block_hop_ool(const Geom &g, const BlockInfo &bi, int r, int p, int dag,
                                              const typename S::elem *in, long long in_cs, long long in_off,
                                              typename S::elem *out, long long out_cs, long long out_off,
                                              const typename SY::elem *y, long long y_cs, long long y_off, double a,
                                              double b, const typename SL::elem *U, int jlo, int jhi) {
-    return block_hop<S, SL, SY, BF>(g, bi, r, p, dag, in, in_cs, in_off, out, out_cs, out_off, y, y_cs, y_off, a, b,
-                                    U, jlo, jhi);
+    return block_hop<S, SL, SY, BF, LSM>(g, bi, r, p, dag, in, in_cs, in_off, out, out_cs, out_off, y, y_cs, y_off,
+                                         a, b, U, jlo, jhi);
 }
 
-// HV: bit 0 = out-of-line hop, bit 1 = branch-free hop
+// HV: bit 0 = out-of-line hop, bit 1 = branch-free hop, bit 3 = links of
+// the inner-precision hops in shared memory (U then points there)
 template <int HV, class S, class SL, class SY>
 __device__ __forceinline__ double hop_call(const Geom &g, const BlockInfo &bi, int r, int p, int dag,
                                            const typename S::elem *in, long long in_cs, long long in_off,
@@ -182,12 +231,15 @@ __device__ __forceinline__ double hop_call(const Geom &g, const BlockInfo &bi, i
                                            const typename SY::elem *y, long long y_cs, long long y_off, double a,
                                            double b, const typename SL::elem *U, int jlo, int jhi) {
     constexpr int BF = (HV >> 1) & 1;
+    // only the inner-precision links live in shared memory; the FP64
+    // residual hops (S = SL = Store<double>) read global memory
+    constexpr int LSM = ((HV >> 3) & 1) && std::is_same<typename SL::R, float>::value;
     if constexpr (HV & 1)
-        return block_hop_ool<S, SL, SY, BF>(g, bi, r, p, dag, in, in_cs, in_off, out, out_cs, out_off, y, y_cs, y_off,
-                                            a, b, U, jlo, jhi);
+        return block_hop_ool<S, SL, SY, BF, LSM>(g, bi, r, p, dag, in, in_cs, in_off, out, out_cs, out_off, y, y_cs,
+                                                 y_off, a, b, U, jlo, jhi);
     else
-        return block_hop<S, SL, SY, BF>(g, bi, r, p, dag, in, in_cs, in_off, out, out_cs, out_off, y, y_cs, y_off, a,
-                                        b, U, jlo, jhi);
+        return block_hop<S, SL, SY, BF, LSM>(g, bi, r, p, dag, in, in_cs, in_off, out, out_cs, out_off, y, y_cs,
+                                             y_off, a, b, U, jlo, jhi);
 }
 
 template <class E>
@@ -252,6 +304,15 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
     double2 *r64 = a.r64.p + k * a.r64.bs;
     const double2 *U64 = a.U64 + k * a.U64_bs;
     const typename SL::elem *Uin = (const typename SL::elem *)a.Uin + k * a.Uin_bs;
+    if constexpr (((HV >> 3) & 1) && std::is_same<typename SL::R, float>::value) {
+        // the block's inner-precision links, read by every hop of the
+        // Krylov iterations, staged once into shared memory
+        extern __shared__ float4 psms_blk_smem[];
+        float2 *sm = reinterpret_cast<float2 *>(psms_blk_smem);
+        stage_block_links<NT>(g, reinterpret_cast<const float2 *>(Uin), r, sm);
+        __syncthreads();
+        Uin = reinterpret_cast<const typename SL::elem *>(sm);
+    }
     E *base = (E *)a.vin + k * a.vin_bs;
     // inner scratch layout per system: rhs (V), e (V), 6 odd halves, 1 even half
     BlockVecs<E> v;
@@ -573,11 +634,22 @@ __global__ void __launch_bounds__(NT, MINB) block_solve_cluster_kernel(const Blo
     block_solve_item<SV, SL, NT, CL, HV>(a, blockIdx.x / CL, blockIdx.y, sh);
 }
 
+// dynamic shared memory of a variant: the block's FP32 links when HV bit 3
+// is set (4 directions x 9 complex x 2 Vbh sites)
+inline size_t block_links_smem(const Geom &g) { return (size_t)4 * 9 * 2 * g.Vbh * sizeof(float2); }
+
 template <class SV, class SL, int CL, int MINB, int HV = 0>
 void launch_block_cl(psms_ctx *c, const BlockSolveArgs &a, int n_ranks, int n_sys) {
     constexpr int NT = 128;
     if constexpr (CL == 1) {
-        block_solve_cluster_kernel<SV, SL, NT, 1, MINB, HV><<<dim3(n_ranks, n_sys), NT, 0, c->stream>>>(a);
+        size_t smem = 0;
+        if constexpr ((HV >> 3) & 1) {
+            smem = block_links_smem(a.g);
+            cuda_check(cudaFuncSetAttribute(block_solve_cluster_kernel<SV, SL, NT, 1, MINB, HV>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                       "block solver shared memory");
+        }
+        block_solve_cluster_kernel<SV, SL, NT, 1, MINB, HV><<<dim3(n_ranks, n_sys), NT, smem, c->stream>>>(a);
         PSMS_LAUNCH_CHECK("block_solve_cluster_kernel");
     } else {
         cudaLaunchConfig_t cfg = {};
@@ -606,6 +678,7 @@ void launch_block_cl(psms_ctx *c, const BlockSolveArgs &a, int n_ranks, int n_sy
 #define PSMS_BLOCK_VARIANTS_FORMS(X, SV) \
     X(SV, 1, 1, 1) X(SV, 1, 4, 1) X(SV, 1, 1, 2) X(SV, 1, 4, 2) X(SV, 4, 4, 2) X(SV, 8, 4, 2) X(SV, 1, 4, 3) \
     X(SV, 1, 4, 6) X(SV, 1, 4, 5) X(SV, 8, 4, 6)
+#define PSMS_BLOCK_VARIANTS_SMEM(X, SV) X(SV, 1, 3, 8) X(SV, 1, 3, 10) X(SV, 1, 3, 9)
 #define PSMS_BLOCK_EXTERN(SV, CL, MINB, HV) \
     extern template void launch_block_cl<SV, SV, CL, MINB, HV>(psms_ctx *, const BlockSolveArgs &, int, int);
 #define PSMS_BLOCK_INSTANTIATE(SV, CL, MINB, HV) \

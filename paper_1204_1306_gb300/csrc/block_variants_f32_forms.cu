@@ -5,4 +5,5 @@
 
 namespace psms {
 PSMS_BLOCK_VARIANTS_FORMS(PSMS_BLOCK_INSTANTIATE, Store<float>)
+PSMS_BLOCK_VARIANTS_SMEM(PSMS_BLOCK_INSTANTIATE, Store<float>)
 }  // namespace psms

@@ -1302,7 +1302,7 @@ psms_status psms_profile_read_block(psms_ctx *ctx, long long *launches, double *
 
 psms_status psms_autotune(psms_ctx *ctx, int enable, int block_variant) {
     PSMS_TRY(ctx)
-    if (block_variant < -1 || block_variant > 17) fail(PSMS_EINVAL, "block_variant must be -1 or 0..17");
+    if (block_variant < -1 || block_variant > 20) fail(PSMS_EINVAL, "block_variant must be -1 or 0..20");
     ctx->autotune = enable != 0;
     ctx->forced_block_variant = block_variant;
     ctx->block_variant.clear();

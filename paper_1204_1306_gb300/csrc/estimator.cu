@@ -134,13 +134,15 @@ __global__ void __launch_bounds__(NT) block_norm_kernel(Geom g, const double2 *v
     }
 }
 
-// delta[lex(r) * N + i0 + i] = a[i * nr + r] - b[i * nr + r], i < n
+// delta[lex(r) * N + i0 + i] = a[i * nr + r] - b[i * nr + r], i < n; 0 for
+// blocks the mask (an earlier level) turned away, whose solves were skipped
 __global__ void block_delta_kernel(const BlockInfo *binfo, const double *a, const double *b, int nr, int n, int N,
-                                   int i0, double *delta) {
+                                   int i0, const int *mask, double *delta) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nr * n) return;
     const int i = t / nr, r = t % nr;
-    delta[(long long)binfo[r].lex * N + i0 + i] = a[t] - b[t];
+    const int lex = binfo[r].lex;
+    delta[(long long)lex * N + i0 + i] = (mask && !mask[lex]) ? 0.0 : a[t] - b[t];
 }
 
 int chunk_size(psms_ctx *c, int N, double bytes_per_site) {
@@ -259,7 +261,8 @@ static long long block_level_chunk(psms_ctx *c, const double2 *U, const double2 
     block_solve(c, q);
     block_norm_kernel<128><<<dim3(nr, n), 128, 0, c->stream>>>(g, xi, fs, 0, nr, xin);
     PSMS_LAUNCH_CHECK("block_norm_kernel");
-    block_delta_kernel<<<(nr * n + 127) / 128, 128, 0, c->stream>>>(c->d_binfo, xn, xin, nr, n, N, i0, d_delta);
+    block_delta_kernel<<<(nr * n + 127) / 128, 128, 0, c->stream>>>(c->d_binfo, xn, xin, nr, n, N, i0, d_mask,
+                                                                   d_delta);
     PSMS_LAUNCH_CHECK("block_delta_kernel");
     check_status(c, status, nr * n, "block level");
     std::vector<int> hit(nr * n);

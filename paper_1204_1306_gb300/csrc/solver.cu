@@ -19,6 +19,8 @@
 #include "kernels.hpp"
 #include "solver.hpp"
 
+#include <type_traits>
+
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -31,6 +33,7 @@ PSMS_BLOCK_VARIANTS_CG(PSMS_BLOCK_EXTERN, Store<double>)
 PSMS_BLOCK_VARIANTS_FORMS(PSMS_BLOCK_EXTERN, Store<double>)
 PSMS_BLOCK_VARIANTS_CG(PSMS_BLOCK_EXTERN, Store<float>)
 PSMS_BLOCK_VARIANTS_FORMS(PSMS_BLOCK_EXTERN, Store<float>)
+PSMS_BLOCK_VARIANTS_SMEM(PSMS_BLOCK_EXTERN, Store<float>)
 
 template <class SV, class SL>
 static void launch_block_variant(psms_ctx *c, const BlockSolveArgs &a, int n_ranks, int n_sys, int cl, int minb,
@@ -46,6 +49,18 @@ static void launch_block_variant(psms_ctx *c, const BlockSolveArgs &a, int n_ran
         case 614: launch_block_cl<SV, SL, 1, 4, 6>(c, a, n_ranks, n_sys); break;
         case 514: launch_block_cl<SV, SL, 1, 4, 5>(c, a, n_ranks, n_sys); break;
         case 684: launch_block_cl<SV, SL, 8, 4, 6>(c, a, n_ranks, n_sys); break;
+        case 813:
+        case 1013:
+        case 913:
+            // links in shared memory: FP32 inner iterations only (admissible() checks)
+            if constexpr (std::is_same<SL, Store<float>>::value) {
+                if (hv == 8) launch_block_cl<SV, SL, 1, 3, 8>(c, a, n_ranks, n_sys);
+                else if (hv == 10) launch_block_cl<SV, SL, 1, 3, 10>(c, a, n_ranks, n_sys);
+                else launch_block_cl<SV, SL, 1, 3, 9>(c, a, n_ranks, n_sys);
+            } else {
+                fail(PSMS_EINVAL, "block solver: shared-memory links need FP32 inner iterations");
+            }
+            break;
         case 11: launch_block_cl<SV, SL, 1, 1>(c, a, n_ranks, n_sys); break;
         case 14: launch_block_cl<SV, SL, 1, 4>(c, a, n_ranks, n_sys); break;
         case 21: launch_block_cl<SV, SL, 2, 1>(c, a, n_ranks, n_sys); break;
@@ -102,9 +117,13 @@ void block_solve(psms_ctx *c, const BlockSolveReq &q) {
     };
     static const Var vars[] = {{1, 1, 0}, {1, 4, 0}, {2, 1, 0}, {2, 4, 0}, {4, 1, 0}, {4, 4, 0}, {8, 1, 0},
                                {8, 4, 0}, {1, 1, 1}, {1, 4, 1}, {1, 1, 2}, {1, 4, 2}, {4, 4, 2}, {8, 4, 2},
-                               {1, 4, 3}, {1, 4, 6}, {1, 4, 5}, {8, 4, 6}};
-    const int nvar = 18;
-    auto admissible = [&](int v) { return vars[v].cl == 1 || g.Vbh / vars[v].cl >= 128; };
+                               {1, 4, 3}, {1, 4, 6}, {1, 4, 5}, {8, 4, 6}, {1, 3, 8}, {1, 3, 10}, {1, 3, 9}};
+    const int nvar = 21;
+    auto admissible = [&](int v) {
+        if (vars[v].hv & 8)  // the block's FP32 links in shared memory (at most 100 KB)
+            return !in64 && block_links_smem(g) <= 100 * 1024;
+        return vars[v].cl == 1 || g.Vbh / vars[v].cl >= 128;
+    };
     auto launch = [&](int v) {
         if (in64)
             launch_block_variant<Store<double>, Store<double>>(c, a, q.n_ranks, q.n_sys, vars[v].cl, vars[v].minb,

@@ -148,3 +148,47 @@ def test_block_solver_cluster_variants(variant):
         r = b - dirac.apply_D(U, got, c["kappa"], geom, mode="block")
         assert np.sqrt(linalg.norm2(r) / linalg.norm2(b)) <= 1e-13
         assert rel_err(dirac.extract_block(got, geom, 1), ref1) < 1e-11
+
+
+_SMEM_CASE = dict(dims=(8, 8, 8, 8), block=(4, 4, 4, 4), kappa=0.156)
+
+
+@functools.lru_cache(maxsize=1)
+def _smem_reference():
+    """The oracle's block solutions on blocks 0 and 9 of the 4^4-block case."""
+    c = _SMEM_CASE
+    geom = lattice.Geometry(c["dims"], c["block"])
+    U = gauge.generate_links(c["dims"], 0.5, 25)
+    b = seeded.spinor(c["dims"], 26)
+    ref = estimator.solve_blocks(U, b, geom, c["kappa"], [0, 9], 1e-14)
+    return geom, U, b, {bb: dirac.extract_block(ref, geom, bb) for bb in (0, 9)}
+
+
+@pytest.mark.parametrize("variant", [18, 19, 20])
+def test_block_solver_shared_memory_link_variants(variant):
+    """The variants that stage each block's FP32 links in shared memory once
+    per solve (4^4 blocks) give the oracle's solution, alone and batched
+    over several right-hand sides."""
+    c = _SMEM_CASE
+    geom, U, b, refs = _smem_reference()
+    ctx = ps.psms_create(c["dims"], c["block"], c["kappa"], 1)
+    ps.psms_gauge_init(ctx, 0, 0.5, 25)
+    ps.psms_autotune(ctx, False, variant)
+    x = torch.zeros_like(native(ctx, b))
+    info = ps.psms_solve(ctx, 0, ps.OP_BLOCKS, native(ctx, b), x, 1e-13, 20000, ps.PREC_F32)
+    got = canonical(ctx, x)
+    r = b - dirac.apply_D(U, got, c["kappa"], geom, mode="block")
+    assert np.sqrt(linalg.norm2(r) / linalg.norm2(b)) <= 1e-13
+    for bb, ref in refs.items():
+        assert rel_err(dirac.extract_block(got, geom, bb), ref) < 1e-11
+    # batched over interpolation steps (the block level): the same estimates
+    # as the default variant, to the solve tolerance
+    c2 = ps.psms_create(c["dims"], c["block"], c["kappa"], 2)
+    ps.psms_gauge_init(c2, 0, 0.5, 25)
+    ps.psms_gauge_copy(c2, 1, 0)
+    ps.psms_gauge_sweep(c2, 1, ps.ACTIVE_BLOCKS, 1, 1, 5.3, 3, 0)
+    ps.psms_autotune(c2, False, 0)
+    ref = ps.psms_logdet_ratio(c2, ps.LEVEL_BLOCK, 0, 1, 3, ps.EST_INTERP, 5, 0, 1e-13, ps.PREC_F32)
+    ps.psms_autotune(c2, False, variant)
+    got = ps.psms_logdet_ratio(c2, ps.LEVEL_BLOCK, 0, 1, 3, ps.EST_INTERP, 5, 0, 1e-13, ps.PREC_F32)
+    assert np.abs(got - ref).max() < 1e-8
