@@ -554,6 +554,8 @@ def block_only(args):
     ps.psms_gauge_copy(ctx, 1, 0)
     ps.psms_gauge_sweep(ctx, 1, ps.ACTIVE_BLOCKS, wl["n_iter"], wl["n_or"], wl["beta"], seed, 9 << 20)
     ps.psms_relative_gauge_fix(ctx, 0, 1, 2, 3, prec=ps.PREC_F32)
+    if args.block_variant >= 0:
+        ps.psms_autotune(ctx, False, args.block_variant)
     n = args.block_n
     for r in range(args.warmup):
         ps.psms_logdet_ratio(ctx, ps.LEVEL_BLOCK, 2, 3, n, ps.EST_INTERP, seed, r, wl["tol"], ps.PREC_F32)
@@ -570,7 +572,8 @@ def block_only(args):
     nl, bms, bbytes = ps.psms_profile_read_block(ctx)
     peak, kind = peaks()
     nb = ps.psms_geometry_info(ctx)[0]
-    print(json.dumps({"workload": "16^4 block level", "n": n, "blocks": nb, "ms_per_call": statistics.median(ms),
+    print(json.dumps({"workload": "16^4 block level", "n": n, "blocks": nb, "variant": args.block_variant,
+                      "ms_per_call": statistics.median(ms),
                       "estimates_per_s": nb * n / (statistics.median(ms) * 1e-3),
                       "block_solver": {"launches": nl, "ms": round(bms, 3), "algorithmic_GB/s": round(
                           bbytes / (bms * 1e-3) / 1e9, 1) if bms > 0 else None, "peak_gbs": peak, "peak_kind": kind}}),
@@ -1211,6 +1214,7 @@ def main():
     ap.add_argument("--batch-only", action="store_true", help="multi-lattice batched block solves (8^4, 12^4, 16^3x32)")
     ap.add_argument("--block-only", action="store_true", help="the 16^4 block level alone (ncu case)")
     ap.add_argument("--block-n", type=int, default=12, help="interpolation steps of --block-only")
+    ap.add_argument("--block-variant", type=int, default=-1, help="force a block-solver variant (--block-only)")
     ap.add_argument("--levels-only", action="store_true",
                     help="parametrised levels and the recursive decomposition on 16^4 (auxiliary line)")
     args = ap.parse_args()

@@ -22,6 +22,7 @@ struct HopArgs {
     const int *active;
     double *partial;
     unsigned long long *prof_sites;  // profiling: output sites of active systems
+    const int *sys_map;              // systems launched (null: all, k = blockIdx.y)
 };
 
 template <int NT>
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
     using E = typename S::elem;
     using EL = typename SL::elem;
     __shared__ double sh[NT / 32];
-    const int k = blockIdx.y;
+    const int k = a.sys_map ? a.sys_map[blockIdx.y] : (int)blockIdx.y;
     if (a.active && !a.active[k]) {
         if (a.partial && threadIdx.x == 0) a.partial[(long long)k * gridDim.x + blockIdx.x] = 0.0;
         return;
@@ -87,6 +88,18 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
             p = a.p;
             r = a.rank_lo + (int)(t >> g.vbh_sh);
             j = (int)(t & (g.Vbh - 1));
+            if (a.n_ranks == g.nblocks && g.coloured) {
+                // whole lattice, one parity: walk the blocks in lexicographic
+                // order (colours interleaved), so that the faces a block
+                // reads from its neighbours were loaded by CTAs that ran
+                // just before and are still in L2
+                int B[4], rem = r;
+                for (int m = 3; m >= 0; --m) {
+                    B[m] = rem % g.nb[m];
+                    rem /= g.nb[m];
+                }
+                r = rank_of_lex(g, r, B);
+            }
         }
         int y[4];
         const int ll = local_lex(g, p, j, y);
@@ -228,9 +241,11 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
     a.active = h.active;
     a.partial = h.partial;
     a.prof_sites = nullptr;
+    a.sys_map = h.sys_map;
     const int nct = hop_ctas(c, h);
-    if (nct == 0 || h.n_sys == 0) return 0;
-    dim3 grid(nct, h.n_sys);
+    const int nsys = h.sys_map ? h.n_map : h.n_sys;
+    if (nct == 0 || nsys == 0) return 0;
+    dim3 grid(nct, nsys);
     double bytes = 0;
     int slot = -1;
     if (c->prof && h.mode == HOP_ALL && (c->prof_prec < 0 || c->prof_prec == h.prec)) {

@@ -30,6 +30,10 @@ struct HopCall {
     int p = -1, rank_lo = 0, n_ranks = -1, mode = HOP_ALL, dag = 0, n_sys = 1;
     const int *active = nullptr;
     double *partial = nullptr;
+    // optional list of the systems to launch (device, n_map entries): the
+    // launch covers only them (system k = sys_map[blockIdx.y])
+    const int *sys_map = nullptr;
+    int n_map = 0;
 };
 // returns the number of CTAs per system (for the partial sums)
 int hop_launch(psms_ctx *c, const HopCall &h);

@@ -703,9 +703,10 @@ template <class S, int NT>
 __global__ void __launch_bounds__(NT) bcg_axpy_kernel(const BCS *st, int mode, View<typename S::elem> x,
                                                       View<typename S::elem> p, View<typename S::elem> r,
                                                       View<typename S::elem> s_, View<typename S::elem> v,
-                                                      View<typename S::elem> t, long long s_lo, long long n) {
+                                                      View<typename S::elem> t, long long s_lo, long long n,
+                                                      const int *map) {
     using R = typename S::R;
-    const int k = blockIdx.y;
+    const int k = map ? map[blockIdx.y] : (int)blockIdx.y;
     if (!st[k].active) return;
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
     if (i >= n) return;
@@ -735,8 +736,7 @@ __global__ void __launch_bounds__(NT) bcg_axpy_kernel(const BCS *st, int mode, V
 template <int NT>
 __device__ __forceinline__ void bcg_partials_and_stage(BCS *st, double re, double im, double aa, double *p_re,
                                                        double *p_im, double *p_aa, unsigned int *counters, int stage,
-                                                       int maxit, int *flags, double (*sh)[NT / 32]) {
-    const int k = blockIdx.y;
+                                                       int maxit, int *flags, double (*sh)[NT / 32], int k) {
     const long long slot = (long long)k * gridDim.x + blockIdx.x;
     __shared__ int last;
 #pragma unroll
@@ -801,10 +801,11 @@ template <class S, int NT>
 __global__ void __launch_bounds__(NT) bcg_dot_stage_kernel(BCS *st, View<typename S::elem> a,
                                                            View<typename S::elem> b, long long s_lo, long long n,
                                                            double *p_re, double *p_im, double *p_aa,
-                                                           unsigned int *counters, int stage, int maxit, int *flags) {
+                                                           unsigned int *counters, int stage, int maxit, int *flags,
+                                                           const int *map) {
     using R = typename S::R;
     __shared__ double sh[3][NT / 32];
-    const int k = blockIdx.y;
+    const int k = map ? map[blockIdx.y] : (int)blockIdx.y;
     if (!st[k].active) return;
     double re = 0, im = 0, aa = 0;
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
@@ -822,7 +823,7 @@ __global__ void __launch_bounds__(NT) bcg_dot_stage_kernel(BCS *st, View<typenam
         im = (double)tim;
         aa = (double)taa;
     }
-    bcg_partials_and_stage<NT>(st, re, im, aa, p_re, p_im, p_aa, counters, stage, maxit, flags, sh);
+    bcg_partials_and_stage<NT>(st, re, im, aa, p_re, p_im, p_aa, counters, stage, maxit, flags, sh, k);
 }
 
 // x += alpha p + omega s, r = s - omega t, then the partials of
@@ -833,10 +834,11 @@ __global__ void __launch_bounds__(NT) bcg_update_stage_kernel(BCS *st, View<type
                                                               View<typename S::elem> s_, View<typename S::elem> t,
                                                               View<typename S::elem> rh, long long s_lo, long long n,
                                                               double *p_re, double *p_im, double *p_aa,
-                                                              unsigned int *counters, int maxit, int *flags) {
+                                                              unsigned int *counters, int maxit, int *flags,
+                                                              const int *map) {
     using R = typename S::R;
     __shared__ double sh[3][NT / 32];
-    const int k = blockIdx.y;
+    const int k = map ? map[blockIdx.y] : (int)blockIdx.y;
     if (!st[k].active) return;
     const BCS bs = st[k];
     const cpx<R> al = {(R)bs.alpha.x, (R)bs.alpha.y}, om = {(R)bs.omega.x, (R)bs.omega.y};
@@ -866,7 +868,7 @@ __global__ void __launch_bounds__(NT) bcg_update_stage_kernel(BCS *st, View<type
         im = (double)tim;
         aa = (double)taa;
     }
-    bcg_partials_and_stage<NT>(st, re, im, aa, p_re, p_im, p_aa, counters, 2, maxit, flags, sh);
+    bcg_partials_and_stage<NT>(st, re, im, aa, p_re, p_im, p_aa, counters, 2, maxit, flags, sh, k);
 }
 
 __global__ void iters_bcg_kernel(const BCS *st, int *out, int n) {
@@ -953,40 +955,60 @@ static void inner_bicgstab_full(psms_ctx *c, int n_sys, const void *Uin, long lo
     };
     int it = 0;
     int chunk = 8;
-    std::vector<int> hflags(n_sys);
+    std::vector<int> hflags(n_sys), hmap;
     h.active = flags;
+    // systems still iterating, refreshed at every host check: later launches
+    // cover only them (a converged system's CTAs would exit at once, but
+    // scheduling them costs about as much as a system's work)
+    int *d_map = (int *)scratch(c, "fs_bmap", sizeof(int) * n_sys);
+    const int *map = nullptr;
+    int n_act = n_sys;
     while (it < maxit) {
+        dim3 gridm(nb, n_act);
+        h.sys_map = map;
+        h.n_map = n_act;
         for (int i = 0; i < chunk && it < maxit; ++i, ++it) {
             apply_dhat(pp, vv);
             // alpha = rho / <rh, v>
-            bcg_dot_stage_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, tv(rh), tv(vv), Vh, n, q_re, q_im, q_aa,
-                                                                     cnt, 0, maxit, flags);
+            bcg_dot_stage_kernel<SV, NT><<<gridm, NT, 0, c->stream>>>(st, tv(rh), tv(vv), Vh, n, q_re, q_im, q_aa,
+                                                                      cnt, 0, maxit, flags, map);
             PSMS_LAUNCH_CHECK("bcg_alpha");
-            bcg_axpy_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, 0, tv(e), tv(pp), tv(r), tv(ss), tv(vv), tv(tt),
-                                                                Vh, n);
+            bcg_axpy_kernel<SV, NT><<<gridm, NT, 0, c->stream>>>(st, 0, tv(e), tv(pp), tv(r), tv(ss), tv(vv),
+                                                                 tv(tt), Vh, n, map);
             PSMS_LAUNCH_CHECK("bcg_s");
             apply_dhat(ss, tt);
             // omega = <t, s> / <t, t>
-            bcg_dot_stage_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, tv(tt), tv(ss), Vh, n, q_re, q_im, q_aa,
-                                                                     cnt, 1, maxit, flags);
+            bcg_dot_stage_kernel<SV, NT><<<gridm, NT, 0, c->stream>>>(st, tv(tt), tv(ss), Vh, n, q_re, q_im, q_aa,
+                                                                      cnt, 1, maxit, flags, map);
             PSMS_LAUNCH_CHECK("bcg_omega");
             // x, r updates with <rh, r>, |r|^2 and beta / convergence
-            bcg_update_stage_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, tv(e), tv(pp), tv(r), tv(ss), tv(tt),
-                                                                        tv(rh), Vh, n, q_re, q_im, q_aa, cnt, maxit,
-                                                                        flags);
+            bcg_update_stage_kernel<SV, NT><<<gridm, NT, 0, c->stream>>>(st, tv(e), tv(pp), tv(r), tv(ss), tv(tt),
+                                                                         tv(rh), Vh, n, q_re, q_im, q_aa, cnt,
+                                                                         maxit, flags, map);
             PSMS_LAUNCH_CHECK("bcg_update");
-            bcg_axpy_kernel<SV, NT><<<grid, NT, 0, c->stream>>>(st, 2, tv(e), tv(pp), tv(r), tv(ss), tv(vv), tv(tt),
-                                                                Vh, n);
+            bcg_axpy_kernel<SV, NT><<<gridm, NT, 0, c->stream>>>(st, 2, tv(e), tv(pp), tv(r), tv(ss), tv(vv),
+                                                                 tv(tt), Vh, n, map);
             PSMS_LAUNCH_CHECK("bcg_p");
         }
         cuda_check(cudaMemcpyAsync(hflags.data(), flags, sizeof(int) * n_sys, cudaMemcpyDeviceToHost, c->stream),
                    "bcg flags");
         cuda_check(cudaStreamSynchronize(c->stream), "bcg sync");
-        bool any = false;
-        for (int k = 0; k < n_sys; ++k) any |= hflags[k] != 0;
-        if (!any) break;
+        hmap.clear();
+        for (int k = 0; k < n_sys; ++k)
+            if (hflags[k]) hmap.push_back(k);
+        if (hmap.empty()) break;
+        if ((int)hmap.size() < n_sys) {
+            cuda_check(cudaMemcpyAsync(d_map, hmap.data(), sizeof(int) * hmap.size(), cudaMemcpyHostToDevice,
+                                       c->stream),
+                       "bcg map");
+            cuda_check(cudaStreamSynchronize(c->stream), "bcg map");
+            map = d_map;
+        }
+        n_act = (int)hmap.size();
         chunk = std::min(chunk * 2, 64);
     }
+    h.sys_map = nullptr;
+    h.n_map = 0;
     iters_bcg_kernel<<<(n_sys + 63) / 64, 64, 0, c->stream>>>(st, iters_acc, n_sys);
     PSMS_LAUNCH_CHECK("iters_kernel");
     // e_e = (rhs_e + H_e(e_o)/2)/A
@@ -1038,13 +1060,30 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
     int outer = 0;
     const int NT = 256;
     dim3 grid((unsigned)((V + NT - 1) / NT), n);
+    int *d_omap = (int *)scratch(c, "fb_omap", sizeof(int) * n);
+    std::vector<int> omap;
     for (;; ++outer) {
-        // r = b - D x = b - A x + H(x)/2   (FP64, both parities)
+        // r = b - D x = b - A x + H(x)/2   (FP64, both parities); after the
+        // first step only for the systems that have not converged (the
+        // others keep x, r and their residual norm)
         HopCall h;
         h.prec = P64;
         h.U = q.U64;
         h.U_bs = q.U64_bs;
         h.n_sys = n;
+        if (outer > 0) {
+            omap.clear();
+            for (int k = 0; k < n; ++k)
+                if (hact[k]) omap.push_back(k);
+            if ((int)omap.size() < n) {
+                cuda_check(cudaMemcpyAsync(d_omap, omap.data(), sizeof(int) * omap.size(), cudaMemcpyHostToDevice,
+                                           c->stream),
+                           "outer map");
+                cuda_check(cudaStreamSynchronize(c->stream), "outer map");
+                h.sys_map = d_omap;
+                h.n_map = (int)omap.size();
+            }
+        }
         h.p = -1;
         h.in = x;
         h.out = r;
