@@ -465,11 +465,13 @@ psms_status psms_block_krylov(psms_ctx *ctx, int kind);
 psms_status psms_max_chunk(psms_ctx *ctx, int n);
 
 /* Force the Wilson-hop kernel variant (register cap and, for the whole
- * lattice, the branch-free specialisation; 8 variants for FP32 links in the
- * whole-lattice mode, 4 otherwise, used modulo their count) instead of the
- * autotuned one; -1 returns to autotuning.  All variants compute the same
- * operator.  *n_variants (may be NULL) receives 8.  PSMS_EINVAL outside
- * -1..7. */
+ * lattice, the branch-free specialisation, and on blocks of 2 x 128 sites
+ * (4^4) the variant that stages each block's input of the other parity in
+ * shared memory; 10 variants for FP32 links in the whole-lattice mode on
+ * such blocks, 8 on others, 4 otherwise, used modulo their count) instead
+ * of the autotuned one; -1 returns to autotuning.  All variants compute the
+ * same operator.  *n_variants (may be NULL) receives 10.  PSMS_EINVAL
+ * outside -1..9. */
 psms_status psms_hop_variant(psms_ctx *ctx, int variant, int *n_variants);
 
 /* ---- checkpoint / resume ----------------------------------------------------

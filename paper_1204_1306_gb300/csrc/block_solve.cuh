@@ -353,9 +353,20 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
     }
     for (int outer = 0;; ++outer) {
         // FP64 true residual r64 = b - D_b x  (both parities)
-        // r64_p = b_p + H_p(x_{1-p})/2, then subtract A x_p
+        // r64_p = b_p + H_p(x_{1-p})/2, then subtract A x_p; on the first
+        // step x = 0, so r64 = b and |r64|^2 = |b|^2 without the FP64 hop
+        // (GB300's FP64 rate makes that hop a large part of a block solve)
         double rn = 0;
         bar<CL>();
+        if (outer == 0) {
+            for (int p = 0; p < 2; ++p)
+                for (int j = jlo + threadIdx.x; j < jhi; j += NT) {
+                    const long long s = blo[p] + j;
+                    for (int q = 0; q < 12; ++q)
+                        S64::st(r64, q, a.r64.cs, s - a.r64.off, S64::ld(b, q, a.b.cs, s - a.b.off));
+                }
+            rn = bn;
+        } else {
         for (int p = 0; p < 2; ++p) {
             hop_call<HV, S64, S64, S64>(g, bi, r, p, 0, x, a.x.cs, a.x.off, r64, a.r64.cs, a.r64.off, b, a.b.cs,
                                      a.b.off, 1.0, 0.5, U64, jlo, jhi);
@@ -373,6 +384,7 @@ __device__ void block_solve_item(const BlockSolveArgs &a, const int rl, const in
                 }
             }
         rn = cl_sum<NT, CL>(rn, sh);
+        }
         rel = sqrt(rn / bn);
         if (rel <= a.tol) break;
         if (outer >= a.max_outer || total_it >= a.maxit) {

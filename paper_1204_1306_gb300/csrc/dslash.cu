@@ -202,6 +202,147 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
     }
 }
 
+// Staged variant for whole-lattice launches on blocks of 2 x 128 sites (4^4):
+// one CTA per (block, output parity, system).  The block's own input sites
+// of the other parity (the neighbours of 3/4 of the hops) are copied into
+// shared memory with asynchronous 16-byte copies (cp.async, past the
+// registers and L1), then every direction reads its neighbour through one
+// generic load sequence from shared memory (inside the block) or global
+// memory (across a face), so the two cases do not split the warp.  Blocks
+// are walked in lexicographic order (colours interleaved) as in the
+// unstaged kernel.  Links are read from global memory as there.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <class S, class SL, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) hop_staged_kernel(const HopArgs<typename S::elem> a) {
+    using R = typename SL::R;
+    using E = typename S::elem;
+    using EL = typename SL::elem;
+    constexpr int NU = 12 >> S::VSH;  // 16-byte units per site
+    __shared__ int4 stage[NU * NT];
+    __shared__ double sh[NT / 32];
+    const Geom &g = a.g;
+    const int k = a.sys_map ? a.sys_map[blockIdx.y] : (int)blockIdx.y;
+    if (a.active && !a.active[k]) {
+        if (a.partial && threadIdx.x == 0) a.partial[(long long)k * gridDim.x + blockIdx.x] = 0.0;
+        return;
+    }
+    // CTA -> (block, parity): both parities in block-major order, or one
+    int p, bl;
+    if (a.p < 0) {
+        bl = blockIdx.x >> 1;
+        p = blockIdx.x & 1;
+    } else {
+        bl = blockIdx.x;
+        p = a.p;
+    }
+    int B[4], rem = bl;
+    for (int m = 3; m >= 0; --m) {
+        B[m] = rem % g.nb[m];
+        rem /= g.nb[m];
+    }
+    const int r = rank_of_lex(g, bl, B);
+    if (a.prof_sites && threadIdx.x == 0) atomicAdd(a.prof_sites, (unsigned long long)NT);
+    const E *in = a.in.p + k * a.in.bs;
+    // stage the block's input sites of the other parity (unit u of site s at
+    // 16-byte unit u * cs + s - off)
+    {
+        const long long s0 = (long long)(1 - p) * g.Vh + (long long)r * g.Vbh - a.in.off;
+        const int4 *src = reinterpret_cast<const int4 *>(in);
+#pragma unroll
+        for (int u = 0; u < NU; ++u) cp_async16(&stage[u * NT + threadIdx.x], src + u * a.in.cs + s0 + threadIdx.x);
+        cp_async_wait_all();
+        __syncthreads();
+    }
+    const int j = threadIdx.x;
+    int y[4];
+    const int ll = local_lex(g, p, j, y);
+    const BlockInfo &bi = a.binfo[r];
+    const long long s = (long long)p * g.Vh + (long long)r * g.Vbh + j;
+    const EL *U = (const EL *)a.U + k * a.U_bs;
+    const R sg = a.dag ? R(-1) : R(1);
+    const E *sm = reinterpret_cast<const E *>(stage);
+    // lattice volumes stay below 2^31 sites: 32-bit indices keep the eight
+    // neighbours in registers
+    const int base_opp = (int)((long long)(1 - p) * g.Vh + (long long)r * g.Vbh);
+    int snb[8], idx_[8];
+    unsigned inside = 0, neg = 0;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const int mu = d >> 1, sgn = (d & 1) ? -1 : 1;
+        long long sn;
+        int bs;
+        neighbour(g, bi, r, p, y, ll, mu, sgn, HOP_ALL, sn, bs);
+        snb[d] = (int)sn;
+        if (bs < 0) neg |= 1u << d;
+        const int yn = y[mu] + sgn;
+        if ((unsigned)yn < (unsigned)g.l[mu]) {
+            inside |= 1u << d;
+            idx_[d] = snb[d] - base_opp;
+        } else {
+            idx_[d] = snb[d] - (int)a.in.off;
+        }
+    }
+    Spinor<R> acc;
+    zero(acc);
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const int mu = d >> 1;
+        const bool fwd = (d & 1) == 0;
+        const bool ins = (inside >> d) & 1;
+        Spinor<R> v = load_spinor<S>(ins ? sm : in, ins ? (long long)NT : a.in.cs, idx_[d]);
+        const R tt = fwd ? -sg : sg;
+        Half<R> h = project(mu, tt, v);
+        if (mu == 0 && ((neg >> d) & 1)) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) h.c[q][c] = R(-1) * h.c[q][c];
+        }
+        SU3<R> u = load_link<SL>(U, g.V, mu, fwd ? s : (long long)snb[d]);
+        reconstruct_add(mu, tt, fwd ? su3_mul(u, h) : su3_dag_mul(u, h), acc);
+    }
+    const R cb = (R)a.b;
+    Spinor<R> o;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o.c[q][c] = cb * acc.c[q][c];
+    if (a.y.p) {
+        const R ca = (R)a.a;
+        Spinor<R> v = load_spinor<S>(a.y.p + k * a.y.bs, a.y.cs, s - a.y.off);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o.c[q][c] = o.c[q][c] + ca * v.c[q][c];
+    }
+    if (a.y2.p) {
+        const R ca = (R)a.a2;
+        Spinor<R> v = load_spinor<S>(a.y2.p + k * a.y2.bs, a.y2.cs, s - a.y2.off);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o.c[q][c] = o.c[q][c] + ca * v.c[q][c];
+    }
+    store_spinor<S>(a.out.p + k * a.out.bs, a.out.cs, s - a.out.off, o);
+    if (a.partial) {
+        double nrm = 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) nrm += (double)norm2(o.c[q][c]);
+        double tot = block_sum<NT>(nrm, sh);
+        if (threadIdx.x == 0) a.partial[(long long)k * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
 static constexpr int HOP_NT = 128;
 
 int hop_ctas(psms_ctx *c, const HopCall &h) {
@@ -267,6 +408,8 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
     // FP32 links: register caps 2, 6, 7, 8 CTAs/SM; for the whole lattice
     // (HOP_ALL) the branch-free specialisation with caps 4, 5, 6, 7 besides
     const bool all = h.mode == HOP_ALL;
+    // the staged kernel: whole lattice, 128 sites of each parity per block
+    const bool staged = all && a.n_ranks == c->g.nblocks && h.rank_lo == 0 && c->g.Vbh == HOP_NT;
     const KFn *vars;
     int nvar;
     if constexpr (f32) {
@@ -275,9 +418,10 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
         static const KFn v32all[] = {hop_kernel<S, SL, HOP_NT, 2, 0>, hop_kernel<S, SL, HOP_NT, 6, 0>,
                                      hop_kernel<S, SL, HOP_NT, 7, 0>, hop_kernel<S, SL, HOP_NT, 8, 0>,
                                      hop_kernel<S, SL, HOP_NT, 4, 1>, hop_kernel<S, SL, HOP_NT, 5, 1>,
-                                     hop_kernel<S, SL, HOP_NT, 6, 1>, hop_kernel<S, SL, HOP_NT, 7, 1>};
+                                     hop_kernel<S, SL, HOP_NT, 6, 1>, hop_kernel<S, SL, HOP_NT, 7, 1>,
+                                     hop_staged_kernel<S, SL, HOP_NT, 4>, hop_staged_kernel<S, SL, HOP_NT, 6>};
         vars = all ? v32all : v32;
-        nvar = all ? 8 : 4;
+        nvar = all ? (staged ? 10 : 8) : 4;
     } else {
         static const KFn v64[] = {hop_kernel<S, SL, HOP_NT, 2, 0>};
         vars = v64;

@@ -1034,6 +1034,7 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
     int *act = (int *)scratch(c, "fb_act", sizeof(int) * n);
     int *iters = (int *)scratch(c, "fb_iters", sizeof(int) * n);
     double2 *r64 = (double2 *)scratch(c, "fb_r64", sizeof(double2) * (size_t)12 * V * n);
+    if (q.b.cs != V || q.b.off != 0) fail(PSMS_EINVAL, "whole-lattice solve: right-hand sides must be full fields");
     View<void> b{q.b.p, q.b.cs, q.b.off, q.b.bs}, x{q.x.p, q.x.cs, q.x.off, q.x.bs};
     View<void> r{r64, V, 0, 12 * V};
     const bool in64 = q.inner_prec == P64;
@@ -1063,9 +1064,17 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
     int *d_omap = (int *)scratch(c, "fb_omap", sizeof(int) * n);
     std::vector<int> omap;
     for (;; ++outer) {
-        // r = b - D x = b - A x + H(x)/2   (FP64, both parities); after the
-        // first step only for the systems that have not converged (the
-        // others keep x, r and their residual norm)
+        // r = b - D x = b - A x + H(x)/2   (FP64, both parities); on the
+        // first step x = 0 and r = b exactly (no hop); later only for the
+        // systems that have not converged (the others keep x, r and their
+        // residual norm)
+        if (outer == 0) {
+            for (int k = 0; k < n; ++k)
+                cuda_check(cudaMemcpyAsync(r64 + (size_t)12 * V * k, (const double2 *)q.b.p + (size_t)k * q.b.bs,
+                                           sizeof(double2) * 12 * V, cudaMemcpyDeviceToDevice, c->stream),
+                           "r = b");
+            cuda_check(cudaMemcpyAsync(rn, bn, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "rn = bn");
+        }
         HopCall h;
         h.prec = P64;
         h.U = q.U64;
@@ -1092,8 +1101,10 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
         h.y2 = x;
         h.a2 = -c->A;
         h.b = 0.5;
-        hop_launch(c, h);
-        norm2_batch(c, P64, r, 0, V, n, rn);
+        if (outer > 0) {
+            hop_launch(c, h);
+            norm2_batch(c, P64, r, 0, V, n, rn);
+        }
         residual_flags_kernel<<<(n + 63) / 64, 64, 0, c->stream>>>(rn, bn, q.tol, act, rel, n);
         PSMS_LAUNCH_CHECK("residual_flags_kernel");
         cuda_check(cudaMemcpyAsync(hact.data(), act, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream), "act");

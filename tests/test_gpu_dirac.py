@@ -123,9 +123,19 @@ def test_dw_every_hop_variant(prec, tol):
         out = torch.zeros_like(nat)
         ps.psms_dw_apply(ctx, 0, ps.OP_BLOCKS, nat, out, prec)
         assert rel_err(canonical(ctx, out, prec), ref_blk) < tol, v
+    # the single-parity launches of the even-odd whole-lattice solver with
+    # each whole-lattice variant forced (the staged ones: 8, 9): the FP64
+    # defect correction reaches its true residual only if the inner
+    # operator is right
+    b = native(ctx, seeded.spinor(dims, 25))
+    for v in (5, 8, 9):
+        ps.psms_hop_variant(ctx, v)
+        x = torch.zeros_like(b)
+        info = ps.psms_solve(ctx, 0, ps.OP_FULL, b, x, 1e-11, 4000, ps.PREC_F32)
+        assert info["true_residual"] <= 1e-11 and info["outer_iters"] <= 6, (v, info)
     ps.psms_hop_variant(ctx, -1)
     with pytest.raises(ps.PsmsError):
-        ps.psms_hop_variant(ctx, 8)
+        ps.psms_hop_variant(ctx, n)
 
 
 def test_plaquette_and_translation():
