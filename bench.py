@@ -533,6 +533,38 @@ def levels_only(args):
     print(json.dumps(out), flush=True)
 
 
+def step_only(args):
+    """The headline hierarchy's filter steps alone, for launch-list captures:
+    the learned level trained on two proposals' estimates, `--warmup`
+    untimed steps on a copy of the field, then `--steps` steps inside the
+    NVTX range "timed_steps" (CUDA events around each).  Far fewer launches
+    than the full bench, so that a profiler pass over them stays short."""
+    import torch
+
+    import paper_1204_1306_gb300 as ps
+    from paper_1204_1306_gb300 import build as _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    wl = WORKLOADS[args.workload]
+    seed = SEED + 1
+    prm = _filter_prm(ps, wl, seed)
+    ctx = _new_chain(ps, torch, wl, seed)
+    train_learned(ps, torch, ctx, 2, n_interp=wl["n_block"])
+    ps.psms_gauge_copy(ctx, 3, 0)
+    for i in range(args.warmup):
+        ps.psms_filter_step(ctx, 3, step=100_000 + i, inner_prec=ps.PREC_F32, learned=True, **prm)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed_steps")
+    recs, ms = _timed_steps(ps, torch, ctx, prm, ps.PREC_F32, True, args.steps, flush)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"workload": args.workload, "steps": args.steps, "ms_per_step": ms / args.steps,
+                      "accepted_updates": _accepted(recs)}), flush=True)
+    ctx.close()
+
+
 def block_only(args):
     """The block level alone on the 16^4 workload (4^4 blocks): all blocks x
     n interpolation steps (--block-n, default 12) between the gauge-fixed
@@ -1213,6 +1245,7 @@ def main():
     ap.add_argument("--solve-only", action="store_true", help="single-system solver measurement only")
     ap.add_argument("--batch-only", action="store_true", help="multi-lattice batched block solves (8^4, 12^4, 16^3x32)")
     ap.add_argument("--block-only", action="store_true", help="the 16^4 block level alone (ncu case)")
+    ap.add_argument("--step-only", action="store_true", help="filter steps alone (launch-list case)")
     ap.add_argument("--block-n", type=int, default=12, help="interpolation steps of --block-only")
     ap.add_argument("--block-variant", type=int, default=-1, help="force a block-solver variant (--block-only)")
     ap.add_argument("--levels-only", action="store_true",
@@ -1234,6 +1267,8 @@ def main():
         levels_only(args)
     elif args.block_only:
         block_only(args)
+    elif args.step_only:
+        step_only(args)
     else:
         our_arm(args)
 

@@ -23,6 +23,7 @@ struct HopArgs {
     double *partial;
     unsigned long long *prof_sites;  // profiling: output sites of active systems
     const int *sys_map;              // systems launched (null: all, k = blockIdx.y)
+    const int *rank_active;          // per rank: 0 skips its output sites (null: none skipped)
 };
 
 template <int NT>
@@ -58,17 +59,13 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
     const long long per_p = (long long)a.n_ranks * g.Vbh;
     const long long total = (a.p < 0 ? 2 : 1) * per_p;
     const long long t = (long long)blockIdx.x * NT + threadIdx.x;
-    if (a.prof_sites && threadIdx.x == 0) {
-        const long long first = (long long)blockIdx.x * NT;
-        const long long n = total - first < NT ? total - first : NT;
-        atomicAdd(a.prof_sites, (unsigned long long)n);
-    }
     double nrm = 0.0;
-    if (t < total) {
+    bool work = t < total;
+    int p = 0, r = 0, j = 0;
+    if (work) {
         // both parities: block-major order (block, parity, site) so that the
         // two endpoints of a block's links are processed close in time and
         // each link is fetched from HBM about once per launch
-        int p, r, j;
         if (a.p < 0) {
             r = a.rank_lo + (int)(t >> (g.vbh_sh + 1));
             p = (int)((t >> g.vbh_sh) & 1);
@@ -101,6 +98,14 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
                 r = rank_of_lex(g, r, B);
             }
         }
+        work = !a.rank_active || a.rank_active[r];
+    }
+    if (a.prof_sites) {
+        // output sites this warp computes (algorithmic-byte accounting)
+        const unsigned cnt = __popc(__ballot_sync(0xffffffffu, work));
+        if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(a.prof_sites, (unsigned long long)cnt);
+    }
+    if (work) {
         int y[4];
         const int ll = local_lex(g, p, j, y);
         const BlockInfo &bi = a.binfo[r];
@@ -249,6 +254,10 @@ __global__ void __launch_bounds__(NT, MINB) hop_staged_kernel(const HopArgs<type
         rem /= g.nb[m];
     }
     const int r = rank_of_lex(g, bl, B);
+    if (a.rank_active && !a.rank_active[r]) {
+        if (a.partial && threadIdx.x == 0) a.partial[(long long)k * gridDim.x + blockIdx.x] = 0.0;
+        return;
+    }
     if (a.prof_sites && threadIdx.x == 0) atomicAdd(a.prof_sites, (unsigned long long)NT);
     const E *in = a.in.p + k * a.in.bs;
     // stage the block's input sites of the other parity (unit u of site s at
@@ -383,6 +392,7 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
     a.partial = h.partial;
     a.prof_sites = nullptr;
     a.sys_map = h.sys_map;
+    a.rank_active = h.rank_active;
     const int nct = hop_ctas(c, h);
     const int nsys = h.sys_map ? h.n_map : h.n_sys;
     if (nct == 0 || nsys == 0) return 0;

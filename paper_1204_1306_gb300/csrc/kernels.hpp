@@ -34,6 +34,9 @@ struct HopCall {
     // launch covers only them (system k = sys_map[blockIdx.y])
     const int *sys_map = nullptr;
     int n_map = 0;
+    // optional per-rank flags (device): output sites of ranks flagged 0 are
+    // skipped (left unwritten)
+    const int *rank_active = nullptr;
 };
 // returns the number of CTAs per system (for the partial sums)
 int hop_launch(psms_ctx *c, const HopCall &h);

@@ -220,9 +220,26 @@ void check_status(psms_ctx *c, const int *d_status, int n, const char *what) {
         if (v) fail(PSMS_ENOCONV, std::string(what) + ": a block solve missed its tolerance");
 }
 
-// whole-lattice solve of n systems with the given links
+// per inner-block rank: 1 when its outer block has colour `keep` (device)
+const int *outer_colour_ranks(psms_ctx *c, int keep) {
+    const Geom &g = c->g;
+    std::vector<int> h(g.nblocks);
+    for (int r = 0; r < g.nblocks; ++r) {
+        int col = 0;
+        for (int m = 0; m < 4; ++m) col += c->h_binfo[r].B[m] * g.l[m] / c->outer[m];
+        h[r] = (col & 1) == keep ? 1 : 0;
+    }
+    int *d = (int *)scratch(c, keep ? "outer_ranks1" : "outer_ranks0", sizeof(int) * g.nblocks);
+    cuda_check(cudaMemcpyAsync(d, h.data(), sizeof(int) * g.nblocks, cudaMemcpyHostToDevice, c->stream), "ranks");
+    cuda_check(cudaStreamSynchronize(c->stream), "ranks");
+    return d;
+}
+
+// whole-lattice solve of n systems with the given links; rank_active
+// (optional) restricts it to the inner blocks of one outer colour when the
+// links decouple the colours and b vanishes on the other
 long long solve_all(psms_ctx *c, const double2 *U64, const float2 *U32, long long bs, int n, const double2 *b,
-                    double2 *x, double tol, int inner) {
+                    double2 *x, double tol, int inner, const int *rank_active = nullptr) {
     const long long V = c->g.V, fs = 12 * V;
     FullSolveReq q;
     q.n_sys = n;
@@ -233,6 +250,7 @@ long long solve_all(psms_ctx *c, const double2 *U64, const float2 *U32, long lon
     q.U64_bs = bs;
     q.tol = tol;
     q.inner_prec = inner;
+    q.rank_active = rank_active;
     psms_solve_info info;
     solve_full_batch(c, q, &info);
     return info.inner_iters;
@@ -376,12 +394,16 @@ long long outer_global_chunk(psms_ctx *c, const double2 *U, const double2 *Up, i
     project_sites(c, outer::OUTER, xi, n);
     long long tot = 0;
     // v = (1 - P Q(U_i)) xi, Q = D_bb^-1 D_bw D_ww^-1 D_wb over the outer blocks
+    // the outer Dirichlet solves touch one colour of outer blocks each: the
+    // masked links decouple the outer blocks and the right-hand sides vanish
+    // on the other colour, so only that colour's inner blocks are iterated
+    const int *white = outer_colour_ranks(c, 1), *black = outer_colour_ranks(c, 0);
     hop_all(c, pc.a64, pc.bs, n, xi, t1);  // hops between outer blocks
     keep_colour(c, t1, n, 1);               // D_wb xi
-    tot += solve_all(c, pm.a64, pm.a32, pm.bs, n, t1, t2, tol, inner);  // D_ww^-1 (outer Dirichlet)
+    tot += solve_all(c, pm.a64, pm.a32, pm.bs, n, t1, t2, tol, inner, white);  // D_ww^-1 (outer Dirichlet)
     hop_all(c, pc.a64, pc.bs, n, t2, t1);
     keep_colour(c, t1, n, 0);  // D_bw
-    tot += solve_all(c, pm.a64, pm.a32, pm.bs, n, t1, t2, tol, inner);  // D_bb^-1
+    tot += solve_all(c, pm.a64, pm.a32, pm.bs, n, t1, t2, tol, inner, black);  // D_bb^-1
     sub_projected(c, outer::OUTER, v, xi, t2, n);
     // w = (1 - P Q(U_{i+1}))^-1 v = v - P [D^-1 (0, D_wb v)]_black
     hop_all(c, pc.b64, pc.bs, n, v, t1);

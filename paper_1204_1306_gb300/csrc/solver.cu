@@ -704,12 +704,13 @@ __global__ void __launch_bounds__(NT) bcg_axpy_kernel(const BCS *st, int mode, V
                                                       View<typename S::elem> p, View<typename S::elem> r,
                                                       View<typename S::elem> s_, View<typename S::elem> v,
                                                       View<typename S::elem> t, long long s_lo, long long n,
-                                                      const int *map) {
+                                                      const int *map, const int *rank_active, int vbh_sh) {
     using R = typename S::R;
     const int k = map ? map[blockIdx.y] : (int)blockIdx.y;
     if (!st[k].active) return;
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
     if (i >= n) return;
+    if (rank_active && !rank_active[(int)(i >> vbh_sh)]) return;
     const long long sx = s_lo + i;
     const BCS bs = st[k];
     auto ld = [&](const View<typename S::elem> &w, int c) { return S::ldi(w.p, k * w.bs + S::idx(c, w.cs, sx - w.off)); };
@@ -802,14 +803,14 @@ __global__ void __launch_bounds__(NT) bcg_dot_stage_kernel(BCS *st, View<typenam
                                                            View<typename S::elem> b, long long s_lo, long long n,
                                                            double *p_re, double *p_im, double *p_aa,
                                                            unsigned int *counters, int stage, int maxit, int *flags,
-                                                           const int *map) {
+                                                           const int *map, const int *rank_active, int vbh_sh) {
     using R = typename S::R;
     __shared__ double sh[3][NT / 32];
     const int k = map ? map[blockIdx.y] : (int)blockIdx.y;
     if (!st[k].active) return;
     double re = 0, im = 0, aa = 0;
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
-    if (i < n) {
+    if (i < n && (!rank_active || rank_active[(int)(i >> vbh_sh)])) {
         const long long sx = s_lo + i;
         R tre = 0, tim = 0, taa = 0;
         for (int c = 0; c < 12; ++c) {
@@ -835,7 +836,7 @@ __global__ void __launch_bounds__(NT) bcg_update_stage_kernel(BCS *st, View<type
                                                               View<typename S::elem> rh, long long s_lo, long long n,
                                                               double *p_re, double *p_im, double *p_aa,
                                                               unsigned int *counters, int maxit, int *flags,
-                                                              const int *map) {
+                                                              const int *map, const int *rank_active, int vbh_sh) {
     using R = typename S::R;
     __shared__ double sh[3][NT / 32];
     const int k = map ? map[blockIdx.y] : (int)blockIdx.y;
@@ -844,7 +845,7 @@ __global__ void __launch_bounds__(NT) bcg_update_stage_kernel(BCS *st, View<type
     const cpx<R> al = {(R)bs.alpha.x, (R)bs.alpha.y}, om = {(R)bs.omega.x, (R)bs.omega.y};
     double re = 0, im = 0, aa = 0;
     const long long i = (long long)blockIdx.x * NT + threadIdx.x;
-    if (i < n) {
+    if (i < n && (!rank_active || rank_active[(int)(i >> vbh_sh)])) {
         const long long sx = s_lo + i;
         auto ld = [&](const View<typename S::elem> &w, int c) {
             return S::ldi(w.p, k * w.bs + S::idx(c, w.cs, sx - w.off));
@@ -878,7 +879,8 @@ __global__ void iters_bcg_kernel(const BCS *st, int *out, int n) {
 
 template <class SV>
 static void inner_bicgstab_full(psms_ctx *c, int n_sys, const void *Uin, long long U_bs, int prec, View<void> rhs,
-                                View<void> e, const int *act_in, double delta, int maxit, int *iters_acc) {
+                                View<void> e, const int *act_in, double delta, int maxit, int *iters_acc,
+                                const int *rank_active) {
     using E = typename SV::elem;
     const Geom &g = c->g;
     const long long V = g.V, Vh = g.Vh;
@@ -886,6 +888,10 @@ static void inner_bicgstab_full(psms_ctx *c, int n_sys, const void *Uin, long lo
     const size_t esz = sizeof(E);
     // odd halves: bhat (= rh), r, p, v, s, t ; even half: te
     E *base = (E *)scratch(c, "fs_inner", esz * (size_t)(7 * 12 * Vh) * n_sys);
+    // with a rank mask the skipped sites are never written: start from zeros
+    if (rank_active)
+        cuda_check(cudaMemsetAsync(base, 0, esz * (size_t)(7 * 12 * Vh) * n_sys, c->stream), "inner zero");
+    const int vsh = g.vbh_sh;
     auto half = [&](int i, long long off) {
         View<void> v;
         v.p = base + (long long)i * 12 * Vh * n_sys;
@@ -906,6 +912,8 @@ static void inner_bicgstab_full(psms_ctx *c, int n_sys, const void *Uin, long lo
     h.U_bs = U_bs;
     h.n_sys = n_sys;
     h.active = act_in;
+    h.rank_active = rank_active;
+    h.rank_active = rank_active;
     const int nct = hop_ctas(c, [&] { HopCall x; x.p = 1; return x; }());
     double *p_a = (double *)scratch(c, "fs_pa", sizeof(double) * (size_t)nct * n_sys);
     // rh = bhat_o = rhs_o + H_o(rhs_e)/(2A)
@@ -971,23 +979,23 @@ static void inner_bicgstab_full(psms_ctx *c, int n_sys, const void *Uin, long lo
             apply_dhat(pp, vv);
             // alpha = rho / <rh, v>
             bcg_dot_stage_kernel<SV, NT><<<gridm, NT, 0, c->stream>>>(st, tv(rh), tv(vv), Vh, n, q_re, q_im, q_aa,
-                                                                      cnt, 0, maxit, flags, map);
+                                                                      cnt, 0, maxit, flags, map, rank_active, vsh);
             PSMS_LAUNCH_CHECK("bcg_alpha");
             bcg_axpy_kernel<SV, NT><<<gridm, NT, 0, c->stream>>>(st, 0, tv(e), tv(pp), tv(r), tv(ss), tv(vv),
-                                                                 tv(tt), Vh, n, map);
+                                                                 tv(tt), Vh, n, map, rank_active, vsh);
             PSMS_LAUNCH_CHECK("bcg_s");
             apply_dhat(ss, tt);
             // omega = <t, s> / <t, t>
             bcg_dot_stage_kernel<SV, NT><<<gridm, NT, 0, c->stream>>>(st, tv(tt), tv(ss), Vh, n, q_re, q_im, q_aa,
-                                                                      cnt, 1, maxit, flags, map);
+                                                                      cnt, 1, maxit, flags, map, rank_active, vsh);
             PSMS_LAUNCH_CHECK("bcg_omega");
             // x, r updates with <rh, r>, |r|^2 and beta / convergence
             bcg_update_stage_kernel<SV, NT><<<gridm, NT, 0, c->stream>>>(st, tv(e), tv(pp), tv(r), tv(ss), tv(tt),
                                                                          tv(rh), Vh, n, q_re, q_im, q_aa, cnt,
-                                                                         maxit, flags, map);
+                                                                         maxit, flags, map, rank_active, vsh);
             PSMS_LAUNCH_CHECK("bcg_update");
             bcg_axpy_kernel<SV, NT><<<gridm, NT, 0, c->stream>>>(st, 2, tv(e), tv(pp), tv(r), tv(ss), tv(vv),
-                                                                 tv(tt), Vh, n, map);
+                                                                 tv(tt), Vh, n, map, rank_active, vsh);
             PSMS_LAUNCH_CHECK("bcg_p");
         }
         cuda_check(cudaMemcpyAsync(hflags.data(), flags, sizeof(int) * n_sys, cudaMemcpyDeviceToHost, c->stream),
@@ -1101,6 +1109,7 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
         h.y2 = x;
         h.a2 = -c->A;
         h.b = 0.5;
+        h.rank_active = q.rank_active;  // skipped sites keep r = b = 0
         if (outer > 0) {
             hop_launch(c, h);
             norm2_batch(c, P64, r, 0, V, n, rn);
@@ -1124,8 +1133,11 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
             scale_convert_kernel<Store<double>, NT><<<grid, NT, 0, c->stream>>>(
                 View<double2>{(double2 *)rin_p, V, 0, 12 * V}, r2, rn, 1, act, 0, V);
             PSMS_LAUNCH_CHECK("scale_convert_kernel");
-            (bicg ? inner_bicgstab_full<Store<double>> : inner_cg_full<Store<double>>)(
-                c, n, q.U64, q.U64_bs, P64, rin, ein, act, delta, q.maxit, iters);
+            if (bicg)
+                inner_bicgstab_full<Store<double>>(c, n, q.U64, q.U64_bs, P64, rin, ein, act, delta, q.maxit, iters,
+                                                   q.rank_active);
+            else
+                inner_cg_full<Store<double>>(c, n, q.U64, q.U64_bs, P64, rin, ein, act, delta, q.maxit, iters);
             accumulate_kernel<Store<double>, NT><<<grid, NT, 0, c->stream>>>(
                 View<double2>{(double2 *)q.x.p, q.x.cs, q.x.off, q.x.bs}, View<double2>{(double2 *)ein_p, V, 0, 12 * V},
                 rn, act, 0, V);
@@ -1134,8 +1146,11 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
             scale_convert_kernel<Store<float>, NT><<<grid, NT, 0, c->stream>>>(
                 View<float2>{(float2 *)rin_p, V, 0, 12 * V}, r2, rn, 1, act, 0, V);
             PSMS_LAUNCH_CHECK("scale_convert_kernel");
-            (bicg ? inner_bicgstab_full<Store<float>> : inner_cg_full<Store<float>>)(
-                c, n, q.U32, q.U64_bs, P32, rin, ein, act, delta, q.maxit, iters);
+            if (bicg)
+                inner_bicgstab_full<Store<float>>(c, n, q.U32, q.U64_bs, P32, rin, ein, act, delta, q.maxit, iters,
+                                                  q.rank_active);
+            else
+                inner_cg_full<Store<float>>(c, n, q.U32, q.U64_bs, P32, rin, ein, act, delta, q.maxit, iters);
             accumulate_kernel<Store<float>, NT><<<grid, NT, 0, c->stream>>>(
                 View<double2>{(double2 *)q.x.p, q.x.cs, q.x.off, q.x.bs}, View<float2>{(float2 *)ein_p, V, 0, 12 * V},
                 rn, act, 0, V);
@@ -1144,8 +1159,12 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
             scale_convert_kernel<Store<__nv_bfloat16>, NT><<<grid, NT, 0, c->stream>>>(
                 View<__nv_bfloat162>{(__nv_bfloat162 *)rin_p, V, 0, 12 * V}, r2, rn, 1, act, 0, V);
             PSMS_LAUNCH_CHECK("scale_convert_kernel");
-            (bicg ? inner_bicgstab_full<Store<__nv_bfloat16>> : inner_cg_full<Store<__nv_bfloat16>>)(
-                c, n, q.U32, q.U64_bs, PB16, rin, ein, act, delta, q.maxit, iters);
+            if (bicg)
+                inner_bicgstab_full<Store<__nv_bfloat16>>(c, n, q.U32, q.U64_bs, PB16, rin, ein, act, delta, q.maxit,
+                                                          iters, q.rank_active);
+            else
+                inner_cg_full<Store<__nv_bfloat16>>(c, n, q.U32, q.U64_bs, PB16, rin, ein, act, delta, q.maxit,
+                                                    iters);
             accumulate_kernel<Store<__nv_bfloat16>, NT><<<grid, NT, 0, c->stream>>>(
                 View<double2>{(double2 *)q.x.p, q.x.cs, q.x.off, q.x.bs},
                 View<__nv_bfloat162>{(__nv_bfloat162 *)ein_p, V, 0, 12 * V}, rn, act, 0, V);

@@ -38,6 +38,10 @@ struct FullSolveReq {
     int maxit = 100000;
     int inner_prec = P64;
     double *rel_out = nullptr;  // device, per system (nullable)
+    // per rank (device, nullable): the operator is block-diagonal between the
+    // flagged and unflagged ranks (links across are zero) and b vanishes on
+    // the unflagged ones, so x vanishes there too and those sites are skipped
+    const int *rank_active = nullptr;
 };
 void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info);
 

@@ -84,6 +84,20 @@ def test_block_level_parity_4x4_blocks():
     assert np.all(np.abs(got) > 0)
 
 
+def test_block_level_parity_16x4_sampled():
+    """The 16^4 workload's block level (256 blocks of 4^4, batched with the
+    batch split into chunks of two interpolation steps): three sampled
+    blocks against the oracle."""
+    dims, block, kappa = (16, 16, 16, 16), (4, 4, 4, 4), 0.156
+    ctx, geom, U, Up = _pair(dims, block, kappa, 0.5, SEED + 9)
+    N = 3
+    ps.psms_max_chunk(ctx, 2)
+    got = ps.psms_logdet_ratio(ctx, ps.LEVEL_BLOCK, 0, 1, N, ps.EST_INTERP, SEED, 8, 1e-13, ps.PREC_F32)
+    blocks = [0, 117, 255]
+    ref = estimator.block_level(U, Up, geom, kappa, N, SEED, 8, tol=1e-13, blocks=blocks)
+    assert np.abs(got[blocks] - ref[blocks]).max() < 1e-8
+
+
 @pytest.mark.parametrize("inner", [ps.PREC_F64, ps.PREC_F32])
 def test_global_level_parity(inner):
     dims, block, kappa = (4, 4, 4, 4), (2, 2, 2, 2), 0.15
