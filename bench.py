@@ -267,8 +267,19 @@ def dw_only(args):
     ps.psms_gauge_init(ctx, 0, wl["eps"], SEED + 4)
     dw = measure_dw(ps, ctx, torch, reps=args.steps)
     peak, kind = peaks()
-    print(json.dumps({"workload": args.workload, "dw": dw, "peak_gbs": peak, "peak_kind": kind,
-                      "frac": {k: round(v["GB/s"] / peak, 4) for k, v in dw.items()}}), flush=True)
+    out = {"workload": args.workload, "dw": dw, "peak_gbs": peak, "peak_kind": kind,
+           "frac": {k: round(v["GB/s"] / peak, 4) for k, v in dw.items()}}
+    if args.hop_variants:
+        # every hop variant forced in turn (same operator): GB/s per variant
+        n = ps.psms_hop_variant(ctx, 0)
+        per = {}
+        for v in range(n):
+            ps.psms_hop_variant(ctx, v)
+            d = measure_dw(ps, ctx, torch, reps=args.steps)
+            per[v] = {k: d[k]["GB/s"] for k in ("bf16", "f32")}
+        ps.psms_hop_variant(ctx, -1)
+        out["per_variant_GB/s"] = per
+    print(json.dumps(out), flush=True)
 
 
 def solve_only(args):
@@ -1242,6 +1253,7 @@ def main():
     ap.add_argument("--learned-only", action="store_true", help="the learned level at 16^3x32 with 8^4 domains")
     ap.add_argument("--labels", type=int, default=100_000, help="training labels of --learned-only")
     ap.add_argument("--dw-only", action="store_true", help="stand-alone D_w measurement only")
+    ap.add_argument("--hop-variants", action="store_true", help="--dw-only: time every hop variant")
     ap.add_argument("--solve-only", action="store_true", help="single-system solver measurement only")
     ap.add_argument("--batch-only", action="store_true", help="multi-lattice batched block solves (8^4, 12^4, 16^3x32)")
     ap.add_argument("--block-only", action="store_true", help="the 16^4 block level alone (ncu case)")
