@@ -158,7 +158,11 @@ def allsum(ws, v):
 # first timed block-solver launch, branch-free hop variant: 0.148); None
 # once the kernel changes.  The kernel has changed since that capture (the
 # per-site norm sums), so no ratio is applied.
-TRAFFIC_RATIO = {"block_solve_cluster_kernel": None}
+# DRAM bytes (ncu dram__bytes_read.sum + write.sum) / algorithmic bytes of
+# captured launches of the current kernels (None: no capture of this build)
+TRAFFIC_RATIO = {"block_solve_cluster_kernel": None,
+                 # one FP32 half-hop pair of the whole-lattice solver, 32^3x64
+                 "hop_kernel": 1.058}
 
 
 def roofline_entry(kernel, n, ms, nbytes, peak, peak_kind):
@@ -510,12 +514,22 @@ def levels_only(args):
     ps.psms_gauge_sweep(ctx, 1, ps.ACTIVE_BLOCKS, wl["n_iter"], wl["n_or"], wl["beta"], seed, 9 << 20)
     V = float(np.prod(wl["dims"]))
     out = {"workload": "16^4", "data": "synthetic"}
+    fp64 = measure_fp64_peak(torch)
+    out["fp64_peak_measured"] = fp64
     ms = timed(lambda: ps.psms_hyp_block_action(ctx, 0), max(3, args.steps))
     flop = 55e3 * V  # per-site model of one smearing (fat links dominate)
     out["hyp_block_action"] = {"ms": round(ms, 3), "model_gflops_fp64": round(flop / ms * 1e-6, 1),
-                               "frac_of_nominal_fp64": round(flop / ms * 1e-9 / 1.25, 4)}
+                               "frac_of_measured_fp64": round(flop / ms * 1e-6 / fp64["gflops"], 4)}
     ms = timed(lambda: ps.psms_block_action_change(ctx, 0, 1), max(3, args.steps))
     out["block_action_change"] = {"ms": round(ms, 3)}
+    # exact block determinants (batched FP64 LU of the even-odd reduced block
+    # operator, n = 6 x block volume): (8/3) n^3 real flop per block
+    ms = timed(lambda: ps.psms_block_logdet(ctx, 0), 1)
+    nb = int(np.prod([d // b for d, b in zip(wl["dims"], wl["block"])]))
+    n = 6 * int(np.prod(wl["block"]))
+    flop = nb * 8.0 / 3.0 * n ** 3
+    out["block_logdet"] = {"blocks": nb, "n": n, "ms": round(ms, 2), "gflops_fp64": round(flop / ms * 1e-6, 1),
+                           "frac_of_measured_fp64": round(flop / ms * 1e-6 / fp64["gflops"], 4)}
     ps.psms_set_outer_blocks(ctx, (8, 8, 8, 8))
     n_sub = 12
     ms = timed(lambda: ps.psms_logdet_ratio(ctx, ps.LEVEL_SUB, 0, 1, n_sub, ps.EST_INTERP, seed, 0, wl["tol"],
@@ -941,6 +955,12 @@ def our_arm(args):
                             hop_bytes, peak, peak_kind)
     rl_blk = roofline_entry("block_solve_cluster_kernel<float> (persistent Dirichlet-block CG, FP32 inner)", blk_n,
                             blk_ms, blk_bytes, peak, peak_kind)
+    ratio = TRAFFIC_RATIO.get("hop_kernel")
+    if ratio is not None and hop_n:
+        rl_hop["traffic"] = ratio * hop_bytes / hop_n
+        rl_hop["traffic_note"] = ("ncu dram__bytes_read+write / algorithmic bytes of a half-hop pair of the "
+                                  f"whole-lattice FP32 solver (32^3x64, one system) = {ratio}, times the mean "
+                                  "algorithmic bytes per launch of the timed steps")
     ratio = TRAFFIC_RATIO.get("block_solve_cluster_kernel")
     if ratio is not None and blk_n:
         # DRAM bytes per launch, scaled from the capture by the algorithmic

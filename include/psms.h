@@ -454,6 +454,13 @@ psms_status psms_relative_gauge_fix(psms_ctx *ctx, int field_old, int field_new,
  * PSMS_EINVAL for another kind. */
 enum { PSMS_SOLVER_CGNR = 0, PSMS_SOLVER_BICGSTAB = 1 };
 psms_status psms_full_solver(psms_ctx *ctx, int kind);
+/* Relative residual reduction that the FP32 / BF16 inner Krylov solve of one
+ * defect-correction step of a whole-lattice solve aims for (delta in
+ * [1e-8, 0.5]); 0 restores the defaults (BiCGStab 1e-4, CGNR 2e-6 in FP32,
+ * 5e-3 in BF16).  A smaller delta means fewer outer steps (each one FP64
+ * application of D) and longer inner solves; the FP64 true-residual target
+ * is unchanged.  PSMS_EINVAL outside the range. */
+psms_status psms_inner_reduction(psms_ctx *ctx, double delta);
 /* Inner Krylov method of the Dirichlet block solves (default CGNR; the
  * autotuner then chooses among that method's variants only, so every tuned
  * choice gives identical results).  PSMS_EINVAL for another kind. */

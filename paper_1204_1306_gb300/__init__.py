@@ -23,6 +23,7 @@ __all__ = [
     "psms_block_plan_destroy", "BlockPlan", "psms_autotune", "psms_profile_read_block",
     "psms_domain_features_pair", "psms_checkpoint_save", "psms_checkpoint_load",
     "psms_relative_gauge_fix", "psms_profile_block_launches", "psms_hop_variant", "psms_full_solver",
+    "psms_inner_reduction",
     "psms_block_krylov", "SOLVER_CGNR", "SOLVER_BICGSTAB", "psms_level_covariance", "psms_level_coefficients",
     "psms_hyp_smear", "psms_hyp_block_action", "psms_block_action_change",
     "PREC_F64", "PREC_F32", "PREC_BF16", "OP_FULL", "OP_BLOCKS", "ACTIVE_BLOCKS", "ACTIVE_ALL",
@@ -145,6 +146,7 @@ _SIGS = {
     "psms_profile_block_launches": [_P, _I, _P, _P, _P],
     "psms_hop_variant": [_P, _I, _P],
     "psms_full_solver": [_P, _I],
+    "psms_inner_reduction": [_P, ctypes.c_double],
     "psms_block_krylov": [_P, _I],
     "psms_checkpoint_load": [_P, _I, ctypes.c_char_p, ctypes.POINTER(_U64), ctypes.POINTER(_U64)],
     "psms_profile_read_block": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), ctypes.POINTER(_D)],
@@ -523,6 +525,12 @@ def psms_full_solver(ctx, kind):
     ctx.check(ctx.lib.psms_full_solver(ctx.handle, int(kind)))
 
 
+def psms_inner_reduction(ctx, delta):
+    """Inner relative reduction per defect-correction step of whole-lattice
+    solves (0 restores the defaults)."""
+    ctx.check(ctx.lib.psms_inner_reduction(ctx.handle, float(delta)))
+
+
 def psms_block_krylov(ctx, kind):
     """Inner Krylov method of block solves: SOLVER_CGNR or SOLVER_BICGSTAB."""
     ctx.check(ctx.lib.psms_block_krylov(ctx.handle, int(kind)))
@@ -572,7 +580,9 @@ def psms_autotune(ctx, enable=True, block_variant=-1):
 
 
 def psms_profile_enable(ctx, enable):
-    ctx.check(ctx.lib.psms_profile_enable(ctx.handle, int(bool(enable))))
+    """0 off, 1 every full-operator hop launch, 10 + PREC_* only the launches
+    of that storage precision."""
+    ctx.check(ctx.lib.psms_profile_enable(ctx.handle, int(enable)))
 
 
 def psms_profile_read(ctx):

@@ -874,6 +874,7 @@ psms_status psms_filter_step(psms_ctx *ctx, int field, const psms_filter_params 
         cuda_check(cudaMemcpyAsync(ctx->rec_h.data(), d_h, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream),
                    "l3");
         cuda_check(cudaStreamSynchronize(ctx->stream), "l3");
+        mlp_check(ctx);
         n_learned = 0;
         for (int v : h3) n_learned += v;
         d_mask = d_acc3;
@@ -1187,6 +1188,13 @@ psms_status psms_full_solver(psms_ctx *ctx, int kind) {
     PSMS_TRY(ctx)
     if (kind != PSMS_SOLVER_CGNR && kind != PSMS_SOLVER_BICGSTAB) fail(PSMS_EINVAL, "unknown solver");
     ctx->full_solver = kind;
+    PSMS_CATCH(ctx)
+}
+
+psms_status psms_inner_reduction(psms_ctx *ctx, double delta) {
+    PSMS_TRY(ctx)
+    if (!(delta == 0.0 || (delta >= 1e-8 && delta <= 0.5))) fail(PSMS_EINVAL, "delta must be 0 or in [1e-8, 0.5]");
+    ctx->inner_delta = delta;
     PSMS_CATCH(ctx)
 }
 

@@ -65,6 +65,7 @@ struct psms_ctx {
     int hop_variant[3][2][2] = {{{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}};
     bool autotune = true;
     int forced_hop_variant = -1;  // -1: autotuned; else the variant index (mod the variant count)
+    double inner_delta = 0;       // inner relative reduction of whole-lattice solves (0: defaults)
     int full_solver = 1;          // inner Krylov method of whole-lattice solves: 0 CGNR, 1 BiCGStab
     int block_krylov = 0;         // inner Krylov method of block solves: 0 CGNR, 1 BiCGStab
     int outer[4] = {0, 0, 0, 0};  // outer blocks of the recursive decomposition (0: none)

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "mlp.hpp"
+#include "tc_gemm.cuh"
 
 namespace psms {
 
@@ -222,7 +223,7 @@ void pair_features(psms_ctx *c, const double2 *U, const double2 *Up, float *out)
 
 // ---------------------------------------------------------------------------
 // BF16 tensor-core GEMM: C[m][n] = alpha * sum_k A(m,k) B(n,k) + beta*C + bias[n]
-// (optional ReLU and BF16 copy), mma.sync.m16n8k16 with FP32 accumulation.
+// (optional ReLU and BF16 copy), FP32 accumulation in TMEM (tc_gemm.cuh).
 // A(m,k) = A[m*sAm + k*sAk] (FP32 or BF16), B(n,k) likewise.
 // ---------------------------------------------------------------------------
 struct GemmArgs {
@@ -242,86 +243,25 @@ struct GemmArgs {
     int relu;
 };
 
-constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
-
-__device__ __forceinline__ float ld_any(const void *p, long long i, int f32) {
-    return f32 ? ((const float *)p)[i] : __bfloat162float(((const __nv_bfloat16 *)p)[i]);
+template <int TN>
+static void gemm_tn(psms_ctx *c, const tc::Args &t) {
+    constexpr int smem = tc::smem_bytes<TN>();
+    cuda_check(cudaFuncSetAttribute(tc::gemm_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+               "tc gemm smem");
+    dim3 grid((t.N + TN - 1) / TN, (t.M + tc::TM - 1) / tc::TM);
+    tc::gemm_kernel<TN><<<grid, tc::NTHR, smem, c->stream>>>(t);
+    PSMS_LAUNCH_CHECK("tc::gemm_kernel");
 }
 
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs a) {
-    __shared__ __nv_bfloat16 As[GBM][GBK + GPAD];
-    __shared__ __nv_bfloat16 Bs[GBN][GBK + GPAD];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp >> 1, wn = warp & 1;
-    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-    const int gid = lane >> 2, tig = lane & 3;
-    float acc[2][4][4];
-    for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 4; ++j)
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-    for (int k0 = 0; k0 < a.K; k0 += GBK) {
-        for (int e = tid; e < GBM * GBK; e += 128) {
-            const int r = e / GBK, kk = e % GBK;
-            const int m = m0 + r, k = k0 + kk;
-            float v = (m < a.M && k < a.K) ? ld_any(a.A, (long long)m * a.sAm + (long long)k * a.sAk, a.a_f32) : 0.f;
-            As[r][kk] = __float2bfloat16(v);
-            const int n = n0 + r;
-            float w = (n < a.N && k < a.K) ? ld_any(a.B, (long long)n * a.sBn + (long long)k * a.sBk, a.b_f32) : 0.f;
-            Bs[r][kk] = __float2bfloat16(w);
-        }
-        __syncthreads();
-        for (int ks = 0; ks < GBK; ks += 16) {
-            uint32_t af[2][4], bfr[4][2];
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r = wm * 32 + mt * 16 + gid;
-                const int c = ks + tig * 2;
-                af[mt][0] = pack2(As[r][c], As[r][c + 1]);
-                af[mt][1] = pack2(As[r + 8][c], As[r + 8][c + 1]);
-                af[mt][2] = pack2(As[r][c + 8], As[r][c + 9]);
-                af[mt][3] = pack2(As[r + 8][c + 8], As[r + 8][c + 9]);
-            }
-            for (int nt = 0; nt < 4; ++nt) {
-                const int n = wn * 32 + nt * 8 + gid;
-                const int c = ks + tig * 2;
-                bfr[nt][0] = pack2(Bs[n][c], Bs[n][c + 1]);
-                bfr[nt][1] = pack2(Bs[n][c + 8], Bs[n][c + 9]);
-            }
-            for (int mt = 0; mt < 2; ++mt)
-                for (int nt = 0; nt < 4; ++nt) {
-                    float *d = acc[mt][nt];
-                    asm volatile(
-                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-                        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-                        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                        : "r"(af[mt][0]), "r"(af[mt][1]), "r"(af[mt][2]), "r"(af[mt][3]), "r"(bfr[nt][0]),
-                          "r"(bfr[nt][1]));
-                }
-        }
-        __syncthreads();
-    }
-    for (int mt = 0; mt < 2; ++mt)
-        for (int nt = 0; nt < 4; ++nt)
-            for (int q = 0; q < 4; ++q) {
-                const int m = m0 + wm * 32 + mt * 16 + gid + (q >= 2 ? 8 : 0);
-                const int n = n0 + wn * 32 + nt * 8 + tig * 2 + (q & 1);
-                if (m >= a.M || n >= a.N) continue;
-                float v = a.alpha * acc[mt][nt][q];
-                if (a.beta != 0.f && a.Cf) v += a.beta * a.Cf[(long long)m * a.ldc + n];
-                if (a.bias) v += a.bias[n];
-                if (a.relu) v = fmaxf(v, 0.f);
-                if (a.Cf) a.Cf[(long long)m * a.ldc + n] = v;
-                if (a.Cb) a.Cb[(long long)m * a.ldcb + n] = __float2bfloat16(v);
-            }
-}
-
-static void gemm(psms_ctx *c, const GemmArgs &a) {
-    dim3 grid((a.N + GBN - 1) / GBN, (a.M + GBM - 1) / GBM);
-    gemm_bf16_kernel<<<grid, 128, 0, c->stream>>>(a);
-    PSMS_LAUNCH_CHECK("gemm_bf16_kernel");
+static void gemm(psms_ctx *c, const GemmArgs &a, int *err) {
+    if (a.M < 1 || a.N < 1) return;
+    const tc::Args t{a.M, a.N, a.K, a.A, a.sAm, a.sAk, a.a_f32, a.B, a.sBn, a.sBk, a.b_f32, a.Cf, a.ldc,
+                     a.Cb, a.ldcb, a.bias, a.alpha, a.beta, a.relu, err};
+    // N = 64 (the input layer's weight gradient) takes the narrow tile
+    if (a.N <= 64)
+        gemm_tn<64>(c, t);
+    else
+        gemm_tn<256>(c, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -338,6 +278,7 @@ struct Mlp {
     float *m = nullptr, *v = nullptr;  // Adam moments (N_TRAIN)
     float *g = nullptr;         // gradient (N_TRAIN)
     __nv_bfloat16 *w1b = nullptr, *w2b = nullptr;
+    int *err = nullptr;  // set by a tensor-core GEMM whose bounded wait ran out
     long long step = 0;
 };
 
@@ -350,6 +291,8 @@ static Mlp &mlp_of(psms_ctx *c) {
         cuda_check(cudaMalloc(&m->g, sizeof(float) * N_TRAIN), "mlp alloc");
         cuda_check(cudaMalloc(&m->w1b, sizeof(__nv_bfloat16) * NH * NI), "mlp alloc");
         cuda_check(cudaMalloc(&m->w2b, sizeof(__nv_bfloat16) * NH * NH), "mlp alloc");
+        cuda_check(cudaMalloc(&m->err, sizeof(int)), "mlp alloc");
+        cuda_check(cudaMemset(m->err, 0, sizeof(int)), "mlp alloc");
         c->mlp = m;
         c->mlp_free = [](void *q) {
             Mlp *mm = (Mlp *)q;
@@ -359,6 +302,7 @@ static Mlp &mlp_of(psms_ctx *c) {
             cudaFree(mm->g);
             cudaFree(mm->w1b);
             cudaFree(mm->w2b);
+            cudaFree(mm->err);
             delete mm;
         };
     }
@@ -512,9 +456,9 @@ static void forward(psms_ctx *c, Mlp &m, const Work &w, const float *feats, cons
     to_bf16_kernel<<<(R * NI + 255) / 256, 256, 0, c->stream>>>(w.X, w.Xb, R * NI);
     PSMS_LAUNCH_CHECK("to_bf16");
     GemmArgs g1{R, NH, NI, w.Xb, NI, 1, 0, m.w1b, NI, 1, 0, w.H1, NH, w.H1b, NH, m.p + OFF_B1, 1.f, 0.f, 1};
-    gemm(c, g1);
+    gemm(c, g1, m.err);
     GemmArgs g2{R, NH, NH, w.H1b, NH, 1, 0, m.w2b, NH, 1, 0, w.H2, NH, nullptr, 0, m.p + OFF_B2, 1.f, 0.f, 1};
-    gemm(c, g2);
+    gemm(c, g2, m.err);
     out_kernel<<<(R + 3) / 4, 128, 0, c->stream>>>(w.H2, m.p, R, w.n);
     PSMS_LAUNCH_CHECK("out_kernel");
 }
@@ -533,19 +477,33 @@ static void backward(psms_ctx *c, Mlp &m, const Work &w, int B) {
     PSMS_LAUNCH_CHECK("d2");
     // dW2[j][i] = sum_r D2[r][j] H1[r][i]
     GemmArgs gw2{NH, NH, R, w.D2, 1, NH, 1, w.H1b, 1, NH, 0, g + OFF_W2, NH, nullptr, 0, nullptr, 1.f, 0.f, 0};
-    gemm(c, gw2);
+    gemm(c, gw2, m.err);
     colsum_kernel<<<(NH + 127) / 128, 128, 0, c->stream>>>(w.D2, nullptr, R, NH, g + OFF_B2);
     PSMS_LAUNCH_CHECK("colsum");
     // D1 = (D2 W2) * (H1 > 0)
     GemmArgs gd1{R, NH, NH, w.D2, NH, 1, 1, m.w2b, 1, NH, 0, w.D1, NH, nullptr, 0, nullptr, 1.f, 0.f, 0};
-    gemm(c, gd1);
+    gemm(c, gd1, m.err);
     mask_kernel<<<(unsigned)(((long long)R * NH + 255) / 256), 256, 0, c->stream>>>(w.D1, w.H1, (long long)R * NH);
     PSMS_LAUNCH_CHECK("mask");
     // dW1[i][c] = sum_r D1[r][i] X[r][c]
     GemmArgs gw1{NH, NI, R, w.D1, 1, NH, 1, w.X, 1, NI, 1, g + OFF_W1, NI, nullptr, 0, nullptr, 1.f, 0.f, 0};
-    gemm(c, gw1);
+    gemm(c, gw1, m.err);
     colsum_kernel<<<(NH + 127) / 128, 128, 0, c->stream>>>(w.D1, nullptr, R, NH, g + OFF_B1);
     PSMS_LAUNCH_CHECK("colsum");
+}
+
+// a tensor-core GEMM whose bounded wait ran out leaves the flag set: report
+// it once (PSMS_ETIMEOUT) and clear it
+void mlp_check(psms_ctx *c) {
+    if (!c->mlp) return;
+    Mlp &m = *(Mlp *)c->mlp;
+    int h = 0;
+    cuda_check(cudaMemcpyAsync(&h, m.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "mlp status");
+    cuda_check(cudaStreamSynchronize(c->stream), "mlp status");
+    if (h) {
+        cuda_check(cudaMemsetAsync(m.err, 0, sizeof(int), c->stream), "mlp status");
+        fail(PSMS_ETIMEOUT, "tensor-core GEMM of the MLP: a bounded mbarrier wait ran out");
+    }
 }
 
 void mlp_predict(psms_ctx *c, const float *feats, int B, float *h_out) {
@@ -622,6 +580,7 @@ psms_status psms_mlp_predict(psms_ctx *ctx, const float *feats_dev, int n, float
     MLP_TRY(ctx)
     if (!feats_dev || !h_dev || n < 1) fail(PSMS_EINVAL, "bad arguments");
     mlp_predict(ctx, feats_dev, n, h_dev);
+    mlp_check(ctx);
     MLP_CATCH(ctx)
 }
 
@@ -643,6 +602,7 @@ psms_status psms_mlp_grad(psms_ctx *ctx, const float *feats_dev, const double *l
     if (grad_host)
         cuda_check(cudaMemcpyAsync(grad_host, m.g, sizeof(float) * N_TRAIN, cudaMemcpyDeviceToHost, ctx->stream), "g");
     cuda_check(cudaStreamSynchronize(ctx->stream), "grad");
+    mlp_check(ctx);
     if (loss) *loss = hl / n;
     MLP_CATCH(ctx)
 }
@@ -729,6 +689,7 @@ psms_status psms_mlp_train(psms_ctx *ctx, const float *feats_dev, const double *
             eloss += hl / B;
         }
         if (loss_per_epoch) loss_per_epoch[ep] = nb ? eloss / nb : 0.0;
+        mlp_check(ctx);
     }
     MLP_CATCH(ctx)
 }

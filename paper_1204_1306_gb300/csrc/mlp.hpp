@@ -12,5 +12,8 @@ void domain_features(psms_ctx *c, const double2 *U, float *out, int stride, int 
 void pair_features(psms_ctx *c, const double2 *U, const double2 *Up, float *out);
 // h[b] = ys (n(z_b) - n(swap z_b)) / 2 for rows z_b = feats[b * 64 ..]
 void mlp_predict(psms_ctx *c, const float *feats, int B, float *h_out);
+// throws PSMS_ETIMEOUT if a tensor-core GEMM's bounded wait ran out since the
+// last check (synchronises the stream)
+void mlp_check(psms_ctx *c);
 
 }  // namespace psms

@@ -1061,6 +1061,7 @@ void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info)
     // remaining outer steps of this solve use CGNR
     bool bicg = c->full_solver == 1;
     auto delta_of = [&](bool b) {
+        if (!in64 && c->inner_delta > 0) return c->inner_delta;
         return in64 ? std::max(0.1 * q.tol, 1e-15) : (q.inner_prec == P32 ? (b ? 1e-4 : 2e-6) : 5e-3);
     };
     const int max_outer = in64 ? 6 : 30;

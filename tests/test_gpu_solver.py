@@ -192,3 +192,36 @@ def test_block_solver_shared_memory_link_variants(variant):
     ps.psms_autotune(c2, False, variant)
     got = ps.psms_logdet_ratio(c2, ps.LEVEL_BLOCK, 0, 1, 3, ps.EST_INTERP, 5, 0, 1e-13, ps.PREC_F32)
     assert np.abs(got - ref).max() < 1e-8
+
+
+def test_profile_precision_filter_and_inner_reduction():
+    """The hop profile counts only the launches of the storage precision
+    asked for (FP32 inner iterations and FP64 true residuals add up to all
+    launches), and a smaller inner reduction per defect-correction step
+    reaches the same FP64 true residual in no more outer steps."""
+    dims, block, kappa = (8, 8, 8, 8), (4, 4, 4, 4), 0.15
+    ctx = ps.psms_create(dims, block, kappa, 1)
+    ps.psms_gauge_init(ctx, 0, 0.3, 0x50534D53)
+    b = native(ctx, seeded.spinor(dims, 2))
+    ps.psms_solve(ctx, 0, ps.OP_FULL, b, torch.zeros_like(b), 1e-12, 20000, ps.PREC_F32)  # variants tuned
+    counts = {}
+    for mode in (1, 10 + ps.PREC_F32, 10 + ps.PREC_F64):
+        ps.psms_profile_enable(ctx, mode)
+        ps.psms_solve(ctx, 0, ps.OP_FULL, b, torch.zeros_like(b), 1e-12, 20000, ps.PREC_F32)
+        counts[mode] = ps.psms_profile_read(ctx)
+        ps.psms_profile_enable(ctx, 0)
+    (n_all, _, by_all), (n32, _, by32), (n64, _, by64) = counts[1], counts[10 + ps.PREC_F32], counts[10 + ps.PREC_F64]
+    assert n64 >= 1 and n32 > n64 and n32 + n64 == n_all
+    assert by32 + by64 == pytest.approx(by_all, rel=1e-12)
+    outer, xs = {}, {}
+    for delta in (0.0, 1e-6):
+        ps.psms_inner_reduction(ctx, delta)
+        x = torch.zeros_like(b)
+        info = ps.psms_solve(ctx, 0, ps.OP_FULL, b, x, 1e-12, 20000, ps.PREC_F32)
+        assert info["true_residual"] <= 1e-12
+        outer[delta], xs[delta] = info["outer_iters"], canonical(ctx, x)
+    assert outer[1e-6] <= outer[0.0]
+    assert rel_err(xs[1e-6], xs[0.0]) < 1e-10
+    with pytest.raises(ps.PsmsError):
+        ps.psms_inner_reduction(ctx, 0.9)
+    ps.psms_inner_reduction(ctx, 0.0)
