@@ -456,11 +456,20 @@ enum { PSMS_SOLVER_CGNR = 0, PSMS_SOLVER_BICGSTAB = 1 };
 psms_status psms_full_solver(psms_ctx *ctx, int kind);
 /* Relative residual reduction that the FP32 / BF16 inner Krylov solve of one
  * defect-correction step of a whole-lattice solve aims for (delta in
- * [1e-8, 0.5]); 0 restores the defaults (BiCGStab 1e-4, CGNR 2e-6 in FP32,
+ * [1e-8, 0.5]); 0 restores the defaults (BiCGStab 1e-6, CGNR 2e-6 in FP32,
  * 5e-3 in BF16).  A smaller delta means fewer outer steps (each one FP64
  * application of D) and longer inner solves; the FP64 true-residual target
  * is unchanged.  PSMS_EINVAL outside the range. */
 psms_status psms_inner_reduction(psms_ctx *ctx, double delta);
+/* Links of the FP32 / BF16 inner iterations of the estimators' batched
+ * whole-lattice solves (global level, domain levels): on = 1 (default)
+ * forms system k's links in the hop as a_k U + b_k U' from FP32 copies of
+ * the two endpoint fields of Eq. (gfparam), with the systems of a launch
+ * walked side by side so that every endpoint link leaves HBM about once per
+ * launch; on = 0 reads one materialised FP32 field per interpolation step.
+ * The FP64 true residuals use the FP64 interpolated fields either way, so
+ * both reach the same tolerance.  PSMS_EINVAL for another value. */
+psms_status psms_shared_links(psms_ctx *ctx, int on);
 /* Inner Krylov method of the Dirichlet block solves (default CGNR; the
  * autotuner then chooses among that method's variants only, so every tuned
  * choice gives identical results).  PSMS_EINVAL for another kind. */

@@ -23,7 +23,7 @@ __all__ = [
     "psms_block_plan_destroy", "BlockPlan", "psms_autotune", "psms_profile_read_block",
     "psms_domain_features_pair", "psms_checkpoint_save", "psms_checkpoint_load",
     "psms_relative_gauge_fix", "psms_profile_block_launches", "psms_hop_variant", "psms_full_solver",
-    "psms_inner_reduction",
+    "psms_inner_reduction", "psms_shared_links",
     "psms_block_krylov", "SOLVER_CGNR", "SOLVER_BICGSTAB", "psms_level_covariance", "psms_level_coefficients",
     "psms_hyp_smear", "psms_hyp_block_action", "psms_block_action_change",
     "PREC_F64", "PREC_F32", "PREC_BF16", "OP_FULL", "OP_BLOCKS", "ACTIVE_BLOCKS", "ACTIVE_ALL",
@@ -147,6 +147,7 @@ _SIGS = {
     "psms_hop_variant": [_P, _I, _P],
     "psms_full_solver": [_P, _I],
     "psms_inner_reduction": [_P, ctypes.c_double],
+    "psms_shared_links": [_P, _I],
     "psms_block_krylov": [_P, _I],
     "psms_checkpoint_load": [_P, _I, ctypes.c_char_p, ctypes.POINTER(_U64), ctypes.POINTER(_U64)],
     "psms_profile_read_block": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), ctypes.POINTER(_D)],
@@ -529,6 +530,12 @@ def psms_inner_reduction(ctx, delta):
     """Inner relative reduction per defect-correction step of whole-lattice
     solves (0 restores the defaults)."""
     ctx.check(ctx.lib.psms_inner_reduction(ctx.handle, float(delta)))
+
+
+def psms_shared_links(ctx, on):
+    """Shared-endpoint FP32 links in the estimators' whole-lattice solves
+    (default on)."""
+    ctx.check(ctx.lib.psms_shared_links(ctx.handle, int(on)))
 
 
 def psms_block_krylov(ctx, kind):

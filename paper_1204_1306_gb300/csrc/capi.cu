@@ -1198,6 +1198,13 @@ psms_status psms_inner_reduction(psms_ctx *ctx, double delta) {
     PSMS_CATCH(ctx)
 }
 
+psms_status psms_shared_links(psms_ctx *ctx, int on) {
+    PSMS_TRY(ctx)
+    if (on != 0 && on != 1) fail(PSMS_EINVAL, "on must be 0 or 1");
+    ctx->shared_links = on;
+    PSMS_CATCH(ctx)
+}
+
 psms_status psms_block_krylov(psms_ctx *ctx, int kind) {
     PSMS_TRY(ctx)
     if (kind != PSMS_SOLVER_CGNR && kind != PSMS_SOLVER_BICGSTAB) fail(PSMS_EINVAL, "unknown solver");
@@ -1314,8 +1321,9 @@ psms_status psms_autotune(psms_ctx *ctx, int enable, int block_variant) {
     ctx->autotune = enable != 0;
     ctx->forced_block_variant = block_variant;
     ctx->block_variant.clear();
-    for (auto &row : ctx->hop_variant)
-        for (auto &cell : row) cell[0] = cell[1] = -1;
+    for (auto &plane : ctx->hop_variant)
+        for (auto &row : plane)
+            for (auto &cell : row) cell[0] = cell[1] = -1;
     PSMS_CATCH(ctx)
 }
 

@@ -61,11 +61,14 @@ struct psms_ctx {
     int prof_cap = 0;
     long long prof_launches = 0;
     // autotuned hop-kernel variant per (storage precision, both parities,
-    // whole lattice or not)
-    int hop_variant[3][2][2] = {{{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}};
+    // whole lattice or not, shared-endpoint links or not); -1 untuned
+    int hop_variant[3][2][2][2] = {{{{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}},
+                                   {{{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}},
+                                   {{{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}}};
     bool autotune = true;
     int forced_hop_variant = -1;  // -1: autotuned; else the variant index (mod the variant count)
     double inner_delta = 0;       // inner relative reduction of whole-lattice solves (0: defaults)
+    int shared_links = 1;         // estimators' whole-lattice FP32 solves: shared-endpoint links
     int full_solver = 1;          // inner Krylov method of whole-lattice solves: 0 CGNR, 1 BiCGStab
     int block_krylov = 0;         // inner Krylov method of block solves: 0 CGNR, 1 BiCGStab
     int outer[4] = {0, 0, 0, 0};  // outer blocks of the recursive decomposition (0: none)

@@ -24,7 +24,46 @@ struct HopArgs {
     unsigned long long *prof_sites;  // profiling: output sites of active systems
     const int *sys_map;              // systems launched (null: all, k = blockIdx.y)
     const int *rank_active;          // per rank: 0 skips its output sites (null: none skipped)
+    LinkInterp li;                   // shared-endpoint FP32 links (li.U0 null: U, U_bs)
+    int nsf;                         // > 0: nsf systems fastest in blockIdx.x (gridDim.y = 1)
+    int nct;                         // CTAs per system
 };
+
+// (launched system, CTA of that system) of this CTA
+__device__ __forceinline__ void hop_cta(int nsf, int &ks, int &bx) {
+    if (nsf > 0) {
+        ks = (int)(blockIdx.x % (unsigned)nsf);
+        bx = (int)(blockIdx.x / (unsigned)nsf);
+    } else {
+        ks = (int)blockIdx.y;
+        bx = (int)blockIdx.x;
+    }
+}
+
+// link (mu, idx) of system k: from its own field (LI = 0), or a_k U0 + b_k U1
+// of the shared endpoints (LI = 1; U0 alone where the endpoints agree)
+template <class SL, int LI, class E>
+__device__ __forceinline__ SU3<typename SL::R> hop_link(const HopArgs<E> &a, const typename SL::elem *U, int k, int mu,
+                                                       long long idx) {
+    if constexpr (LI && SL::VSH == 1) {
+        {
+            SU3<float> u = load_link<SL>(a.li.U0, a.g.V, mu, idx);
+            if (__ldg(a.li.flag + (long long)mu * a.g.V + idx)) {
+                const SU3<float> u1 = load_link<SL>(a.li.U1, a.g.V, mu, idx);
+                const float2 ab = __ldg(a.li.ab + k);
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        u.e[i][j].re = fmaf(ab.y, u1.e[i][j].re, ab.x * u.e[i][j].re);
+                        u.e[i][j].im = fmaf(ab.y, u1.e[i][j].im, ab.x * u.e[i][j].im);
+                    }
+            }
+            return u;
+        }
+    }
+    return load_link<SL>(U, a.g.V, mu, idx);
+}
 
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double *sh) {
@@ -44,21 +83,24 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 // neighbour indices are computed first and the eight hops run as one
 // branch-free sequence, so the compiler can issue later directions' loads
 // before earlier directions' arithmetic (more loads in flight per thread).
-template <class S, class SL, int NT, int MINB, int ALL>
+// LI = 1: links from the shared endpoints (FP32 links only).
+template <class S, class SL, int NT, int MINB, int ALL, int LI = 0>
 __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S::elem> a) {
     using R = typename SL::R;
     using E = typename S::elem;
     using EL = typename SL::elem;
     __shared__ double sh[NT / 32];
-    const int k = a.sys_map ? a.sys_map[blockIdx.y] : (int)blockIdx.y;
+    int ks, bx;
+    hop_cta(a.nsf, ks, bx);
+    const int k = a.sys_map ? a.sys_map[ks] : ks;
     if (a.active && !a.active[k]) {
-        if (a.partial && threadIdx.x == 0) a.partial[(long long)k * gridDim.x + blockIdx.x] = 0.0;
+        if (a.partial && threadIdx.x == 0) a.partial[(long long)k * a.nct + bx] = 0.0;
         return;
     }
     const Geom &g = a.g;
     const long long per_p = (long long)a.n_ranks * g.Vbh;
     const long long total = (a.p < 0 ? 2 : 1) * per_p;
-    const long long t = (long long)blockIdx.x * NT + threadIdx.x;
+    const long long t = (long long)bx * NT + threadIdx.x;
     double nrm = 0.0;
     bool work = t < total;
     int p = 0, r = 0, j = 0;
@@ -135,7 +177,7 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
 #pragma unroll
                         for (int c = 0; c < 3; ++c) h.c[q][c] = bsr * h.c[q][c];
                 }
-                SU3<R> u = load_link<SL>(U, g.V, mu, fwd ? s : snb[d]);
+                SU3<R> u = hop_link<SL, LI>(a, U, k, mu, fwd ? s : snb[d]);
                 reconstruct_add(mu, tt, fwd ? su3_mul(u, h) : su3_dag_mul(u, h), acc);
             }
         } else {
@@ -153,7 +195,7 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
 #pragma unroll
                         for (int c = 0; c < 3; ++c) h.c[q][c] = R(-1) * h.c[q][c];
                 }
-                SU3<R> u = load_link<SL>(U, g.V, mu, s);
+                SU3<R> u = hop_link<SL, LI>(a, U, k, mu, s);
                 reconstruct_add(mu, tf, su3_mul(u, h), acc);
             }
             if (neighbour(g, bi, r, p, y, ll, mu, -1, a.mode, sn, bs)) {
@@ -166,7 +208,7 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
 #pragma unroll
                         for (int c = 0; c < 3; ++c) h.c[q][c] = R(-1) * h.c[q][c];
                 }
-                SU3<R> u = load_link<SL>(U, g.V, mu, sn);
+                SU3<R> u = hop_link<SL, LI>(a, U, k, mu, sn);
                 reconstruct_add(mu, tb, su3_dag_mul(u, h), acc);
             }
         }
@@ -203,7 +245,7 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
     }
     if (a.partial) {
         double tot = block_sum<NT>(nrm, sh);
-        if (threadIdx.x == 0) a.partial[(long long)k * gridDim.x + blockIdx.x] = tot;
+        if (threadIdx.x == 0) a.partial[(long long)k * a.nct + bx] = tot;
     }
 }
 
@@ -393,18 +435,33 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
     a.prof_sites = nullptr;
     a.sys_map = h.sys_map;
     a.rank_active = h.rank_active;
+    const bool shared_links = h.li.U0 != nullptr;
+    a.li = h.li;
+    if (shared_links) {
+        if (h.prec == P64 || !h.li.U1 || !h.li.ab || !h.li.flag)
+            fail(PSMS_EINVAL, "hop_launch: shared-endpoint links need FP32 storage, U1, ab and flags");
+        a.U = h.li.U0;
+        a.U_bs = 0;
+    }
     const int nct = hop_ctas(c, h);
     const int nsys = h.sys_map ? h.n_map : h.n_sys;
     if (nct == 0 || nsys == 0) return 0;
-    dim3 grid(nct, nsys);
+    a.nct = nct;
+    // shared-endpoint links: the systems of a launch run side by side (CTA
+    // index = cta * nsys + system), so each endpoint link leaves HBM once
+    a.nsf = shared_links ? nsys : 0;
+    const dim3 grid = shared_links ? dim3((unsigned)((long long)nct * nsys), 1) : dim3(nct, nsys);
     double bytes = 0;
     int slot = -1;
     if (c->prof && h.mode == HOP_ALL && (c->prof_prec < 0 || c->prof_prec == h.prec)) {
         // algorithmic bytes per output site of an active system: in + out
         // (+ y, y2) spinors and 4 links (both parities) or 8 (one parity);
-        // the device counts the output sites of the systems still active
+        // with shared-endpoint links the two endpoint fields are read once
+        // per launch, i.e. 2/nsys of a link field per system; the device
+        // counts the output sites of the systems still active
         const double sp = 12.0 * sizeof(E), lk = 9.0 * sizeof(typename SL::elem);
-        bytes = 2 * sp + (h.y.p ? sp : 0) + (h.y2.p ? sp : 0) + 4 * lk * (h.p < 0 ? 1 : 2);
+        const double links = 4 * lk * (h.p < 0 ? 1 : 2) * (shared_links ? 2.0 / nsys : 1.0);
+        bytes = 2 * sp + (h.y.p ? sp : 0) + (h.y2.p ? sp : 0) + links;
         slot = prof_begin(c);
         a.prof_sites = prof_counter(c, slot);
     }
@@ -430,14 +487,20 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
                                      hop_kernel<S, SL, HOP_NT, 4, 1>, hop_kernel<S, SL, HOP_NT, 5, 1>,
                                      hop_kernel<S, SL, HOP_NT, 6, 1>, hop_kernel<S, SL, HOP_NT, 7, 1>,
                                      hop_staged_kernel<S, SL, HOP_NT, 4>, hop_staged_kernel<S, SL, HOP_NT, 6>};
-        vars = all ? v32all : v32;
-        nvar = all ? (staged ? 10 : 8) : 4;
+        // shared-endpoint links (whole lattice): register caps 2, 3, 4, 5
+        // CTAs/SM, general and branch-free forms
+        static const KFn v32li[] = {hop_kernel<S, SL, HOP_NT, 2, 0, 1>, hop_kernel<S, SL, HOP_NT, 4, 0, 1>,
+                                    hop_kernel<S, SL, HOP_NT, 2, 1, 1>, hop_kernel<S, SL, HOP_NT, 3, 1, 1>,
+                                    hop_kernel<S, SL, HOP_NT, 4, 1, 1>, hop_kernel<S, SL, HOP_NT, 5, 1, 1>};
+        if (shared_links && !all) fail(PSMS_EINVAL, "hop_launch: shared-endpoint links on whole-lattice hops only");
+        vars = shared_links ? v32li : (all ? v32all : v32);
+        nvar = shared_links ? 6 : (all ? (staged ? 10 : 8) : 4);
     } else {
         static const KFn v64[] = {hop_kernel<S, SL, HOP_NT, 2, 0>};
         vars = v64;
         nvar = 1;
     }
-    int &choice = c->hop_variant[h.prec][h.p < 0 ? 1 : 0][all ? 1 : 0];
+    int &choice = c->hop_variant[h.prec][h.p < 0 ? 1 : 0][all ? 1 : 0][shared_links ? 1 : 0];
     if (choice < 0 && c->autotune && nvar > 1 && slot < 0 && c->forced_hop_variant < 0) {
         cudaEvent_t e0, e1;
         cuda_check(cudaEventCreate(&e0), "tune event");

@@ -351,7 +351,8 @@ static long long one_minus_PQ(psms_ctx *c, const double2 *U64, const float2 *U32
 }
 
 // w = (1 - P Q(U_{i+1}))^-1 v = v - P [D^-1 (0, D_wb v)]_black
-static long long inv_one_minus_PQ(psms_ctx *c, const double2 *U64, const float2 *U32, long long Ubs, int N,
+static long long inv_one_minus_PQ(psms_ctx *c, const double2 *U64, const float2 *U32, const LinkInterp &li,
+                                  long long Ubs, int N,
                                   const double2 *v, double2 *w, double tol, int inner) {
     const Geom &g = c->g;
     const long long V = g.V, fs = 12 * V;
@@ -377,6 +378,7 @@ static long long inv_one_minus_PQ(psms_ctx *c, const double2 *U64, const float2 
     q.x = View<double2>{z, V, 0, fs};
     q.U64 = U64;
     q.U32 = U32;
+    q.li32 = li;
     q.U64_bs = Ubs;
     q.tol = tol;
     q.inner_prec = inner;
@@ -385,6 +387,55 @@ static long long inv_one_minus_PQ(psms_ctx *c, const double2 *U64, const float2 
     // z holds values on white sites too; P vanishes there
     sub_proj(c, w, v, z, N);
     return info.inner_iters;
+}
+
+__global__ void link_diff_kernel(const float2 *u0, const float2 *u1, long long V, unsigned char *flag) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4 * V) return;
+    const int mu = (int)(t / V);
+    const long long s = t - (long long)mu * V;
+    const SU3<float> a = load_link<Store<float>>(u0, V, mu, s), b = load_link<Store<float>>(u1, V, mu, s);
+    bool d = false;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) d = d || a.e[i][j].re != b.e[i][j].re || a.e[i][j].im != b.e[i][j].im;
+    flag[t] = d ? 1 : 0;
+}
+
+SharedEnds shared_ends(psms_ctx *c, const double2 *ends64, const char *tag) {
+    const long long V = c->g.V, nel = 36 * V;
+    SharedEnds e;
+    e.u0 = (float2 *)scratch(c, std::string("ends32_") + tag, sizeof(float2) * 2 * nel);
+    e.u1 = e.u0 + nel;
+    e.flag = (unsigned char *)scratch(c, std::string("endsflag_") + tag, (size_t)(4 * V));
+    links_to_f32(c, ends64, e.u0, nel);
+    links_to_f32(c, ends64 + nel, e.u1, nel);
+    link_diff_kernel<<<(unsigned)((4 * V + 255) / 256), 256, 0, c->stream>>>(e.u0, e.u1, V, e.flag);
+    PSMS_LAUNCH_CHECK("link_diff_kernel");
+    return e;
+}
+
+LinkInterp link_interp(psms_ctx *c, const SharedEnds &e, int N, int i0, int n, int shift, int mode,
+                       const char *tag) {
+    std::vector<float2> h(n);
+    for (int k = 0; k < n; ++k) {
+        if (mode == PSMS_EST_INDEPENDENT) {
+            h[k] = shift ? make_float2(0.f, 1.f) : make_float2(1.f, 0.f);
+        } else {
+            const int i = i0 + k + shift;
+            h[k] = make_float2((float)((double)(N - i) / N), (float)((double)i / N));
+        }
+    }
+    float2 *d = (float2 *)scratch(c, std::string("li_ab_") + tag, sizeof(float2) * n);
+    cuda_check(cudaMemcpyAsync(d, h.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, c->stream), "link coefs");
+    cuda_check(cudaStreamSynchronize(c->stream), "link coefs");
+    LinkInterp li;
+    li.U0 = e.u0;
+    li.U1 = e.u1;
+    li.ab = d;
+    li.flag = e.flag;
+    return li;
 }
 
 static long long global_level_chunk(psms_ctx *c, const double2 *U, const double2 *Up, int N, int i0, int n,
@@ -399,7 +450,14 @@ static long long global_level_chunk(psms_ctx *c, const double2 *U, const double2
     double2 *w = (double2 *)scratch(c, "gl_w", sizeof(double2) * fs * n);
     noise(c, xi, n, seed, counter, PSMS_LEVEL_GLOBAL, 1, i0);
     long long tot = one_minus_PQ(c, pr.a64, pr.a32, pr.bs, n, xi, v, tol, inner);
-    tot += inv_one_minus_PQ(c, pr.b64, pr.b32, pr.bs, n, v, w, tol, inner);
+    // the whole-lattice FP32 solves read shared endpoint links (op(U_{i+1}))
+    LinkInterp li;
+    if (inner != P64 && c->shared_links) {
+        double2 *e64 = (double2 *)scratch(c, "ends64_glb", sizeof(double2) * 2 * it.bs);
+        interpolate(c, U, Up, e64, nullptr, 1, 0, 2);
+        li = link_interp(c, shared_ends(c, e64, "glb"), N, i0, n, 1, mode, "glb");
+    }
+    tot += inv_one_minus_PQ(c, pr.b64, pr.b32, li, pr.bs, n, v, w, tol, inner);
     double *nw = (double *)scratch(c, "gl_nw", sizeof(double) * n);
     double *nx = (double *)scratch(c, "gl_nx", sizeof(double) * n);
     norm2_batch(c, P64, View<void>{w, V, 0, fs}, 0, V, n, nw);

@@ -25,4 +25,18 @@ void decide(psms_ctx *c, const double *d_delta, int nb, int N, int per_block, ui
 // h (float, per block) -> FP64 copy
 void float_to_double(psms_ctx *c, const float *a, double *b, int n);
 
+// FP32 copies of the two endpoint fields of Eq. (gfparam) (ends64: U then U',
+// 36 V complex each, masked as the caller needs) and the per-link flags
+// where they differ: the shared-endpoint links of whole-lattice FP32 solves
+struct SharedEnds {
+    float2 *u0 = nullptr, *u1 = nullptr;
+    unsigned char *flag = nullptr;
+};
+SharedEnds shared_ends(psms_ctx *c, const double2 *ends64, const char *tag);
+// the links of a chunk's n systems: system k uses field i0 + k + shift of
+// Eq. (gfparam), a_k = (N - i)/N, b_k = i/N (independent mode: U for
+// shift 0, U' for shift 1)
+LinkInterp link_interp(psms_ctx *c, const SharedEnds &e, int N, int i0, int n, int shift, int mode,
+                       const char *tag);
+
 }  // namespace psms

@@ -16,6 +16,19 @@ struct View {
 
 enum Prec : int { P64 = PSMS_PREC_F64, P32 = PSMS_PREC_F32, PB16 = PSMS_PREC_BF16 };
 
+// FP32 links of system k given as a_k U0 + b_k U1 of two endpoint fields
+// (Eq. (gfparam): every interpolation step's links lie on the line between
+// the endpoints), formed in the hop instead of read from a materialised
+// field per system.  Links where U0 and U1 agree (flag 0: outside the
+// updated blocks) are read from U0 alone.  A launch then walks its systems
+// fastest, so all systems read each endpoint link from HBM about once and
+// from L2 afterwards.
+struct LinkInterp {
+    const float2 *U0 = nullptr, *U1 = nullptr;  // canonical FP32 link layout
+    const float2 *ab = nullptr;                 // device, per system: (a_k, b_k)
+    const unsigned char *flag = nullptr;        // device, per link mu * V + s
+};
+
 // out = a*y + a2*y2 + b*H(in), H the hopping term of Eq. (Dw) (sum over the
 // 8 neighbours of U (1 -/+ gamma) psi), restricted by `mode`, for output
 // parity p (-1: both) on the blocks of rank [rank_lo, rank_lo + n_ranks).
@@ -37,6 +50,8 @@ struct HopCall {
     // optional per-rank flags (device): output sites of ranks flagged 0 are
     // skipped (left unwritten)
     const int *rank_active = nullptr;
+    // optional shared-endpoint FP32 links (replace U / U_bs; FP32 links only)
+    LinkInterp li;
 };
 // returns the number of CTAs per system (for the partial sums)
 int hop_launch(psms_ctx *c, const HopCall &h);

@@ -239,7 +239,8 @@ const int *outer_colour_ranks(psms_ctx *c, int keep) {
 // (optional) restricts it to the inner blocks of one outer colour when the
 // links decouple the colours and b vanishes on the other
 long long solve_all(psms_ctx *c, const double2 *U64, const float2 *U32, long long bs, int n, const double2 *b,
-                    double2 *x, double tol, int inner, const int *rank_active = nullptr) {
+                    double2 *x, double tol, int inner, const int *rank_active = nullptr,
+                    const LinkInterp &li = LinkInterp{}) {
     const long long V = c->g.V, fs = 12 * V;
     FullSolveReq q;
     q.n_sys = n;
@@ -247,6 +248,7 @@ long long solve_all(psms_ctx *c, const double2 *U64, const float2 *U32, long lon
     q.x = View<double2>{x, V, 0, fs};
     q.U64 = U64;
     q.U32 = U32;
+    q.li32 = li;
     q.U64_bs = bs;
     q.tol = tol;
     q.inner_prec = inner;
@@ -254,6 +256,16 @@ long long solve_all(psms_ctx *c, const double2 *U64, const float2 *U32, long lon
     psms_solve_info info;
     solve_full_batch(c, q, &info);
     return info.inner_iters;
+}
+
+// shared FP32 endpoint links (U, U' masked by `kind`) of the whole-lattice
+// FP32 solves
+SharedEnds outer_ends(psms_ctx *c, const double2 *U, const double2 *Up, int kind, const char *tag) {
+    const long long nel = 36 * c->g.V;
+    double2 *e64 = (double2 *)scratch(c, std::string("oends64_") + tag, sizeof(double2) * 2 * nel);
+    interpolate(c, U, Up, e64, nullptr, 1, 0, 2);
+    if (kind) mask_links(c, e64, nel, 2, kind);
+    return shared_ends(c, e64, tag);
 }
 
 // out = -1/2 H(in) with the given links over the whole lattice
@@ -354,7 +366,9 @@ long long sub_chunk(psms_ctx *c, const double2 *U, const double2 *Up, int N, int
     h.in = View<void>{v, V, 0, fs};
     h.out = View<void>{t1, V, 0, fs};
     hop_launch(c, h);
-    tot += solve_all(c, pr.b64, pr.b32, pr.bs, n, t1, t2, tol, inner);
+    LinkInterp li;
+    if (inner != P64 && c->shared_links) li = link_interp(c, outer_ends(c, U, Up, 1, "sub"), N, i0, n, 1, mode, "sub");
+    tot += solve_all(c, pr.b64, pr.b32, pr.bs, n, t1, t2, tol, inner, nullptr, li);
     sub_projected(c, outer::SUB, w, v, t2, n);
     // per outer block |w|^2 - |xi|^2, summed over its inner blocks in rank order
     double *nw = (double *)scratch(c, "sub_nw", sizeof(double) * nr * n);
@@ -383,9 +397,16 @@ long long sub_chunk(psms_ctx *c, const double2 *U, const double2 *Up, int N, int
 long long outer_global_chunk(psms_ctx *c, const double2 *U, const double2 *Up, int N, int i0, int n, int mode,
                              uint64_t seed, uint64_t counter, double tol, int inner, std::vector<double> &h_delta) {
     const long long V = c->g.V, fs = 12 * V;
-    const bool need32 = inner != P64;
-    LinkSet lf = make_links(c, U, Up, N, mode, i0, n, 0, need32, "ogf");
-    LinkSet lm = make_links(c, U, Up, N, mode, i0, n, 1, need32, "ogm");
+    // the whole-lattice FP32 solves read shared endpoint links: no FP32
+    // copies of the interpolated fields
+    const bool shared = inner != P64 && c->shared_links;
+    LinkSet lf = make_links(c, U, Up, N, mode, i0, n, 0, inner != P64 && !shared, "ogf");
+    LinkSet lm = make_links(c, U, Up, N, mode, i0, n, 1, inner != P64 && !shared, "ogm");
+    LinkInterp lim, lif;
+    if (shared) {
+        lim = link_interp(c, outer_ends(c, U, Up, 1, "ogm"), N, i0, n, 0, mode, "ogm");
+        lif = link_interp(c, outer_ends(c, U, Up, 0, "ogf"), N, i0, n, 1, mode, "ogf");
+    }
     LinkSet lc = make_links(c, U, Up, N, mode, i0, n, 2, false, "ogc");
     LP pf = pair_of(lf, mode), pm = pair_of(lm, mode), pc = pair_of(lc, mode);
     auto buf = [&](const char *name) { return (double2 *)scratch(c, name, sizeof(double2) * fs * n); };
@@ -400,15 +421,15 @@ long long outer_global_chunk(psms_ctx *c, const double2 *U, const double2 *Up, i
     const int *white = outer_colour_ranks(c, 1), *black = outer_colour_ranks(c, 0);
     hop_all(c, pc.a64, pc.bs, n, xi, t1);  // hops between outer blocks
     keep_colour(c, t1, n, 1);               // D_wb xi
-    tot += solve_all(c, pm.a64, pm.a32, pm.bs, n, t1, t2, tol, inner, white);  // D_ww^-1 (outer Dirichlet)
+    tot += solve_all(c, pm.a64, pm.a32, pm.bs, n, t1, t2, tol, inner, white, lim);  // D_ww^-1 (outer Dirichlet)
     hop_all(c, pc.a64, pc.bs, n, t2, t1);
     keep_colour(c, t1, n, 0);  // D_bw
-    tot += solve_all(c, pm.a64, pm.a32, pm.bs, n, t1, t2, tol, inner, black);  // D_bb^-1
+    tot += solve_all(c, pm.a64, pm.a32, pm.bs, n, t1, t2, tol, inner, black, lim);  // D_bb^-1
     sub_projected(c, outer::OUTER, v, xi, t2, n);
     // w = (1 - P Q(U_{i+1}))^-1 v = v - P [D^-1 (0, D_wb v)]_black
     hop_all(c, pc.b64, pc.bs, n, v, t1);
     keep_colour(c, t1, n, 1);
-    tot += solve_all(c, pf.b64, pf.b32, pf.bs, n, t1, t2, tol, inner);
+    tot += solve_all(c, pf.b64, pf.b32, pf.bs, n, t1, t2, tol, inner, nullptr, lif);
     sub_projected(c, outer::OUTER, w, v, t2, n);
     double *nw = (double *)scratch(c, "og_nw", sizeof(double) * n);
     double *nx = (double *)scratch(c, "og_nx", sizeof(double) * n);

@@ -42,6 +42,9 @@ struct FullSolveReq {
     // flagged and unflagged ranks (links across are zero) and b vanishes on
     // the unflagged ones, so x vanishes there too and those sites are skipped
     const int *rank_active = nullptr;
+    // optional: the FP32/BF16 inner iterations take system k's links as
+    // a_k U0 + b_k U1 of two shared FP32 endpoint fields (U32 unused)
+    LinkInterp li32;
 };
 void solve_full_batch(psms_ctx *c, const FullSolveReq &q, psms_solve_info *info);
 
