@@ -161,8 +161,7 @@ def allsum(ws, v):
 # DRAM bytes (ncu dram__bytes_read.sum + write.sum) / algorithmic bytes of
 # captured launches of the current kernels (None: no capture of this build)
 TRAFFIC_RATIO = {"block_solve_cluster_kernel": None,
-                 # one FP32 half-hop pair of the whole-lattice solver, 32^3x64
-                 "hop_kernel": 1.058}
+                 "hop_kernel": None}
 
 
 def roofline_entry(kernel, n, ms, nbytes, peak, peak_kind):
@@ -958,8 +957,8 @@ def our_arm(args):
     ratio = TRAFFIC_RATIO.get("hop_kernel")
     if ratio is not None and hop_n:
         rl_hop["traffic"] = ratio * hop_bytes / hop_n
-        rl_hop["traffic_note"] = ("ncu dram__bytes_read+write / algorithmic bytes of a half-hop pair of the "
-                                  f"whole-lattice FP32 solver (32^3x64, one system) = {ratio}, times the mean "
+        rl_hop["traffic_note"] = ("ncu dram__bytes_read+write / algorithmic bytes of captured launches of the "
+                                  f"shared-endpoint-link FP32 hop (32^3x64 global level) = {ratio}, times the mean "
                                   "algorithmic bytes per launch of the timed steps")
     ratio = TRAFFIC_RATIO.get("block_solve_cluster_kernel")
     if ratio is not None and blk_n:

@@ -6,6 +6,7 @@
 // (rank-2 projectors), SU(3) x half-spinor, reconstruction.  Fields use the
 // structure-of-arrays even-odd block-major layout, so a warp reads each
 // component of 32 consecutive sites in one coalesced transaction.
+#include "bicgstab.cuh"
 #include "kernels.hpp"
 
 namespace psms {
@@ -27,6 +28,14 @@ struct HopArgs {
     LinkInterp li;                   // shared-endpoint FP32 links (li.U0 null: U, U_bs)
     int nsf;                         // > 0: nsf systems fastest in blockIdx.x (gridDim.y = 1)
     int nct;                         // CTAs per system
+    // fused BiCGStab reduction (dot 0: none; see HopDot)
+    int dot;
+    View<E> dx;
+    BCS *dst;
+    double *dre, *dim, *daa;
+    unsigned int *dcnt;
+    int dstage, dmaxit;
+    int *dflags;
 };
 
 // (launched system, CTA of that system) of this CTA
@@ -41,11 +50,24 @@ __device__ __forceinline__ void hop_cta(int nsf, int &ks, int &bx) {
 }
 
 // link (mu, idx) of system k: from its own field (LI = 0), or a_k U0 + b_k U1
-// of the shared endpoints (LI = 1; U0 alone where the endpoints agree)
+// of the shared endpoints (LI = 1: U0 alone where the endpoints agree; LI =
+// 2: always both, no flag and no divergent branch)
 template <class SL, int LI, class E>
 __device__ __forceinline__ SU3<typename SL::R> hop_link(const HopArgs<E> &a, const typename SL::elem *U, int k, int mu,
                                                        long long idx) {
-    if constexpr (LI && SL::VSH == 1) {
+    if constexpr (LI == 2 && SL::VSH == 1) {
+        SU3<float> u = load_link<SL>(a.li.U0, a.g.V, mu, idx);
+        const SU3<float> u1 = load_link<SL>(a.li.U1, a.g.V, mu, idx);
+        const float2 ab = __ldg(a.li.ab + k);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                u.e[i][j].re = fmaf(ab.y, u1.e[i][j].re, ab.x * u.e[i][j].re);
+                u.e[i][j].im = fmaf(ab.y, u1.e[i][j].im, ab.x * u.e[i][j].im);
+            }
+        return u;
+    } else if constexpr (LI == 1 && SL::VSH == 1) {
         {
             SU3<float> u = load_link<SL>(a.li.U0, a.g.V, mu, idx);
             if (__ldg(a.li.flag + (long long)mu * a.g.V + idx)) {
@@ -102,6 +124,7 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
     const long long total = (a.p < 0 ? 2 : 1) * per_p;
     const long long t = (long long)bx * NT + threadIdx.x;
     double nrm = 0.0;
+    double d_re = 0.0, d_im = 0.0, d_aa = 0.0;  // fused BiCGStab dot partials
     bool work = t < total;
     int p = 0, r = 0, j = 0;
     if (work) {
@@ -236,6 +259,26 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
                 for (int c = 0; c < 3; ++c) o.c[q][c] = o.c[q][c] + ca * v.c[q][c];
         }
         store_spinor<S>(a.out.p + k * a.out.bs, a.out.cs, s - a.out.off, o);
+        if (a.dot) {
+            // the BiCGStab dot product of the output: the 12 components
+            // summed in the inner precision (threads and CTAs in FP64)
+            const Spinor<R> w = a.dot == 1 ? load_spinor<S>(a.dx.p + k * a.dx.bs, a.dx.cs, s - a.dx.off)
+                                           : load_spinor<S>(a.y.p + k * a.y.bs, a.y.cs, s - a.y.off);
+            R tre = 0, tim = 0, taa = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const cpx<R> x = a.dot == 1 ? w.c[q][c] : o.c[q][c];
+                    const cpx<R> y = a.dot == 1 ? o.c[q][c] : w.c[q][c];
+                    tre += x.re * y.re + x.im * y.im;
+                    tim += x.re * y.im - x.im * y.re;
+                    taa += x.re * x.re + x.im * x.im;
+                }
+            d_re = (double)tre;
+            d_im = (double)tim;
+            d_aa = (double)taa;
+        }
         if (a.partial) {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
@@ -246,6 +289,11 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
     if (a.partial) {
         double tot = block_sum<NT>(nrm, sh);
         if (threadIdx.x == 0) a.partial[(long long)k * a.nct + bx] = tot;
+    }
+    if (a.dot) {
+        __shared__ double shd[3][NT / 32];
+        bcg_partials_and_stage<NT>(a.dst, d_re, d_im, d_aa, a.dre, a.dim, a.daa, a.dcnt, a.dstage, a.dmaxit,
+                                   a.dflags, shd, k, bx, a.nct);
     }
 }
 
@@ -437,6 +485,19 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
     a.rank_active = h.rank_active;
     const bool shared_links = h.li.U0 != nullptr;
     a.li = h.li;
+    a.dot = h.dot.dot;
+    a.dx = cv(h.dot.x);
+    a.dst = h.dot.st;
+    a.dre = h.dot.re;
+    a.dim = h.dot.im;
+    a.daa = h.dot.aa;
+    a.dcnt = h.dot.cnt;
+    a.dstage = h.dot.stage;
+    a.dmaxit = h.dot.maxit;
+    a.dflags = h.dot.flags;
+    if (a.dot && (h.prec != P32 || h.p < 0 || !h.dot.st || !h.dot.cnt || (a.dot == 2 && !h.y.p) ||
+                  (a.dot == 1 && !h.dot.x.p)))
+        fail(PSMS_EINVAL, "hop_launch: a fused reduction needs FP32 storage, one parity and its vectors");
     if (shared_links) {
         if (h.prec == P64 || !h.li.U1 || !h.li.ab || !h.li.flag)
             fail(PSMS_EINVAL, "hop_launch: shared-endpoint links need FP32 storage, U1, ab and flags");
@@ -461,7 +522,7 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
         // counts the output sites of the systems still active
         const double sp = 12.0 * sizeof(E), lk = 9.0 * sizeof(typename SL::elem);
         const double links = 4 * lk * (h.p < 0 ? 1 : 2) * (shared_links ? 2.0 / nsys : 1.0);
-        bytes = 2 * sp + (h.y.p ? sp : 0) + (h.y2.p ? sp : 0) + links;
+        bytes = 2 * sp + (h.y.p ? sp : 0) + (h.y2.p ? sp : 0) + (a.dot == 1 ? sp : 0) + links;
         slot = prof_begin(c);
         a.prof_sites = prof_counter(c, slot);
     }
@@ -487,21 +548,27 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
                                      hop_kernel<S, SL, HOP_NT, 4, 1>, hop_kernel<S, SL, HOP_NT, 5, 1>,
                                      hop_kernel<S, SL, HOP_NT, 6, 1>, hop_kernel<S, SL, HOP_NT, 7, 1>,
                                      hop_staged_kernel<S, SL, HOP_NT, 4>, hop_staged_kernel<S, SL, HOP_NT, 6>};
-        // shared-endpoint links (whole lattice): register caps 2, 3, 4, 5
-        // CTAs/SM, general and branch-free forms
+        // shared-endpoint links (whole lattice): register caps 2-8 CTAs/SM,
+        // general and branch-free forms, flagged or unconditional U1 reads
         static const KFn v32li[] = {hop_kernel<S, SL, HOP_NT, 2, 0, 1>, hop_kernel<S, SL, HOP_NT, 4, 0, 1>,
                                     hop_kernel<S, SL, HOP_NT, 2, 1, 1>, hop_kernel<S, SL, HOP_NT, 3, 1, 1>,
-                                    hop_kernel<S, SL, HOP_NT, 4, 1, 1>, hop_kernel<S, SL, HOP_NT, 5, 1, 1>};
+                                    hop_kernel<S, SL, HOP_NT, 4, 1, 1>, hop_kernel<S, SL, HOP_NT, 5, 1, 1>,
+                                    hop_kernel<S, SL, HOP_NT, 6, 0, 1>, hop_kernel<S, SL, HOP_NT, 8, 0, 1>,
+                                    hop_kernel<S, SL, HOP_NT, 6, 1, 1>, hop_kernel<S, SL, HOP_NT, 4, 0, 2>,
+                                    hop_kernel<S, SL, HOP_NT, 6, 0, 2>, hop_kernel<S, SL, HOP_NT, 4, 1, 2>,
+                                    hop_kernel<S, SL, HOP_NT, 6, 1, 2>};
         if (shared_links && !all) fail(PSMS_EINVAL, "hop_launch: shared-endpoint links on whole-lattice hops only");
         vars = shared_links ? v32li : (all ? v32all : v32);
-        nvar = shared_links ? 6 : (all ? (staged ? 10 : 8) : 4);
+        nvar = shared_links ? 13 : (all ? (staged ? 10 : 8) : 4);
     } else {
         static const KFn v64[] = {hop_kernel<S, SL, HOP_NT, 2, 0>};
         vars = v64;
         nvar = 1;
     }
     int &choice = c->hop_variant[h.prec][h.p < 0 ? 1 : 0][all ? 1 : 0][shared_links ? 1 : 0];
-    if (choice < 0 && c->autotune && nvar > 1 && slot < 0 && c->forced_hop_variant < 0) {
+    // (launches with a fused reduction are not used for tuning: they advance
+    // the solver's scalars)
+    if (choice < 0 && c->autotune && nvar > 1 && slot < 0 && c->forced_hop_variant < 0 && !a.dot) {
         cudaEvent_t e0, e1;
         cuda_check(cudaEventCreate(&e0), "tune event");
         cuda_check(cudaEventCreate(&e1), "tune event");
@@ -527,6 +594,8 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
     }
     int v = (choice >= 0 && choice < nvar) ? choice : (f32 ? 1 : 0);
     if (c->forced_hop_variant >= 0) v = c->forced_hop_variant % nvar;
+    // the staged kernels (v32all entries 8, 9) carry no fused reduction
+    if (a.dot && !shared_links && all && v >= 8) v = 6;
     vars[v]<<<grid, HOP_NT, 0, c->stream>>>(a);
     PSMS_LAUNCH_CHECK("hop_kernel");
     if (slot >= 0) prof_end(c, slot, bytes);

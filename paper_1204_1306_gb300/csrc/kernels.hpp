@@ -29,6 +29,21 @@ struct LinkInterp {
     const unsigned char *flag = nullptr;        // device, per link mu * V + s
 };
 
+struct BCS;
+// A BiCGStab reduction fused into a single-parity hop (FP32 storage):
+// dot = 1 sums conj(x) out (x = the vector `x`), dot = 2 sums conj(out) y and
+// |out|^2; per-CTA partials go to re/im/aa (n_cta per system) and the last
+// CTA of each system applies the scalar `stage` to st (counters cnt).
+struct HopDot {
+    int dot = 0;
+    View<void> x;
+    BCS *st = nullptr;
+    double *re = nullptr, *im = nullptr, *aa = nullptr;
+    unsigned int *cnt = nullptr;
+    int stage = 0, maxit = 0;
+    int *flags = nullptr;
+};
+
 // out = a*y + a2*y2 + b*H(in), H the hopping term of Eq. (Dw) (sum over the
 // 8 neighbours of U (1 -/+ gamma) psi), restricted by `mode`, for output
 // parity p (-1: both) on the blocks of rank [rank_lo, rank_lo + n_ranks).
@@ -52,6 +67,8 @@ struct HopCall {
     const int *rank_active = nullptr;
     // optional shared-endpoint FP32 links (replace U / U_bs; FP32 links only)
     LinkInterp li;
+    // optional fused BiCGStab reduction of the output
+    HopDot dot;
 };
 // returns the number of CTAs per system (for the partial sums)
 int hop_launch(psms_ctx *c, const HopCall &h);

@@ -15,6 +15,7 @@
 //    own gauge field) batched into every launch, BiCGStab (default) or CGNR
 //    inner iterations; per-system scalars live on the device; the host only
 //    polls convergence flags every few iterations.
+#include "bicgstab.cuh"
 #include "block_solve.cuh"
 #include "kernels.hpp"
 #include "solver.hpp"
@@ -550,20 +551,6 @@ static void inner_cg_full(psms_ctx *c, int n_sys, const void *Uin, long long U_b
 // restarts from the true residual.  Reductions: per-CTA partials in FP64,
 // finished in a fixed order (deterministic).
 // ---------------------------------------------------------------------------
-struct BCS {
-    double2 rho, alpha, omega, beta;
-    double rr, target;
-    int active, iters;
-};
-
-__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
-    const double d = b.x * b.x + b.y * b.y;
-    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
-}
-__device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
 __global__ void bcg_init_kernel(BCS *st, const double *bb, int n, double delta, const int *act, int *flags) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -654,10 +641,6 @@ __device__ double finish_sum(const double *p, int k, int m, double *sh) {
     return t;
 }
 
-// stage: 0 alpha = rho / <rh, v>; 1 omega = <t, s> / <t, t>;
-//        2 rho_new = <rh, r>, rr = |r|^2, beta, convergence
-__device__ void bcg_stage(BCS *st, int k, double re, double im, double aa, int stage, int maxit, int *flags);
-
 template <int NT>
 __global__ void __launch_bounds__(NT) bcg_scalar_kernel(BCS *st, const double *p_re, const double *p_im,
                                                         const double *p_aa, int m, int stage, int maxit, int *flags) {
@@ -671,32 +654,6 @@ __global__ void __launch_bounds__(NT) bcg_scalar_kernel(BCS *st, const double *p
     bcg_stage(st, k, re, im, aa, stage, maxit, flags);
 }
 
-__device__ void bcg_stage(BCS *st, int k, double re, double im, double aa, int stage, int maxit, int *flags) {
-    BCS s = st[k];
-    const double2 d = make_double2(re, im);
-    if (stage == 0) {
-        if (!(re * re + im * im > 0.0)) {
-            s.active = 0;  // breakdown: <rh, v> = 0
-        } else {
-            s.alpha = cdiv(s.rho, d);
-        }
-    } else if (stage == 1) {
-        s.omega = aa > 0.0 ? make_double2(re / aa, im / aa) : make_double2(0.0, 0.0);
-    } else {
-        // the partials are sum conj(r) rh = conj(<rh, r>) and |r|^2 of the
-        // new residual
-        const double2 dr = make_double2(re, -im);
-        s.iters += 1;
-        s.rr = aa;
-        const bool stalled = !(s.omega.x * s.omega.x + s.omega.y * s.omega.y > 0.0) ||
-                             !(re * re + im * im > 0.0);
-        if (!stalled) s.beta = cmul2(cdiv(dr, s.rho), cdiv(s.alpha, s.omega));
-        s.rho = dr;
-        if (aa <= s.target || s.iters >= maxit || stalled || !(aa == aa)) s.active = 0;
-    }
-    st[k] = s;
-    flags[k] = s.active;
-}
 
 // mode 0: s = r - alpha v
 // mode 1: x += alpha p + omega s, r = s - omega t
@@ -732,73 +689,6 @@ __global__ void __launch_bounds__(NT) bcg_axpy_kernel(const BCS *st, int mode, V
     }
 }
 
-// Writes this CTA's partials of system k; the last CTA of the system to
-// finish (a counter per system, no waiting) sums all partials in a fixed
-// order and applies the scalar stage, so the result does not depend on
-// which CTA finishes last.
-template <int NT>
-__device__ __forceinline__ void bcg_partials_and_stage(BCS *st, double re, double im, double aa, double *p_re,
-                                                       double *p_im, double *p_aa, unsigned int *counters, int stage,
-                                                       int maxit, int *flags, double (*sh)[NT / 32], int k) {
-    const long long slot = (long long)k * gridDim.x + blockIdx.x;
-    __shared__ int last;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        re += __shfl_xor_sync(0xffffffffu, re, o);
-        im += __shfl_xor_sync(0xffffffffu, im, o);
-        aa += __shfl_xor_sync(0xffffffffu, aa, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        sh[0][threadIdx.x >> 5] = re;
-        sh[1][threadIdx.x >> 5] = im;
-        sh[2][threadIdx.x >> 5] = aa;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t0 = 0, t1 = 0, t2 = 0;
-        for (int w = 0; w < NT / 32; ++w) {
-            t0 += sh[0][w];
-            t1 += sh[1][w];
-            t2 += sh[2][w];
-        }
-        p_re[slot] = t0;
-        p_im[slot] = t1;
-        p_aa[slot] = t2;
-        __threadfence();
-        last = atomicAdd(&counters[k], 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // the other CTAs' partials, read past L1 (written by other SMs)
-    const int m = gridDim.x;
-    double v[3] = {0, 0, 0};
-    for (int i = threadIdx.x; i < m; i += NT) {
-        const long long q = (long long)k * m + i;
-        v[0] += __ldcg(p_re + q);
-        v[1] += __ldcg(p_im + q);
-        v[2] += __ldcg(p_aa + q);
-    }
-    double tot[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double x = v[a];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) sh[a][threadIdx.x >> 5] = x;
-        __syncthreads();
-        double t = 0;
-        for (int w = 0; w < NT / 32; ++w) t += sh[a][w];
-        tot[a] = t;
-    }
-    const double r0 = tot[0], r1 = tot[1], r2 = tot[2];
-    if (threadIdx.x == 0) {
-        counters[k] = 0;
-        bcg_stage(st, k, r0, r1, r2, stage, maxit, flags);
-    }
-}
-
 // <a, b> partials (sum conj(a) b, and |a|^2) and the scalar stage
 template <class S, int NT>
 __global__ void __launch_bounds__(NT) bcg_dot_stage_kernel(BCS *st, View<typename S::elem> a,
@@ -826,7 +716,8 @@ __global__ void __launch_bounds__(NT) bcg_dot_stage_kernel(BCS *st, View<typenam
         im = (double)tim;
         aa = (double)taa;
     }
-    bcg_partials_and_stage<NT>(st, re, im, aa, p_re, p_im, p_aa, counters, stage, maxit, flags, sh, k);
+    bcg_partials_and_stage<NT>(st, re, im, aa, p_re, p_im, p_aa, counters, stage, maxit, flags, sh, k,
+                               (int)blockIdx.x, (int)gridDim.x);
 }
 
 // x += alpha p + omega s, r = s - omega t, then the partials of
@@ -871,7 +762,8 @@ __global__ void __launch_bounds__(NT) bcg_update_stage_kernel(BCS *st, View<type
         im = (double)tim;
         aa = (double)taa;
     }
-    bcg_partials_and_stage<NT>(st, re, im, aa, p_re, p_im, p_aa, counters, 2, maxit, flags, sh, k);
+    bcg_partials_and_stage<NT>(st, re, im, aa, p_re, p_im, p_aa, counters, 2, maxit, flags, sh, k,
+                               (int)blockIdx.x, (int)gridDim.x);
 }
 
 __global__ void iters_bcg_kernel(const BCS *st, int *out, int n) {
@@ -944,8 +836,20 @@ static void inner_bicgstab_full(psms_ctx *c, int n_sys, const void *Uin, long lo
     // leaves them at zero)
     unsigned int *cnt = (unsigned int *)scratch(c, "fs_bcnt", sizeof(unsigned int) * n_sys);
     cuda_check(cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * n_sys, c->stream), "bcg counters");
-    // w = Dhat u = A u + c4 H_o(H_e u)
-    auto apply_dhat = [&](View<void> u, View<void> w) {
+    // FP32 storage: the dot products of alpha and omega are taken in the
+    // epilogue of the second half hop of Dhat (partials per hop CTA, the
+    // last CTA of a system applies the stage), saving two passes over two
+    // vectors per iteration
+    const bool fuse = prec == P32;
+    double *f_re = nullptr, *f_im = nullptr, *f_aa = nullptr;
+    if (fuse) {
+        f_re = (double *)scratch(c, "fs_fre", sizeof(double) * (size_t)nct * n_sys);
+        f_im = (double *)scratch(c, "fs_fim", sizeof(double) * (size_t)nct * n_sys);
+        f_aa = (double *)scratch(c, "fs_faa", sizeof(double) * (size_t)nct * n_sys);
+    }
+    // w = Dhat u = A u + c4 H_o(H_e u); dot 1: stage 0 on <x, w>; dot 2:
+    // stage 1 on <w, u>, |w|^2
+    auto apply_dhat = [&](View<void> u, View<void> w, int dot, View<void> x, int stage) {
         h.dag = 0;
         h.p = 0;
         h.in = u;
@@ -954,6 +858,7 @@ static void inner_bicgstab_full(psms_ctx *c, int n_sys, const void *Uin, long lo
         h.a = 0;
         h.b = 1.0;
         h.partial = nullptr;
+        h.dot = HopDot{};
         hop_launch(c, h);
         h.p = 1;
         h.in = te;
@@ -961,7 +866,20 @@ static void inner_bicgstab_full(psms_ctx *c, int n_sys, const void *Uin, long lo
         h.y = u;
         h.a = A;
         h.b = c4;
+        if (fuse && dot) {
+            h.dot.dot = dot;
+            h.dot.x = x;
+            h.dot.st = st;
+            h.dot.re = f_re;
+            h.dot.im = f_im;
+            h.dot.aa = f_aa;
+            h.dot.cnt = cnt;
+            h.dot.stage = stage;
+            h.dot.maxit = maxit;
+            h.dot.flags = flags;
+        }
         hop_launch(c, h);
+        h.dot = HopDot{};
     };
     int it = 0;
     int chunk = 8;
@@ -978,19 +896,23 @@ static void inner_bicgstab_full(psms_ctx *c, int n_sys, const void *Uin, long lo
         h.sys_map = map;
         h.n_map = n_act;
         for (int i = 0; i < chunk && it < maxit; ++i, ++it) {
-            apply_dhat(pp, vv);
             // alpha = rho / <rh, v>
-            bcg_dot_stage_kernel<SV, NT><<<gridm, NT, 0, c->stream>>>(st, tv(rh), tv(vv), Vh, n, q_re, q_im, q_aa,
-                                                                      cnt, 0, maxit, flags, map, rank_active, vsh);
-            PSMS_LAUNCH_CHECK("bcg_alpha");
+            apply_dhat(pp, vv, 1, rh, 0);
+            if (!fuse) {
+                bcg_dot_stage_kernel<SV, NT><<<gridm, NT, 0, c->stream>>>(st, tv(rh), tv(vv), Vh, n, q_re, q_im, q_aa,
+                                                                          cnt, 0, maxit, flags, map, rank_active, vsh);
+                PSMS_LAUNCH_CHECK("bcg_alpha");
+            }
             bcg_axpy_kernel<SV, NT><<<gridm, NT, 0, c->stream>>>(st, 0, tv(e), tv(pp), tv(r), tv(ss), tv(vv),
                                                                  tv(tt), Vh, n, map, rank_active, vsh);
             PSMS_LAUNCH_CHECK("bcg_s");
-            apply_dhat(ss, tt);
             // omega = <t, s> / <t, t>
-            bcg_dot_stage_kernel<SV, NT><<<gridm, NT, 0, c->stream>>>(st, tv(tt), tv(ss), Vh, n, q_re, q_im, q_aa,
-                                                                      cnt, 1, maxit, flags, map, rank_active, vsh);
-            PSMS_LAUNCH_CHECK("bcg_omega");
+            apply_dhat(ss, tt, 2, View<void>(), 1);
+            if (!fuse) {
+                bcg_dot_stage_kernel<SV, NT><<<gridm, NT, 0, c->stream>>>(st, tv(tt), tv(ss), Vh, n, q_re, q_im, q_aa,
+                                                                          cnt, 1, maxit, flags, map, rank_active, vsh);
+                PSMS_LAUNCH_CHECK("bcg_omega");
+            }
             // x, r updates with <rh, r>, |r|^2 and beta / convergence
             bcg_update_stage_kernel<SV, NT><<<gridm, NT, 0, c->stream>>>(st, tv(e), tv(pp), tv(r), tv(ss), tv(tt),
                                                                          tv(rh), Vh, n, q_re, q_im, q_aa, cnt,

@@ -46,12 +46,14 @@ def test_sub_level_parity(mode, inner):
     assert np.all(np.abs(got) > 1e-6)   # every outer block changed
 
 
-@pytest.mark.parametrize("inner", [ps.PREC_F32])
-def test_outer_global_level_parity(inner):
+@pytest.mark.parametrize("inner,shared", [(ps.PREC_F32, 1), (ps.PREC_F32, 0)])
+def test_outer_global_level_parity(inner, shared):
     """Global Schur complement of the outer decomposition = the oracle's
-    global level with the outer blocks as blocks."""
+    global level with the outer blocks as blocks (FP32 inner iterations on
+    shared-endpoint or materialised FP32 links)."""
     nest = recursive.Nested(DIMS, OUTER, INNER)
     ctx, U, Up = _pair(DIMS, OUTER, INNER, KAPPA, SEED + 12)
+    ps.psms_shared_links(ctx, shared)
     N = 2
     got = ps.psms_logdet_ratio(ctx, ps.LEVEL_OUTER_GLOBAL, 0, 1, N, ps.EST_INTERP, SEED, 4, 1e-13, inner)
     ref = estimator.global_level(U, Up, nest.outer, KAPPA, N, SEED, 4, tol=1e-13)
