@@ -483,11 +483,12 @@ psms_status psms_max_chunk(psms_ctx *ctx, int n);
 /* Force the Wilson-hop kernel variant (register cap and, for the whole
  * lattice, the branch-free specialisation, and on blocks of 2 x 128 sites
  * (4^4) the variant that stages each block's input of the other parity in
- * shared memory; 10 variants for FP32 links in the whole-lattice mode on
- * such blocks, 8 on others, 4 otherwise, used modulo their count) instead
- * of the autotuned one; -1 returns to autotuning.  All variants compute the
- * same operator.  *n_variants (may be NULL) receives 10.  PSMS_EINVAL
- * outside -1..9. */
+ * shared memory; for FP32 links in the whole-lattice mode 10 variants on
+ * such blocks, 8 on others, 13 with shared-endpoint links, 4 otherwise; for
+ * FP64 links 4 in the whole-lattice mode, 1 otherwise; used modulo their
+ * count) instead of the autotuned one; -1 returns to autotuning.  All
+ * variants compute the same operator.  *n_variants (may be NULL) receives
+ * 13.  PSMS_EINVAL outside -1..12. */
 psms_status psms_hop_variant(psms_ctx *ctx, int variant, int *n_variants);
 
 /* ---- checkpoint / resume ----------------------------------------------------

@@ -516,12 +516,13 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
     int slot = -1;
     if (c->prof && h.mode == HOP_ALL && (c->prof_prec < 0 || c->prof_prec == h.prec)) {
         // algorithmic bytes per output site of an active system: in + out
-        // (+ y, y2) spinors and 4 links (both parities) or 8 (one parity);
-        // with shared-endpoint links the two endpoint fields are read once
-        // per launch, i.e. 2/nsys of a link field per system; the device
-        // counts the output sites of the systems still active
+        // (+ y, y2, + the fused reduction's vector) spinors and 4 links
+        // (both parities) or 8 (one parity) of that system's field -- also
+        // with shared-endpoint links, whose HBM traffic is lower (the
+        // systems share the endpoint links through L2); the device counts
+        // the output sites of the systems still active
         const double sp = 12.0 * sizeof(E), lk = 9.0 * sizeof(typename SL::elem);
-        const double links = 4 * lk * (h.p < 0 ? 1 : 2) * (shared_links ? 2.0 / nsys : 1.0);
+        const double links = 4 * lk * (h.p < 0 ? 1 : 2);
         bytes = 2 * sp + (h.y.p ? sp : 0) + (h.y2.p ? sp : 0) + (a.dot == 1 ? sp : 0) + links;
         slot = prof_begin(c);
         a.prof_sites = prof_counter(c, slot);
@@ -561,9 +562,13 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
         vars = shared_links ? v32li : (all ? v32all : v32);
         nvar = shared_links ? 13 : (all ? (staged ? 10 : 8) : 4);
     } else {
+        // FP64 (ALU bound): the general form, and for the whole lattice the
+        // branch-free form, register caps 3 and 4 CTAs/SM
         static const KFn v64[] = {hop_kernel<S, SL, HOP_NT, 2, 0>};
-        vars = v64;
-        nvar = 1;
+        static const KFn v64all[] = {hop_kernel<S, SL, HOP_NT, 2, 0>, hop_kernel<S, SL, HOP_NT, 2, 1>,
+                                     hop_kernel<S, SL, HOP_NT, 4, 0>, hop_kernel<S, SL, HOP_NT, 3, 1>};
+        vars = all ? v64all : v64;
+        nvar = all ? 4 : 1;
     }
     int &choice = c->hop_variant[h.prec][h.p < 0 ? 1 : 0][all ? 1 : 0][shared_links ? 1 : 0];
     // (launches with a fused reduction are not used for tuning: they advance

@@ -60,6 +60,21 @@ def test_outer_global_level_parity(inner, shared):
     assert np.abs(got - ref).max() < 1e-8
 
 
+def test_outer_global_level_every_shared_link_hop_variant():
+    """Every form of the shared-endpoint-link hop (register caps, branch-free
+    or general, flagged or unconditional endpoint reads), forced one by one,
+    gives the oracle's global level of the outer decomposition."""
+    nest = recursive.Nested(DIMS, OUTER, INNER)
+    ctx, U, Up = _pair(DIMS, OUTER, INNER, KAPPA, SEED + 15)
+    ref = estimator.global_level(U, Up, nest.outer, KAPPA, 2, SEED, 8, tol=1e-12)
+    n = ps.psms_hop_variant(ctx, 0)
+    for v in range(n):
+        ps.psms_hop_variant(ctx, v)
+        got = ps.psms_logdet_ratio(ctx, ps.LEVEL_OUTER_GLOBAL, 0, 1, 2, ps.EST_INTERP, SEED, 8, 1e-12, ps.PREC_F32)
+        assert np.abs(got - ref).max() < 1e-8, v
+    ps.psms_hop_variant(ctx, -1)
+
+
 def test_global_level_ignores_outer_blocks():
     """PSMS_LEVEL_GLOBAL is the Schur complement of the context's blocks
     whether or not outer blocks are set."""
