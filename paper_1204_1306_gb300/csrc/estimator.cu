@@ -151,7 +151,12 @@ int chunk_size(psms_ctx *c, int N, double bytes_per_site) {
     double budget = std::min(64e9, 0.45 * (double)tot);
     int k = (int)(budget / (bytes_per_site * (double)c->g.V));
     if (c->max_chunk > 0) k = std::min(k, c->max_chunk);
-    return std::max(1, std::min(N, k));
+    k = std::max(1, std::min(N, k));
+    // as many chunks as the budget needs, of equal size (N = 12 with room
+    // for 11 runs as 6 + 6, not 11 + 1: a chunk costs about the same time
+    // whatever its number of systems while the solves are latency-bound)
+    const int n_chunks = (N + k - 1) / k;
+    return (N + n_chunks - 1) / n_chunks;
 }
 
 static void check_status(psms_ctx *c, const int *d_status, int n, const char *what) {

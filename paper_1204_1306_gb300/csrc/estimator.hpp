@@ -7,7 +7,8 @@ namespace psms {
 
 // number of interpolation steps batched per launch, from a per-system
 // device-memory estimate (bytes per lattice site), a 64 GB budget and the
-// context's cap (psms_max_chunk)
+// context's cap (psms_max_chunk), balanced so that the chunks of N have
+// equal sizes (the last one at most one smaller)
 int chunk_size(psms_ctx *c, int N, double bytes_per_site);
 // noise fields xi_i (i = 0..n-1) for `level`, FP64 full layout, optional P projection
 void noise(psms_ctx *c, double2 *out, int n, uint64_t seed, uint64_t counter, int level, int proj, int i0);
