@@ -315,7 +315,28 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-template <class S, class SL, int NT, int MINB>
+// TMA = 1: the block's input rows (one contiguous 16-byte unit row of NT
+// sites per spinor unit) are moved by the bulk-copy engine
+// (cp.async.bulk, completion counted in bytes on an mbarrier) instead of
+// per-thread 16-byte copies.  The wait is bounded; if it ran out, the
+// neighbours are read from global memory instead (same values), after a
+// second bounded wait for the copies in flight.
+__device__ __forceinline__ bool bulk_wait(uint32_t bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred q;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, q;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <class S, class SL, int NT, int MINB, int TMA = 0>
 __global__ void __launch_bounds__(NT, MINB) hop_staged_kernel(const HopArgs<typename S::elem> a) {
     using R = typename SL::R;
     using E = typename S::elem;
@@ -352,13 +373,43 @@ __global__ void __launch_bounds__(NT, MINB) hop_staged_kernel(const HopArgs<type
     const E *in = a.in.p + k * a.in.bs;
     // stage the block's input sites of the other parity (unit u of site s at
     // 16-byte unit u * cs + s - off)
+    bool staged_ok = true;
     {
         const long long s0 = (long long)(1 - p) * g.Vh + (long long)r * g.Vbh - a.in.off;
         const int4 *src = reinterpret_cast<const int4 *>(in);
+        if constexpr (TMA) {
+            __shared__ __align__(8) uint64_t bar;
+            const uint32_t sbar = (uint32_t)__cvta_generic_to_shared(&bar);
+            if (threadIdx.x == 0) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sbar) : "memory");
+                asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sbar),
+                             "r"((uint32_t)(NU * NT * 16))
+                             : "memory");
 #pragma unroll
-        for (int u = 0; u < NU; ++u) cp_async16(&stage[u * NT + threadIdx.x], src + u * a.in.cs + s0 + threadIdx.x);
-        cp_async_wait_all();
-        __syncthreads();
+                for (int u = 0; u < NU; ++u) {
+                    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&stage[u * NT]);
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                            dst),
+                        "l"(src + u * a.in.cs + s0), "r"((uint32_t)(NT * 16)), "r"(sbar)
+                        : "memory");
+                }
+            }
+            staged_ok = bulk_wait(sbar, 0);
+            if (!staged_ok) bulk_wait(sbar, 0);
+            staged_ok = __syncthreads_and(staged_ok);
+            if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(sbar) : "memory");
+        } else {
+#pragma unroll
+            for (int u = 0; u < NU; ++u)
+                cp_async16(&stage[u * NT + threadIdx.x], src + u * a.in.cs + s0 + threadIdx.x);
+            cp_async_wait_all();
+            __syncthreads();
+        }
     }
     const int j = threadIdx.x;
     int y[4];
@@ -382,7 +433,7 @@ __global__ void __launch_bounds__(NT, MINB) hop_staged_kernel(const HopArgs<type
         snb[d] = (int)sn;
         if (bs < 0) neg |= 1u << d;
         const int yn = y[mu] + sgn;
-        if ((unsigned)yn < (unsigned)g.l[mu]) {
+        if (staged_ok && (unsigned)yn < (unsigned)g.l[mu]) {
             inside |= 1u << d;
             idx_[d] = snb[d] - base_opp;
         } else {
@@ -548,7 +599,8 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
                                      hop_kernel<S, SL, HOP_NT, 7, 0>, hop_kernel<S, SL, HOP_NT, 8, 0>,
                                      hop_kernel<S, SL, HOP_NT, 4, 1>, hop_kernel<S, SL, HOP_NT, 5, 1>,
                                      hop_kernel<S, SL, HOP_NT, 6, 1>, hop_kernel<S, SL, HOP_NT, 7, 1>,
-                                     hop_staged_kernel<S, SL, HOP_NT, 4>, hop_staged_kernel<S, SL, HOP_NT, 6>};
+                                     hop_staged_kernel<S, SL, HOP_NT, 4>, hop_staged_kernel<S, SL, HOP_NT, 6>,
+                                     hop_staged_kernel<S, SL, HOP_NT, 4, 1>, hop_staged_kernel<S, SL, HOP_NT, 6, 1>};
         // shared-endpoint links (whole lattice): register caps 2-8 CTAs/SM,
         // general and branch-free forms, flagged or unconditional U1 reads
         static const KFn v32li[] = {hop_kernel<S, SL, HOP_NT, 2, 0, 1>, hop_kernel<S, SL, HOP_NT, 4, 0, 1>,
@@ -560,7 +612,7 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
                                     hop_kernel<S, SL, HOP_NT, 6, 1, 2>};
         if (shared_links && !all) fail(PSMS_EINVAL, "hop_launch: shared-endpoint links on whole-lattice hops only");
         vars = shared_links ? v32li : (all ? v32all : v32);
-        nvar = shared_links ? 13 : (all ? (staged ? 10 : 8) : 4);
+        nvar = shared_links ? 13 : (all ? (staged ? 12 : 8) : 4);
     } else {
         // FP64 (ALU bound): the general form, and for the whole lattice the
         // branch-free form, register caps 3 and 4 CTAs/SM
@@ -599,7 +651,7 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
     }
     int v = (choice >= 0 && choice < nvar) ? choice : (f32 ? 1 : 0);
     if (c->forced_hop_variant >= 0) v = c->forced_hop_variant % nvar;
-    // the staged kernels (v32all entries 8, 9) carry no fused reduction
+    // the staged kernels (v32all entries 8 to 11) carry no fused reduction
     if (a.dot && !shared_links && all && v >= 8) v = 6;
     vars[v]<<<grid, HOP_NT, 0, c->stream>>>(a);
     PSMS_LAUNCH_CHECK("hop_kernel");
