@@ -160,7 +160,9 @@ def allsum(ws, v):
 # per-site norm sums), so no ratio is applied.
 # DRAM bytes (ncu dram__bytes_read.sum + write.sum) / algorithmic bytes of
 # captured launches of the current kernels (None: no capture of this build)
-TRAFFIC_RATIO = {"block_solve_cluster_kernel": None,
+TRAFFIC_RATIO = {# 16^4 block level, 256 blocks x 12 systems: 12.48 GB of DRAM traffic
+                 # for 118.9 GB of algorithmic bytes in one launch
+                 "block_solve_cluster_kernel": 0.105,
                  # shared-endpoint-link FP32 hop, 32^3x64 global level, 8 systems:
                  # 3.75 GB of DRAM traffic for 6.4-7.3 GB of algorithmic bytes
                  "hop_kernel": 0.55}
