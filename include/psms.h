@@ -481,15 +481,15 @@ psms_status psms_block_krylov(psms_ctx *ctx, int kind);
 psms_status psms_max_chunk(psms_ctx *ctx, int n);
 
 /* Force the Wilson-hop kernel variant (register cap and, for the whole
- * lattice, the branch-free specialisation, and on blocks of 2 x 128 sites
- * (4^4) the variants that stage each block's input of the other parity in
- * shared memory by per-thread or bulk (TMA) copies; for FP32 links in the
- * whole-lattice mode 12 variants on such blocks, 8 on others, 13 with
- * shared-endpoint links, 4 otherwise; for
+ * lattice, the branch-free specialisation, the form with two threads per
+ * output site, and on blocks of 2 x 128 sites (4^4) the variants that stage
+ * each block's input of the other parity in shared memory by per-thread or
+ * bulk (TMA) copies; for FP32 links in the whole-lattice mode 14 variants on
+ * such blocks, 10 on others, 15 with shared-endpoint links, 4 otherwise; for
  * FP64 links 4 in the whole-lattice mode, 1 otherwise; used modulo their
  * count) instead of the autotuned one; -1 returns to autotuning.  All
  * variants compute the same operator.  *n_variants (may be NULL) receives
- * 13.  PSMS_EINVAL outside -1..12. */
+ * 15.  PSMS_EINVAL outside -1..14. */
 psms_status psms_hop_variant(psms_ctx *ctx, int variant, int *n_variants);
 
 /* ---- checkpoint / resume ----------------------------------------------------

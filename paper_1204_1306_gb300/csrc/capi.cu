@@ -1214,9 +1214,9 @@ psms_status psms_block_krylov(psms_ctx *ctx, int kind) {
 
 psms_status psms_hop_variant(psms_ctx *ctx, int variant, int *n_variants) {
     PSMS_TRY(ctx)
-    if (variant < -1 || variant > 12) fail(PSMS_EINVAL, "hop variant must be -1 or 0..12");
+    if (variant < -1 || variant > 14) fail(PSMS_EINVAL, "hop variant must be -1 or 0..14");
     ctx->forced_hop_variant = variant;
-    if (n_variants) *n_variants = 13;
+    if (n_variants) *n_variants = 15;
     PSMS_CATCH(ctx)
 }
 

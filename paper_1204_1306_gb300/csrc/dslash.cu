@@ -101,16 +101,56 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return t;  // valid in thread 0
 }
 
+// Directions [D0, D1) of the branch-free whole-lattice hop of one output
+// site (d = 2 mu + (0 forward, 1 backward)), accumulated into acc.
+template <int D0, int D1, class S, class SL, int LI, class E>
+__device__ __forceinline__ void hop_dirs(const HopArgs<E> &a, const Geom &g, const BlockInfo &bi, int r, int p,
+                                         const int y[4], int ll, long long s, int k, const E *in,
+                                         const typename SL::elem *U, typename SL::R sg,
+                                         Spinor<typename SL::R> &acc) {
+    using R = typename SL::R;
+    long long snb[8];
+    int bsg[8];
+#pragma unroll
+    for (int d = D0; d < D1; ++d) neighbour(g, bi, r, p, y, ll, d >> 1, (d & 1) ? -1 : 1, HOP_ALL, snb[d], bsg[d]);
+#pragma unroll
+    for (int d = D0; d < D1; ++d) {
+        const int mu = d >> 1;
+        const bool fwd = (d & 1) == 0;
+        Spinor<R> v = load_spinor_ro<S>(in, a.in.cs, snb[d] - a.in.off);
+        const R tt = fwd ? -sg : sg;
+        Half<R> h = project(mu, tt, v);
+        if (mu == 0) {
+            // antiperiodic time boundary: sign on the hop
+            const R bsr = R(bsg[d]);
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) h.c[q][c] = bsr * h.c[q][c];
+        }
+        SU3<R> u = hop_link<SL, LI>(a, U, k, mu, fwd ? s : snb[d]);
+        reconstruct_add(mu, tt, fwd ? su3_mul(u, h) : su3_dag_mul(u, h), acc);
+    }
+}
+
 // ALL = 1: specialised for HOP_ALL (every neighbour exists): the eight
 // neighbour indices are computed first and the eight hops run as one
 // branch-free sequence, so the compiler can issue later directions' loads
 // before earlier directions' arithmetic (more loads in flight per thread).
 // LI = 1: links from the shared endpoints (FP32 links only).
-template <class S, class SL, int NT, int MINB, int ALL, int LI = 0>
+// SPLIT = 1 (whole lattice, FP32 arithmetic): two threads per output site in
+// a CTA of NT = 256 (128 sites), the first half of the CTA summing the
+// directions mu = 0, 1 and the second mu = 2, 3 (halves of whole warps, so
+// no divergence); the second half's partial spinors join the first's
+// through shared memory and the first half finishes the site -- half the
+// per-thread state, twice the threads in flight.
+template <class S, class SL, int NT, int MINB, int ALL, int LI = 0, int SPLIT = 0>
 __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S::elem> a) {
     using R = typename SL::R;
     using E = typename S::elem;
     using EL = typename SL::elem;
+    static_assert(!SPLIT || (ALL && NT == 256 && sizeof(R) == 4), "split form: whole lattice, 256 threads, FP32");
+    constexpr int SN = SPLIT ? NT / 2 : NT;  // output sites per CTA
     __shared__ double sh[NT / 32];
     int ks, bx;
     hop_cta(a.nsf, ks, bx);
@@ -122,7 +162,8 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
     const Geom &g = a.g;
     const long long per_p = (long long)a.n_ranks * g.Vbh;
     const long long total = (a.p < 0 ? 2 : 1) * per_p;
-    const long long t = (long long)bx * NT + threadIdx.x;
+    const int half = SPLIT ? (int)(threadIdx.x >= SN) : 0;
+    const long long t = (long long)bx * SN + (threadIdx.x - half * SN);
     double nrm = 0.0;
     double d_re = 0.0, d_im = 0.0, d_aa = 0.0;  // fused BiCGStab dot partials
     bool work = t < total;
@@ -167,42 +208,27 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
     }
     if (a.prof_sites) {
         // output sites this warp computes (algorithmic-byte accounting)
-        const unsigned cnt = __popc(__ballot_sync(0xffffffffu, work));
+        const unsigned cnt = __popc(__ballot_sync(0xffffffffu, work && !half));
         if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(a.prof_sites, (unsigned long long)cnt);
     }
+    const long long s = (long long)p * g.Vh + (long long)r * g.Vbh + j;
+    Spinor<R> acc;
+    zero(acc);
     if (work) {
         int y[4];
         const int ll = local_lex(g, p, j, y);
         const BlockInfo &bi = a.binfo[r];
-        const long long s = (long long)p * g.Vh + (long long)r * g.Vbh + j;
         const E *in = a.in.p + k * a.in.bs;
         const EL *U = (const EL *)a.U + k * a.U_bs;
         const R sg = a.dag ? R(-1) : R(1);
-        Spinor<R> acc;
-        zero(acc);
-        if constexpr (ALL) {
-            long long snb[8];
-            int bsg[8];
-#pragma unroll
-            for (int d = 0; d < 8; ++d) neighbour(g, bi, r, p, y, ll, d >> 1, (d & 1) ? -1 : 1, HOP_ALL, snb[d], bsg[d]);
-#pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                const int mu = d >> 1;
-                const bool fwd = (d & 1) == 0;
-                Spinor<R> v = load_spinor_ro<S>(in, a.in.cs, snb[d] - a.in.off);
-                const R tt = fwd ? -sg : sg;
-                Half<R> h = project(mu, tt, v);
-                if (mu == 0) {
-                    // antiperiodic time boundary: sign on the hop
-                    const R bsr = R(bsg[d]);
-#pragma unroll
-                    for (int q = 0; q < 2; ++q)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) h.c[q][c] = bsr * h.c[q][c];
-                }
-                SU3<R> u = hop_link<SL, LI>(a, U, k, mu, fwd ? s : snb[d]);
-                reconstruct_add(mu, tt, fwd ? su3_mul(u, h) : su3_dag_mul(u, h), acc);
-            }
+        if constexpr (SPLIT) {
+            // warp-uniform halves: mu = 0, 1 in the first, mu = 2, 3 in the second
+            if (half)
+                hop_dirs<4, 8, S, SL, LI>(a, g, bi, r, p, y, ll, s, k, in, U, sg, acc);
+            else
+                hop_dirs<0, 4, S, SL, LI>(a, g, bi, r, p, y, ll, s, k, in, U, sg, acc);
+        } else if constexpr (ALL) {
+            hop_dirs<0, 8, S, SL, LI>(a, g, bi, r, p, y, ll, s, k, in, U, sg, acc);
         } else {
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
@@ -236,6 +262,33 @@ __global__ void __launch_bounds__(NT, MINB) hop_kernel(const HopArgs<typename S:
             }
         }
         }
+    }
+    if constexpr (SPLIT) {
+        // join the halves: the second half's partial spinor goes through
+        // shared memory to the first, which finishes the site
+        __shared__ float red[24][SN];
+        if (half && work) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    red[2 * (3 * q + c)][threadIdx.x - SN] = acc.c[q][c].re;
+                    red[2 * (3 * q + c) + 1][threadIdx.x - SN] = acc.c[q][c].im;
+                }
+        }
+        __syncthreads();
+        if (!half && work) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    acc.c[q][c].re += red[2 * (3 * q + c)][threadIdx.x];
+                    acc.c[q][c].im += red[2 * (3 * q + c) + 1][threadIdx.x];
+                }
+        }
+        work = work && !half;
+    }
+    if (work) {
         const R cb = (R)a.b;
         Spinor<R> o;
 #pragma unroll
@@ -591,6 +644,7 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
     // the staged kernel: whole lattice, 128 sites of each parity per block
     const bool staged = all && a.n_ranks == c->g.nblocks && h.rank_lo == 0 && c->g.Vbh == HOP_NT;
     const KFn *vars;
+    const int *thr = nullptr;  // threads per CTA of each variant (null: all HOP_NT)
     int nvar;
     if constexpr (f32) {
         static const KFn v32[] = {hop_kernel<S, SL, HOP_NT, 2, 0>, hop_kernel<S, SL, HOP_NT, 6, 0>,
@@ -599,8 +653,11 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
                                      hop_kernel<S, SL, HOP_NT, 7, 0>, hop_kernel<S, SL, HOP_NT, 8, 0>,
                                      hop_kernel<S, SL, HOP_NT, 4, 1>, hop_kernel<S, SL, HOP_NT, 5, 1>,
                                      hop_kernel<S, SL, HOP_NT, 6, 1>, hop_kernel<S, SL, HOP_NT, 7, 1>,
+                                     hop_kernel<S, SL, 2 * HOP_NT, 3, 1, 0, 1>, hop_kernel<S, SL, 2 * HOP_NT, 4, 1, 0, 1>,
                                      hop_staged_kernel<S, SL, HOP_NT, 4>, hop_staged_kernel<S, SL, HOP_NT, 6>,
                                      hop_staged_kernel<S, SL, HOP_NT, 4, 1>, hop_staged_kernel<S, SL, HOP_NT, 6, 1>};
+        static const int t32all[] = {HOP_NT, HOP_NT, HOP_NT, HOP_NT, HOP_NT, HOP_NT, HOP_NT,
+                                     HOP_NT, 2 * HOP_NT, 2 * HOP_NT, HOP_NT, HOP_NT, HOP_NT, HOP_NT};
         // shared-endpoint links (whole lattice): register caps 2-8 CTAs/SM,
         // general and branch-free forms, flagged or unconditional U1 reads
         static const KFn v32li[] = {hop_kernel<S, SL, HOP_NT, 2, 0, 1>, hop_kernel<S, SL, HOP_NT, 4, 0, 1>,
@@ -609,10 +666,16 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
                                     hop_kernel<S, SL, HOP_NT, 6, 0, 1>, hop_kernel<S, SL, HOP_NT, 8, 0, 1>,
                                     hop_kernel<S, SL, HOP_NT, 6, 1, 1>, hop_kernel<S, SL, HOP_NT, 4, 0, 2>,
                                     hop_kernel<S, SL, HOP_NT, 6, 0, 2>, hop_kernel<S, SL, HOP_NT, 4, 1, 2>,
-                                    hop_kernel<S, SL, HOP_NT, 6, 1, 2>};
+                                    hop_kernel<S, SL, HOP_NT, 6, 1, 2>,
+                                    hop_kernel<S, SL, 2 * HOP_NT, 2, 1, 1, 1>, hop_kernel<S, SL, 2 * HOP_NT, 3, 1, 1, 1>};
+        static const int t32li[] = {HOP_NT, HOP_NT, HOP_NT, HOP_NT, HOP_NT, HOP_NT, HOP_NT, HOP_NT,
+                                    HOP_NT, HOP_NT, HOP_NT, HOP_NT, HOP_NT, 2 * HOP_NT, 2 * HOP_NT};
         if (shared_links && !all) fail(PSMS_EINVAL, "hop_launch: shared-endpoint links on whole-lattice hops only");
         vars = shared_links ? v32li : (all ? v32all : v32);
-        nvar = shared_links ? 13 : (all ? (staged ? 12 : 8) : 4);
+        thr = shared_links ? t32li : (all ? t32all : nullptr);
+        // two-threads-per-site forms: v32all entries 8, 9 and v32li 13, 14;
+        // staged forms: v32all 10 to 13 (blocks of 2 x 128 sites only)
+        nvar = shared_links ? 15 : (all ? (staged ? 14 : 10) : 4);
     } else {
         // FP64 (ALU bound): the general form, and for the whole lattice the
         // branch-free form, register caps 3 and 4 CTAs/SM
@@ -631,10 +694,10 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
         cuda_check(cudaEventCreate(&e1), "tune event");
         float best = 1e30f;
         for (int v = 0; v < nvar; ++v) {
-            vars[v]<<<grid, HOP_NT, 0, c->stream>>>(a);
+            vars[v]<<<grid, thr ? thr[v] : HOP_NT, 0, c->stream>>>(a);
             cuda_check(cudaEventRecord(e0, c->stream), "tune record");
-            vars[v]<<<grid, HOP_NT, 0, c->stream>>>(a);
-            vars[v]<<<grid, HOP_NT, 0, c->stream>>>(a);
+            vars[v]<<<grid, thr ? thr[v] : HOP_NT, 0, c->stream>>>(a);
+            vars[v]<<<grid, thr ? thr[v] : HOP_NT, 0, c->stream>>>(a);
             cuda_check(cudaEventRecord(e1, c->stream), "tune record");
             cuda_check(cudaEventSynchronize(e1), "tune sync");
             launch_counter() += 3;
@@ -651,9 +714,9 @@ static int hop_launch_t(psms_ctx *c, const HopCall &h) {
     }
     int v = (choice >= 0 && choice < nvar) ? choice : (f32 ? 1 : 0);
     if (c->forced_hop_variant >= 0) v = c->forced_hop_variant % nvar;
-    // the staged kernels (v32all entries 8 to 11) carry no fused reduction
-    if (a.dot && !shared_links && all && v >= 8) v = 6;
-    vars[v]<<<grid, HOP_NT, 0, c->stream>>>(a);
+    // the staged kernels (v32all entries 10 to 13) carry no fused reduction
+    if (a.dot && !shared_links && all && v >= 10) v = 6;
+    vars[v]<<<grid, thr ? thr[v] : HOP_NT, 0, c->stream>>>(a);
     PSMS_LAUNCH_CHECK("hop_kernel");
     if (slot >= 0) prof_end(c, slot, bytes);
     return nct;

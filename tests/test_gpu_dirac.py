@@ -124,12 +124,12 @@ def test_dw_every_hop_variant(prec, tol):
         ps.psms_dw_apply(ctx, 0, ps.OP_BLOCKS, nat, out, prec)
         assert rel_err(canonical(ctx, out, prec), ref_blk) < tol, v
     # the single-parity launches of the even-odd whole-lattice solver with
-    # each whole-lattice variant forced (the staged ones: 8, 9 with
-    # per-thread copies, 10, 11 with bulk copies): the FP64 defect
-    # correction reaches its true residual only if the inner operator is
-    # right
+    # each whole-lattice variant forced (two threads per site: 8, 9; staged
+    # with per-thread copies: 10, 11, with bulk copies: 12, 13): the FP64
+    # defect correction reaches its true residual only if the inner
+    # operator is right
     b = native(ctx, seeded.spinor(dims, 25))
-    for v in (5, 8, 9, 10, 11):
+    for v in (5, 8, 9, 10, 11, 12, 13):
         ps.psms_hop_variant(ctx, v)
         x = torch.zeros_like(b)
         info = ps.psms_solve(ctx, 0, ps.OP_FULL, b, x, 1e-11, 4000, ps.PREC_F32)
