@@ -566,95 +566,6 @@ __global__ void bcg_init_kernel(BCS *st, const double *bb, int n, double delta, 
     flags[k] = s.active;
 }
 
-// per-CTA partials of sum conj(a) b (complex) and, if p_aa, sum |a|^2
-template <class S, int NT>
-__global__ void __launch_bounds__(NT) bcg_dot_kernel(const BCS *st, View<typename S::elem> a, View<typename S::elem> b,
-                                                     long long s_lo, long long n, double *p_re, double *p_im,
-                                                     double *p_aa) {
-    using R = typename S::R;
-    __shared__ double sh[3][NT / 32];
-    const int k = blockIdx.y;
-    const long long slot = (long long)k * gridDim.x + blockIdx.x;
-    if (!st[k].active) {
-        if (threadIdx.x == 0) {
-            p_re[slot] = 0;
-            p_im[slot] = 0;
-            if (p_aa) p_aa[slot] = 0;
-        }
-        return;
-    }
-    // a thread's 12 components are summed in the inner precision (GB300's
-    // FP64 rate is 1/64 of FP32), the sums over threads and CTAs in FP64
-    double re = 0, im = 0, aa = 0;
-    const long long i = (long long)blockIdx.x * NT + threadIdx.x;
-    if (i < n) {
-        const long long sx = s_lo + i;
-        R tre = 0, tim = 0, taa = 0;
-        for (int c = 0; c < 12; ++c) {
-            const cpx<R> x = S::ldi(a.p, k * a.bs + S::idx(c, a.cs, sx - a.off));
-            const cpx<R> y = S::ldi(b.p, k * b.bs + S::idx(c, b.cs, sx - b.off));
-            tre += x.re * y.re + x.im * y.im;
-            tim += x.re * y.im - x.im * y.re;
-            taa += x.re * x.re + x.im * x.im;
-        }
-        re = (double)tre;
-        im = (double)tim;
-        aa = (double)taa;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        re += __shfl_xor_sync(0xffffffffu, re, o);
-        im += __shfl_xor_sync(0xffffffffu, im, o);
-        aa += __shfl_xor_sync(0xffffffffu, aa, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        sh[0][threadIdx.x >> 5] = re;
-        sh[1][threadIdx.x >> 5] = im;
-        sh[2][threadIdx.x >> 5] = aa;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t0 = 0, t1 = 0, t2 = 0;
-        for (int w = 0; w < NT / 32; ++w) {
-            t0 += sh[0][w];
-            t1 += sh[1][w];
-            t2 += sh[2][w];
-        }
-        p_re[slot] = t0;
-        p_im[slot] = t1;
-        if (p_aa) p_aa[slot] = t2;
-    }
-}
-
-// fixed-order sum of m per-CTA partials of system k (one warp per array)
-template <int NT>
-__device__ double finish_sum(const double *p, int k, int m, double *sh) {
-    double v = 0;
-    for (int i = threadIdx.x; i < m; i += NT) v += p[(long long)k * m + i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double t = 0;
-    for (int i = 0; i < NT / 32; ++i) t += sh[i];
-    return t;
-}
-
-template <int NT>
-__global__ void __launch_bounds__(NT) bcg_scalar_kernel(BCS *st, const double *p_re, const double *p_im,
-                                                        const double *p_aa, int m, int stage, int maxit, int *flags) {
-    __shared__ double sh[NT / 32];
-    const int k = blockIdx.x;
-    if (!st[k].active) return;
-    const double re = finish_sum<NT>(p_re, k, m, sh);
-    const double im = finish_sum<NT>(p_im, k, m, sh);
-    const double aa = p_aa ? finish_sum<NT>(p_aa, k, m, sh) : 0.0;
-    if (threadIdx.x != 0) return;
-    bcg_stage(st, k, re, im, aa, stage, maxit, flags);
-}
-
-
 // mode 0: s = r - alpha v
 // mode 1: x += alpha p + omega s, r = s - omega t
 // mode 2: p = r + beta (p - omega v)
