@@ -28,11 +28,11 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "tc_layout.hpp"
+
 namespace psms {
 namespace tc {
 
-constexpr int TM = 128;  // tile rows = TMEM lanes
-constexpr int TK = 64;   // K chunk per shared-memory stage
 constexpr int NTHR = 128;
 
 struct Args {
@@ -62,27 +62,6 @@ constexpr int smem_bytes() {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// byte offset of element (r, k) in a K-major no-swizzle tile of TK columns
-__device__ __forceinline__ uint32_t canon_off(int r, int k) {
-    return (uint32_t)((((r >> 3) * (TK / 8) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
-}
-
-// shared-memory matrix descriptor, no swizzle: start address, leading
-// (K-direction core-matrix) byte offset, stride (8-row group) byte offset,
-// the fixed descriptor version 1 at bit 46
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
-}
-
-// instruction descriptor of kind::f16: FP32 accumulator (bit 4), BF16 A
-// (bits 7-9 = 1) and B (bits 10-12 = 1), both K-major, N/8 at bit 17,
-// M/16 at bit 24
-template <int TN>
-__device__ __forceinline__ uint32_t instr_desc() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
@@ -171,8 +150,8 @@ __global__ void __launch_bounds__(NTHR) gemm_kernel(const Args a) {
 #pragma unroll
             for (int j = 0; j < TK / 16; ++j) {
                 // K = 16 per MMA: two core matrices along K (256 bytes)
-                const uint64_t ad = smem_desc(abase + j * 256, 128, (TK / 8) * 128);
-                const uint64_t bd = smem_desc(bbase + j * 256, 128, (TK / 8) * 128);
+                const uint64_t ad = smem_desc(abase + j * 2 * LBO, LBO, SBO);
+                const uint64_t bd = smem_desc(bbase + j * 2 * LBO, LBO, SBO);
                 const uint32_t acc = (c > 0 || j > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
