@@ -153,8 +153,8 @@ int chunk_size(psms_ctx *c, int N, double bytes_per_site) {
     if (c->max_chunk > 0) k = std::min(k, c->max_chunk);
     k = std::max(1, std::min(N, k));
     // as many chunks as the budget needs, of equal size (N = 12 with room
-    // for 11 runs as 6 + 6, not 11 + 1: a chunk costs about the same time
-    // whatever its number of systems while the solves are latency-bound)
+    // for 11 runs as 6 + 6, not 11 + 1, so that no chunk runs a lone system
+    // through a level's fixed per-chunk work)
     const int n_chunks = (N + k - 1) / k;
     return (N + n_chunks - 1) / n_chunks;
 }
