@@ -1204,6 +1204,23 @@ def oracle_step_seconds(workload, comp, full_iters):
     return t
 
 
+def oracle_model_check(steps=2):
+    """The component model of oracle_step_seconds against complete oracle
+    filter steps, both on the 4^4 workload (small enough to run the oracle
+    chain): measured seconds per step, the model's seconds from the same
+    components (whole-lattice iterations counted on the 4^4 lattice
+    itself), and their ratio."""
+    wl = WORKLOADS["4^4"]
+    base = {"dims": list(wl["dims"]), "block": list(wl["block"]), "kappa": wl["kappa"], "eps": wl["eps"],
+            "beta": wl["beta"], "seed": SEED, "tol": wl["tol"]}
+    full = _oracle_run(_FILTER_STEPS, dict(base, n_block=wl["n_block"], n_global=wl["n_global"], steps=steps))
+    comp = _oracle_run(_COMPONENTS, dict(base, n_or=wl["n_or"], n_sample=4, full_dims=list(wl["dims"]), sweep=True))
+    model = oracle_step_seconds("4^4", comp, comp["full_solve_iterations"])
+    return {"workload": "4^4", "measured_s_per_step": round(full["s_per_step"], 3),
+            "model_s_per_step": round(model, 3), "model_over_measured": round(model / full["s_per_step"], 3),
+            "steps": full["steps"]}
+
+
 def cpu_baseline(workload, recs):
     """The oracle on this host, one thread: its filter-step time from measured
     components (oracle_step_seconds; the whole-lattice solve's iteration
@@ -1221,7 +1238,15 @@ def cpu_baseline(workload, recs):
                        f"whole-lattice solve {comp['full_solve_iterations']} CGNR iterations (oracle, 8^4); "
                        f"step time from the levels' solve counts = {step_s:.0f} s; accepted updates per step from "
                        f"the GPU chain ({_accepted(recs)}/{len(recs)}, identical decisions by parity); extrapolated"),
-            "components": comp, "extrapolated_step_s": step_s}
+            "components": comp, "extrapolated_step_s": step_s, "model_check": _model_check_or_error()}
+
+
+def _model_check_or_error():
+    # a calibration beside the baseline: its failure must not cost the line
+    try:
+        return oracle_model_check()
+    except Exception as e:  # noqa: BLE001
+        return {"error": f"{type(e).__name__}: {str(e)[-300:]}"}
 
 
 def reference_arm(args):
