@@ -159,7 +159,7 @@ def allsum(ws, v):
 # once the kernel changes.  The kernel has changed since that capture (the
 # per-site norm sums), so no ratio is applied.
 # DRAM bytes (ncu dram__bytes_read.sum + write.sum) / algorithmic bytes of
-# captured launches of the current kernels (None: no capture of this build)
+# captured launches of the current kernels (None: no capture of the current code)
 TRAFFIC_RATIO = {# 16^4 block level, 256 blocks x 12 systems: 12.48 GB of DRAM traffic
                  # for 118.9 GB of algorithmic bytes in one launch
                  "block_solve_cluster_kernel": 0.105,
