@@ -153,13 +153,9 @@ def allsum(ws, v):
     return float(t.item())
 
 
-# DRAM bytes / algorithmic bytes of one ncu capture of the kernel on the
-# bench's workload (profiles/block_solve_cluster_kernel_fp32_16x4.md: the
-# first timed block-solver launch, branch-free hop variant: 0.148); None
-# once the kernel changes.  The kernel has changed since that capture (the
-# per-site norm sums), so no ratio is applied.
 # DRAM bytes (ncu dram__bytes_read.sum + write.sum) / algorithmic bytes of
-# captured launches of the current kernels (None: no capture of the current code)
+# captured launches of the current kernels (profiles/; None: no capture of
+# the current code -- set back to None whenever the kernel changes)
 TRAFFIC_RATIO = {# 16^4 block level, 256 blocks x 12 systems: 12.48 GB of DRAM traffic
                  # for 118.9 GB of algorithmic bytes in one launch
                  "block_solve_cluster_kernel": 0.105,
