@@ -104,3 +104,12 @@ def test_delta_statistics_and_gaussian_prediction():
     assert bench.delta_stats([{"delta_block": np.zeros(3), "accept_block": np.ones(3, bool),
                                "delta_global": 0.0, "accept_global": True,
                                "n_accept_blocks": 0}])["block"]["gaussian_prediction"] == 1.0
+
+
+def test_oracle_step_model_against_complete_oracle_steps():
+    """The calibration the CPU baseline carries: complete oracle filter steps
+    at 4^4 against the component model's prediction (within a factor of 2)."""
+    r = bench.oracle_model_check(steps=1)
+    assert r["workload"] == "4^4" and r["steps"] == 1
+    assert r["measured_s_per_step"] > 0 and r["model_s_per_step"] > 0
+    assert 0.5 < r["model_over_measured"] < 2.0, r
