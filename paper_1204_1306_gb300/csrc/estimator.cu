@@ -13,6 +13,7 @@
 // All interpolation steps i are batched into every launch (system index =
 // i), and all blocks of a level are solved by one persistent launch.
 #include "estimator.hpp"
+#include "interp_plan.hpp"
 #include "gauge.hpp"
 #include "solver.hpp"
 
@@ -151,12 +152,10 @@ int chunk_size(psms_ctx *c, int N, double bytes_per_site) {
     double budget = std::min(64e9, 0.45 * (double)tot);
     int k = (int)(budget / (bytes_per_site * (double)c->g.V));
     if (c->max_chunk > 0) k = std::min(k, c->max_chunk);
-    k = std::max(1, std::min(N, k));
-    // as many chunks as the budget needs, of equal size (N = 12 with room
-    // for 11 runs as 6 + 6, not 11 + 1, so that no chunk runs a lone system
-    // through a level's fixed per-chunk work)
-    const int n_chunks = (N + k - 1) / k;
-    return (N + n_chunks - 1) / n_chunks;
+    // chunks of equal size (N = 12 with room for 11 runs as 6 + 6, not
+    // 11 + 1, so that no chunk runs a lone system through a level's fixed
+    // per-chunk work)
+    return balanced_chunk(std::max(N, 1), k);
 }
 
 static void check_status(psms_ctx *c, const int *d_status, int n, const char *what) {
@@ -424,14 +423,7 @@ SharedEnds shared_ends(psms_ctx *c, const double2 *ends64, const char *tag) {
 LinkInterp link_interp(psms_ctx *c, const SharedEnds &e, int N, int i0, int n, int shift, int mode,
                        const char *tag) {
     std::vector<float2> h(n);
-    for (int k = 0; k < n; ++k) {
-        if (mode == PSMS_EST_INDEPENDENT) {
-            h[k] = shift ? make_float2(0.f, 1.f) : make_float2(1.f, 0.f);
-        } else {
-            const int i = i0 + k + shift;
-            h[k] = make_float2((float)((double)(N - i) / N), (float)((double)i / N));
-        }
-    }
+    interp_coefs(N, i0, n, shift, mode == PSMS_EST_INDEPENDENT, reinterpret_cast<float *>(h.data()));
     float2 *d = (float2 *)scratch(c, std::string("li_ab_") + tag, sizeof(float2) * n);
     cuda_check(cudaMemcpyAsync(d, h.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, c->stream), "link coefs");
     cuda_check(cudaStreamSynchronize(c->stream), "link coefs");
